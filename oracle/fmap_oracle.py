@@ -1,0 +1,220 @@
+"""FP64 CPU oracle for the functional-map hot path.
+
+TEST INFRASTRUCTURE ONLY. This module is imported by the tests, by
+``__graft_entry__.smoke()`` and by the ``cpu_baseline`` / reference leg of
+``bench.py``, and by nothing else. The CUDA path never imports, links or calls
+it, and it shares no code, table or helper with the CUDA path.
+
+Everything is plain NumPy in float64, written from the paper (DeepShapeMatchingKit,
+arXiv 2604.10377, Sec. 3.1 "Batched Functional Map Solver"):
+
+* Eq. 1: spectral descriptors A = Phi_X^+ F_X, B = Phi_Y^+ F_Y. The pseudo-inverse
+  of an M-orthonormal basis is taken in the M inner product, Phi^+ = Phi^T M
+  (reading R1 of the design notes: it is the left inverse, Phi^T M Phi = I).
+* Eq. 2: the energy ||C A - B||^2 + lambda ||C Delta_X - Delta_Y C||^2.
+* Eq. 3: with Delta diagonal in its eigenbasis, the commutativity term is the
+  entry-wise weight D_ij = (Lambda_Y(i) - Lambda_X(j))^2.
+* Eq. 4: normal equations C A A^T + lambda (D o C) = B A^T.
+* Eq. 5-7: row i of C solves (A A^T + lambda diag(D_i)) c_i = (B A^T)_i.
+* Eq. 8-9: the rows are independent, so all of them are solved as one batch.
+
+The solve uses a Cholesky factorisation written out below (the row systems are
+symmetric positive definite when A A^T or every lambda D_ij is positive). If a
+pivot is not positive the oracle raises ``NotSPD``.
+
+The backward pass (not in the paper) is the adjoint of Eq. 5 derived by hand:
+gamma_i = S_i^{-1} dL/dc_i, dB = Gamma A, dA = Gamma^T B - (Gamma^T C + C^T Gamma) A,
+dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C), dF = M Phi dA.
+
+Parity pins: every function here is checked against something other than itself
+in tests/test_oracle_pins.py (Kronecker k^2 x k^2 solve, lambda = 0 closed form,
+identity case, energy minimality, exact rational solve, Moore-Penrose inverse,
+finite differences, LAPACK). No function is "parity unpinned".
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+class NotSPD(ArithmeticError):
+    def __init__(self, row, column):
+        super().__init__(f"row system {row}: pivot {column} is not positive")
+        self.row = row
+        self.column = column
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 — spectral projection
+# --------------------------------------------------------------------------
+def project(phi, mass, feat):
+    """A = Phi^T diag(M) F (Eq. 1 with Phi^+ = Phi^T M). phi (n, k), mass (n,), feat (n, d)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    mass = np.asarray(mass, dtype=np.float64)
+    feat = np.asarray(feat, dtype=np.float64)
+    return phi.T @ (mass[:, None] * feat)
+
+
+def project_backward(phi, mass, d_a):
+    """dL/dF = diag(M) Phi dL/dA (chain rule of Eq. 1)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    mass = np.asarray(mass, dtype=np.float64)
+    return mass[:, None] * (phi @ np.asarray(d_a, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# Eq. 3 / Eq. 4 — the penalty mask
+# --------------------------------------------------------------------------
+def mask_from_evals(evals_x, evals_y):
+    """D_ij = (Lambda_Y(i) - Lambda_X(j))^2: row i indexes the target basis."""
+    ex = np.asarray(evals_x, dtype=np.float64)
+    ey = np.asarray(evals_y, dtype=np.float64)
+    return (ey[:, None] - ex[None, :]) ** 2
+
+
+# --------------------------------------------------------------------------
+# Eq. 2 — the energy the map minimises
+# --------------------------------------------------------------------------
+def energy(c, a, b, evals_x, evals_y, lam):
+    """||C A - B||_F^2 + lambda ||C Delta_X - Delta_Y C||_F^2 with Delta = diag(eigenvalues)."""
+    c = np.asarray(c, dtype=np.float64)
+    dx = np.diag(np.asarray(evals_x, dtype=np.float64))
+    dy = np.diag(np.asarray(evals_y, dtype=np.float64))
+    r = c @ a - b
+    s = c @ dx - dy @ c
+    return float(np.sum(r * r) + lam * np.sum(s * s))
+
+
+# --------------------------------------------------------------------------
+# Cholesky factorisation and triangular solves (batched over leading axes)
+# --------------------------------------------------------------------------
+def cholesky(s):
+    """Lower L with L L^T = S for every matrix of the batch s (..., k, k).
+
+    Column by column (Cholesky-Crout): L_jj = sqrt(S_jj - sum_{m<j} L_jm^2),
+    L_ij = (S_ij - sum_{m<j} L_im L_jm) / L_jj for i > j.
+    """
+    s = np.asarray(s, dtype=np.float64)
+    batch_shape = s.shape[:-2]
+    k = s.shape[-1]
+    sf = s.reshape((-1, k, k))
+    l = np.zeros_like(sf)
+    for j in range(k):
+        lj = l[:, j, :j]                                   # (b, j)
+        piv = sf[:, j, j] - np.einsum("bm,bm->b", lj, lj)
+        bad = ~(piv > 0.0)
+        if np.any(bad):
+            raise NotSPD(int(np.argmax(bad)), j)
+        ljj = np.sqrt(piv)
+        l[:, j, j] = ljj
+        if j + 1 < k:
+            below = sf[:, j + 1:, j] - np.einsum("bim,bm->bi", l[:, j + 1:, :j], lj)
+            l[:, j + 1:, j] = below / ljj[:, None]
+    return l.reshape(batch_shape + (k, k))
+
+
+def cholesky_solve(l, rhs):
+    """x with (L L^T) x = rhs, batched: l (..., k, k), rhs (..., k)."""
+    l = np.asarray(l, dtype=np.float64)
+    rhs = np.asarray(rhs, dtype=np.float64)
+    k = l.shape[-1]
+    lf = l.reshape((-1, k, k))
+    bf = rhs.reshape((-1, k))
+    y = np.zeros_like(bf)
+    for i in range(k):                      # L y = b
+        y[:, i] = (bf[:, i] - np.einsum("bm,bm->b", lf[:, i, :i], y[:, :i])) / lf[:, i, i]
+    x = np.zeros_like(bf)
+    for i in range(k - 1, -1, -1):          # L^T x = y
+        x[:, i] = (y[:, i] - np.einsum("bm,bm->b", lf[:, i + 1:, i], x[:, i + 1:])) / lf[:, i, i]
+    return x.reshape(rhs.shape)
+
+
+# --------------------------------------------------------------------------
+# Eq. 4-9 — the row-wise (batched) regularised solve
+# --------------------------------------------------------------------------
+def row_systems(a, d_mask, lam):
+    """S_i = A A^T + lambda diag(D_i) for every row i, stacked as (k, k, k) (Eq. 5, Eq. 8)."""
+    a = np.asarray(a, dtype=np.float64)
+    d_mask = np.asarray(d_mask, dtype=np.float64)
+    g = a @ a.T
+    k = g.shape[0]
+    s = np.broadcast_to(g, (k, k, k)).copy()
+    idx = np.arange(k)
+    s[:, idx, idx] += lam * d_mask
+    return s
+
+
+def solve(a, b, d_mask, lam, return_factors=False):
+    """C minimising Eq. 2 (with Eq. 3's weights): row i solves Eq. 5."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = row_systems(a, d_mask, lam)
+    r = b @ a.T                              # right-hand sides, row i = (B A^T)_i
+    l = cholesky(s)
+    c = cholesky_solve(l, r)
+    return (c, l) if return_factors else c
+
+
+def solve_backward(a, b, c, d_mask, lam, d_c, factors=None):
+    """Adjoint of the row-wise solve. Returns dict(gamma, dA, dB, dD, dlam)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    d_mask = np.asarray(d_mask, dtype=np.float64)
+    d_c = np.asarray(d_c, dtype=np.float64)
+    l = factors if factors is not None else cholesky(row_systems(a, d_mask, lam))
+    gamma = cholesky_solve(l, d_c)           # row i: S_i gamma_i = dL/dc_i
+    w = gamma.T @ c + c.T @ gamma
+    d_a = gamma.T @ b - w @ a
+    d_b = gamma @ a
+    d_d = -lam * gamma * c
+    d_lam = float(-np.sum(d_mask * gamma * c))
+    return dict(gamma=gamma, dA=d_a, dB=d_b, dD=d_d, dlam=d_lam)
+
+
+# --------------------------------------------------------------------------
+# Training loss used by the differentiable workloads
+# --------------------------------------------------------------------------
+def loss_orth_gt(c, c_gt):
+    """L = ||C C^T - I||_F^2 + ||C - C_gt||_F^2 and dL/dC = 4 (C C^T - I) C + 2 (C - C_gt)."""
+    c = np.asarray(c, dtype=np.float64)
+    c_gt = np.asarray(c_gt, dtype=np.float64)
+    e = c @ c.T - np.eye(c.shape[0])
+    r = c - c_gt
+    return float(np.sum(e * e) + np.sum(r * r)), 4.0 * e @ c + 2.0 * r
+
+
+# --------------------------------------------------------------------------
+# Whole batches: lists of shapes and pairs
+# --------------------------------------------------------------------------
+def pair_mask(shape_x, shape_y, explicit_mask=None):
+    if explicit_mask is not None:
+        return np.asarray(explicit_mask, dtype=np.float64)
+    return mask_from_evals(shape_x["evals"], shape_y["evals"])
+
+
+def forward_batch(shapes, pairs):
+    """shapes: list of dict(phi, mass, feat, evals); pairs: list of dict(x, y, lam, mask).
+
+    Returns dict(A=[per shape], C=[per pair])."""
+    a_list = [project(s["phi"], s["mass"], s["feat"]) for s in shapes]
+    c_list = []
+    for p in pairs:
+        sx, sy = shapes[p["x"]], shapes[p["y"]]
+        dm = pair_mask(sx, sy, p.get("mask"))
+        c_list.append(solve(a_list[p["x"]], a_list[p["y"]], dm, p["lam"]))
+    return dict(A=a_list, C=c_list)
+
+
+def backward_batch(shapes, pairs, fwd, d_c_list):
+    """Gradients of sum_p <dC_p, C_p> w.r.t. every A and F (shapes may be shared by pairs)."""
+    d_a = [np.zeros_like(a) for a in fwd["A"]]
+    extra = []
+    for p, dc in zip(pairs, d_c_list):
+        sx, sy = shapes[p["x"]], shapes[p["y"]]
+        dm = pair_mask(sx, sy, p.get("mask"))
+        g = solve_backward(fwd["A"][p["x"]], fwd["A"][p["y"]], fwd["C"][len(extra)], dm, p["lam"], dc)
+        d_a[p["x"]] += g["dA"]
+        d_a[p["y"]] += g["dB"]
+        extra.append(g)
+    d_f = [project_backward(s["phi"], s["mass"], da) for s, da in zip(shapes, d_a)]
+    return dict(dA=d_a, dF=d_f, pair=extra)

@@ -1,0 +1,337 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each pin is chosen so that a plausible slip in the oracle (a transposed mask, a
+dropped lambda, a sign error in the adjoint, a missing mass factor, a transposed
+operand) fails at least one of them; ``test_planted_mistakes`` plants such slips
+and checks that they are caught.
+"""
+import fractions
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fmap_oracle as orc
+from paper_2604_10377_gb300 import synth
+from _bridge import oracle_inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_problem(seed, k, d, lam=None, positive_mask=True):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((k, d))
+    b = rng.standard_normal((k, d))
+    ex = np.sort(rng.uniform(0, 10, k))
+    ey = np.sort(rng.uniform(0, 10, k))
+    lam = rng.uniform(0.05, 2.0) if lam is None else lam
+    return a, b, ex, ey, lam
+
+
+# ---------------------------------------------------------------- solve pins
+@pytest.mark.parametrize("k,d", [(1, 3), (2, 2), (3, 5), (5, 9), (8, 4), (6, 12)])
+def test_vectorised_least_squares(k, d):
+    """The k^2 x k^2 vectorised least-squares form (Sec. 3.1, the approach that is
+    'only tractable for small k'), solved by LAPACK lstsq (SVD), not by normal
+    equations: vec(C A) = (A^T kron I) vec(C), penalty rows sqrt(lambda D_ij)."""
+    a, b, ex, ey, lam = _rand_problem(k * 100 + d, k, d)
+    dm = orc.mask_from_evals(ex, ey)
+    # column-major vec: vec(C)[i + k j] = C[i, j]
+    top = np.kron(a.T, np.eye(k))                      # (k d, k^2)
+    pen = np.diag(np.sqrt(lam * dm.flatten(order="F")))
+    sys_m = np.vstack([top, pen])
+    rhs = np.concatenate([b.flatten(order="F"), np.zeros(k * k)])
+    vec_c, *_ = np.linalg.lstsq(sys_m, rhs, rcond=None)
+    c_ref = vec_c.reshape((k, k), order="F")
+    c = orc.solve(a, b, dm, lam)
+    np.testing.assert_allclose(c, c_ref, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("k,d", [(3, 7), (10, 30), (30, 64)])
+def test_lambda_zero_closed_form(k, d):
+    """Data term only (lambda = 0): C = B A^T (A A^T)^{-1}."""
+    a, b, ex, ey, _ = _rand_problem(7 + k, k, d)
+    c = orc.solve(a, b, orc.mask_from_evals(ex, ey), 0.0)
+    c_ref = b @ a.T @ np.linalg.inv(a @ a.T)
+    np.testing.assert_allclose(c, c_ref, rtol=1e-9, atol=1e-10)
+
+
+@pytest.mark.parametrize("k,d", [(4, 9), (30, 128), (50, 40)])
+def test_identity_case(k, d):
+    """Same descriptors and same eigenvalues on both sides: zero energy at C = I,
+    and the energy is strictly convex, so C = I (d < k included: the mask's
+    off-diagonal entries are positive)."""
+    rng = np.random.default_rng(k)
+    a = rng.standard_normal((k, d))
+    ev = np.sort(rng.uniform(0, 100, k))
+    c = orc.solve(a, a, orc.mask_from_evals(ev, ev), 1e-3)
+    np.testing.assert_allclose(c, np.eye(k), atol=1e-9)
+
+
+@pytest.mark.parametrize("k,d", [(3, 4), (7, 11), (12, 5)])
+def test_energy_stationary_and_minimal(k, d):
+    """The solution minimises Eq. 2 written with Laplacians Delta = diag(Lambda):
+    finite-difference gradient of that energy vanishes and random perturbations
+    raise it. This pins the orientation of the mask (row = target eigenvalue)."""
+    a, b, ex, ey, lam = _rand_problem(k * 31 + d, k, d)
+    c = orc.solve(a, b, orc.mask_from_evals(ex, ey), lam)
+    e0 = orc.energy(c, a, b, ex, ey, lam)
+    h = 1e-5
+    scale = max(1.0, e0)
+    for i in range(k):
+        for j in range(k):
+            cp = c.copy(); cp[i, j] += h
+            cm = c.copy(); cm[i, j] -= h
+            g = (orc.energy(cp, a, b, ex, ey, lam) - orc.energy(cm, a, b, ex, ey, lam)) / (2 * h)
+            assert abs(g) < 1e-6 * scale
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        v = rng.standard_normal((k, k)) * 1e-3
+        assert orc.energy(c + v, a, b, ex, ey, lam) > e0
+
+
+def test_exact_rational_small():
+    """Exact minimiser of Eq. 2 by symbolic differentiation (sympy, rational
+    arithmetic) on a tiny integer problem."""
+    sp = pytest.importorskip("sympy")
+    k, d = 2, 3
+    a = sp.Matrix([[1, 2, 0], [0, 1, 3]])
+    b = sp.Matrix([[2, 1, 1], [1, 0, 2]])
+    ex, ey = [1, 4], [2, 5]
+    lam = sp.Rational(1, 3)
+    cs = sp.Matrix(k, k, lambda i, j: sp.Symbol(f"c{i}{j}"))
+    dx, dy = sp.diag(*ex), sp.diag(*ey)
+    r = cs * a - b
+    s = cs * dx - dy * cs
+    e = sum(x ** 2 for x in r) + lam * sum(x ** 2 for x in s)
+    sol = sp.solve([sp.diff(e, v) for v in cs], list(cs), dict=True)[0]
+    c_exact = np.array([[float(sol[cs[i, j]]) for j in range(k)] for i in range(k)])
+    c = orc.solve(np.array(a, dtype=float), np.array(b, dtype=float),
+                  orc.mask_from_evals(np.array(ex, float), np.array(ey, float)), 1.0 / 3.0)
+    np.testing.assert_allclose(c, c_exact, rtol=1e-12)
+
+
+def test_golden_scalar_case():
+    """k = 1 worked by hand (tests/golden/scalar_k1.txt)."""
+    vals = {}
+    with open(os.path.join(GOLDEN, "scalar_k1.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                key, val = line.split("=")
+                vals[key.strip()] = val.strip()
+    a = np.array([[float(x) for x in vals["A"].split()]])
+    b = np.array([[float(x) for x in vals["B"].split()]])
+    lam = float(fractions.Fraction(vals["lambda"]))
+    c = orc.solve(a, b, orc.mask_from_evals([float(vals["eval_x"])], [float(vals["eval_y"])]), lam)
+    assert abs(c[0, 0] - float(fractions.Fraction(vals["C"]))) < 1e-14
+
+
+@pytest.mark.parametrize("k", [1, 5, 40])
+def test_cholesky_against_lapack(k):
+    rng = np.random.default_rng(k)
+    m = rng.standard_normal((3, k, k + 3))
+    s = m @ np.swapaxes(m, 1, 2) + 0.1 * np.eye(k)
+    l = orc.cholesky(s)
+    np.testing.assert_allclose(l, np.linalg.cholesky(s), rtol=1e-10, atol=1e-12)
+    rhs = rng.standard_normal((3, k))
+    x = orc.cholesky_solve(l, rhs)
+    np.testing.assert_allclose(x, np.linalg.solve(s, rhs[..., None])[..., 0], rtol=1e-9, atol=1e-11)
+
+
+def test_row_systems_against_lapack_per_row():
+    """Every row of C solves its own system (Eq. 5), checked one row at a time with
+    LAPACK's general LU solve, as the loop formulation does."""
+    k, d = 20, 33
+    a, b, ex, ey, lam = _rand_problem(5, k, d)
+    dm = orc.mask_from_evals(ex, ey)
+    c = orc.solve(a, b, dm, lam)
+    for i in range(k):
+        lhs = a @ a.T + lam * np.diag(dm[i])
+        np.testing.assert_allclose(c[i], np.linalg.solve(lhs, (b @ a.T)[i]), rtol=1e-9, atol=1e-12)
+
+
+def test_not_spd_raises():
+    a = np.zeros((3, 2)); a[0, 0] = 1.0; a[1, 1] = 1.0      # rank 2 < k = 3
+    ev = np.array([1.0, 2.0, 3.0])
+    with pytest.raises(orc.NotSPD):
+        orc.solve(a, a, orc.mask_from_evals(ev, ev), 0.0)
+
+
+def test_feature_rotation_invariance():
+    """F -> F Q with Q orthogonal leaves A A^T and B A^T, hence C, unchanged."""
+    k, d = 6, 10
+    a, b, ex, ey, lam = _rand_problem(11, k, d)
+    q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((d, d)))
+    dm = orc.mask_from_evals(ex, ey)
+    np.testing.assert_allclose(orc.solve(a @ q, b @ q, dm, lam), orc.solve(a, b, dm, lam), rtol=1e-9, atol=1e-12)
+
+
+def test_target_permutation_equivariance():
+    """Permuting the target basis (rows of B, target eigenvalues) permutes rows of C."""
+    k, d = 7, 12
+    a, b, ex, ey, lam = _rand_problem(13, k, d)
+    perm = np.random.default_rng(3).permutation(k)
+    c = orc.solve(a, b, orc.mask_from_evals(ex, ey), lam)
+    cp = orc.solve(a, b[perm], orc.mask_from_evals(ex, ey[perm]), lam)
+    np.testing.assert_allclose(cp, c[perm], rtol=1e-9, atol=1e-12)
+
+
+def test_feature_scaling():
+    """(alpha F, lambda) gives the same C as (F, lambda / alpha^2)."""
+    k, d = 5, 8
+    a, b, ex, ey, lam = _rand_problem(17, k, d)
+    dm = orc.mask_from_evals(ex, ey)
+    np.testing.assert_allclose(orc.solve(3 * a, 3 * b, dm, lam), orc.solve(a, b, dm, lam / 9), rtol=1e-9)
+
+
+# ---------------------------------------------------------------- projection pins
+def test_projection_is_moore_penrose_for_uniform_mass():
+    """Eq. 1 literally: with uniform mass c I and Phi^T M Phi = I, Phi^T M = pinv(Phi)."""
+    n, k, d = 300, 12, 7
+    rng = np.random.default_rng(0)
+    mass = np.full(n, 1.0 / n)
+    phi = synth.m_orthonormalize(rng.standard_normal((n, k)), mass)
+    feat = rng.standard_normal((n, d))
+    np.testing.assert_allclose(orc.project(phi, mass, feat), np.linalg.pinv(phi) @ feat, rtol=1e-9, atol=1e-12)
+
+
+def test_projection_recovers_spectral_coefficients():
+    """Non-uniform mass: F = Phi X with Phi M-orthonormal gives A = X exactly."""
+    n, k, d = 500, 9, 4
+    rng = np.random.default_rng(1)
+    mass = rng.uniform(0.5, 1.5, n) / n
+    phi = synth.m_orthonormalize(rng.standard_normal((n, k)), mass)
+    x = rng.standard_normal((k, d))
+    np.testing.assert_allclose(orc.project(phi, mass, phi @ x), x, rtol=1e-9, atol=1e-11)
+
+
+def test_projection_bruteforce():
+    n, k, d = 17, 3, 4
+    rng = np.random.default_rng(4)
+    phi, mass, feat = rng.standard_normal((n, k)), rng.uniform(0.1, 1, n), rng.standard_normal((n, d))
+    ref = np.zeros((k, d))
+    for v in range(n):
+        for i in range(k):
+            for j in range(d):
+                ref[i, j] += phi[v, i] * mass[v] * feat[v, j]
+    np.testing.assert_allclose(orc.project(phi, mass, feat), ref, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- gradient pins
+def _pipeline_loss(shapes, pairs, gts):
+    fwd = orc.forward_batch(shapes, pairs)
+    total = 0.0
+    dcs = []
+    for c, gt in zip(fwd["C"], gts):
+        l, dc = orc.loss_orth_gt(c, gt)
+        total += l
+        dcs.append(dc)
+    return total, fwd, dcs
+
+
+def test_gradients_against_central_differences():
+    """Analytic dF (adjoint of Eq. 5 + chain rule of Eq. 1) against central finite
+    differences (h = 1e-4) of the whole FP64 pipeline, on 12 random directions per
+    feature tensor plus single coordinates; a shape shared by two pairs included."""
+    wl = synth.make_small(5, 2, (60, 90), [5, 7], 9)
+    shapes, pairs = oracle_inputs(wl)
+    # a third pair maps shape 1 back onto shape 0 (both k = 5): gradients of a
+    # shape used by two pairs must add up
+    pairs.append(dict(x=1, y=0, lam=0.02, mask=None))
+    gts = [synth.random_orthogonal(40 + i, shapes[p["x"]]["phi"].shape[1]) for i, p in enumerate(pairs)]
+    loss0, fwd, dcs = _pipeline_loss(shapes, pairs, gts)
+    grads = orc.backward_batch(shapes, pairs, fwd, dcs)
+    rng = np.random.default_rng(0)
+    h = 1e-4
+    for si, s in enumerate(shapes):
+        for trial in range(14):
+            if trial < 12:
+                v = rng.standard_normal(s["feat"].shape)
+            else:
+                v = np.zeros_like(s["feat"]); v[rng.integers(s["feat"].shape[0]), rng.integers(s["feat"].shape[1])] = 1.0
+            sp = [dict(x) for x in shapes]; sp[si] = dict(s, feat=s["feat"] + h * v)
+            sm = [dict(x) for x in shapes]; sm[si] = dict(s, feat=s["feat"] - h * v)
+            fd = (_pipeline_loss(sp, pairs, gts)[0] - _pipeline_loss(sm, pairs, gts)[0]) / (2 * h)
+            an = float(np.sum(grads["dF"][si] * v))
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (si, trial, fd, an)
+
+
+def test_mask_and_lambda_gradients():
+    k, d = 6, 9
+    a, b, ex, ey, lam = _rand_problem(21, k, d)
+    dm = orc.mask_from_evals(ex, ey)
+    gt = synth.random_orthogonal(3, k).astype(np.float64)
+
+    def loss(dmask, lm):
+        return orc.loss_orth_gt(orc.solve(a, b, dmask, lm), gt)[0]
+
+    c = orc.solve(a, b, dm, lam)
+    _, dc = orc.loss_orth_gt(c, gt)
+    g = orc.solve_backward(a, b, c, dm, lam, dc)
+    h = 1e-4
+    fd_lam = (loss(dm, lam + h) - loss(dm, lam - h)) / (2 * h)
+    assert abs(fd_lam - g["dlam"]) < 1e-6 * max(1, abs(fd_lam))
+    for (i, j) in [(0, 0), (2, 5), (5, 1)]:
+        e = np.zeros_like(dm); e[i, j] = 1.0
+        fd = (loss(dm + h * e, lam) - loss(dm - h * e, lam)) / (2 * h)
+        assert abs(fd - g["dD"][i, j]) < 1e-6 * max(1, abs(fd))
+
+
+def test_loss_gradient_fd():
+    rng = np.random.default_rng(8)
+    c = rng.standard_normal((5, 5)); gt = rng.standard_normal((5, 5))
+    _, g = orc.loss_orth_gt(c, gt)
+    h = 1e-5
+    for i in range(5):
+        for j in range(5):
+            e = np.zeros((5, 5)); e[i, j] = h
+            fd = (orc.loss_orth_gt(c + e, gt)[0] - orc.loss_orth_gt(c - e, gt)[0]) / (2 * h)
+            assert abs(fd - g[i, j]) < 1e-6 * max(1, abs(fd))
+
+
+def test_batched_equals_loop():
+    """Sec. 3.1: the batched solve of all rows equals solving them one at a time."""
+    k, d = 15, 20
+    a, b, ex, ey, lam = _rand_problem(23, k, d)
+    dm = orc.mask_from_evals(ex, ey)
+    c = orc.solve(a, b, dm, lam)
+    g, r = a @ a.T, b @ a.T
+    rows = [orc.cholesky_solve(orc.cholesky(g + lam * np.diag(dm[i])), r[i]) for i in range(k)]
+    np.testing.assert_allclose(np.stack(rows), c, rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_mistakes(monkeypatch):
+    """Each planted slip in the oracle must make at least one pin fail."""
+    import importlib
+    pins = [
+        lambda: test_vectorised_least_squares(5, 9),
+        lambda: test_energy_stationary_and_minimal(7, 11),
+        lambda: test_projection_recovers_spectral_coefficients(),
+        lambda: test_gradients_against_central_differences(),
+        lambda: test_lambda_zero_closed_form(10, 30),
+    ]
+
+    def caught():
+        for pin in pins:
+            try:
+                pin()
+            except AssertionError:
+                return True
+        return False
+
+    good_mask, good_project, good_back = orc.mask_from_evals, orc.project, orc.solve_backward
+    good_rows = orc.row_systems
+    mutants = {
+        "transposed mask": ("mask_from_evals", lambda ex, ey: good_mask(ex, ey).T),
+        "no mass in projection": ("project", lambda phi, mass, feat: good_project(phi, np.ones_like(mass) / len(mass), feat)),
+        "dropped lambda": ("row_systems", lambda a, dm, lam: good_rows(a, dm, 0.0 if lam > 0 else lam)),
+        "sign of Gram term in dA": ("solve_backward", lambda a, b, c, dm, lam, dc, factors=None: dict(
+            good_back(a, b, c, dm, lam, dc, factors),
+            dA=good_back(a, b, c, dm, lam, dc, factors)["dA"] + 2 * (good_back(a, b, c, dm, lam, dc, factors)["gamma"].T @ c) @ a)),
+    }
+    for name, (attr, fn) in mutants.items():
+        monkeypatch.setattr(orc, attr, fn)
+        assert caught(), f"planted mistake not caught: {name}"
+        monkeypatch.undo()
