@@ -1,0 +1,187 @@
+/*
+ * fmap.h — C ABI of the GB300 functional-map hot path.
+ *
+ * Operation (DeepShapeMatchingKit, arXiv 2604.10377, Sec. 3.1):
+ *   Eq. 1      A = Phi_X^+ F_X, B = Phi_Y^+ F_Y, with Phi^+ = Phi^T diag(M) for an
+ *              M-orthonormal Laplace-Beltrami basis Phi (n x k), lumped mass M (n)
+ *              and per-vertex features F (n x d).
+ *   Eq. 2-3    C minimises ||C A - B||^2 + lambda * sum_ij D_ij C_ij^2 with
+ *              D_ij = (Lambda_Y(i) - Lambda_X(j))^2 (or a caller-given mask D).
+ *   Eq. 4-7    row i of C solves (A A^T + lambda diag(D_i)) c_i = (B A^T)_i.
+ *   Eq. 8-9    all rows of all pairs are solved as one batch.
+ * The backward pass (adjoint of Eq. 5 and chain rule of Eq. 1) is not in the
+ * paper; it is given at fmap_solve_backward.
+ *
+ * Conventions for every call:
+ *  - Every matrix is row-major. Every pointer named "device" is CUDA device
+ *    memory on the context's device; the caller owns it and keeps it alive and
+ *    unchanged in place while any call that reads it may still be running.
+ *  - Calls only enqueue work on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and never synchronise or allocate device memory;
+ *    scratch comes from the caller's workspace. They may therefore be captured
+ *    into a CUDA graph. Calls on one batch must not overlap in time.
+ *  - Return value: FMAP_OK, or an argument / launch error detected on the host
+ *    (nothing was enqueued in that case). Numerical failures are reported per
+ *    pair, asynchronously, in the device array `status` (see fmap_status).
+ *  - Nothing crosses the boundary as an exception.
+ */
+#ifndef FMAP_H_
+#define FMAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FMAP_API __attribute__((visibility("default")))
+#else
+#define FMAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes and per-pair status codes. A per-pair status word is 0 (OK) or
+ * code | (row << 8), where row is the row system that failed (for NOT_SPD). */
+enum fmap_status {
+    FMAP_OK = 0,
+    FMAP_ERR_INVALID_ARG = 1,   /* null pointer, bad index, size mismatch */
+    FMAP_ERR_UNSUPPORTED = 2,   /* k > 256, d % 16 != 0, misaligned ld, ... */
+    FMAP_ERR_CUDA = 3,          /* a CUDA runtime call failed (see fmap_last_cuda_error) */
+    FMAP_ERR_NOT_SPD = 4,       /* per pair: a row system had a non-positive pivot */
+    FMAP_ERR_NONFINITE = 5,     /* per pair: NaN/Inf in the result */
+    FMAP_ERR_TIMEOUT = 6,       /* per pair: a bounded device-side wait gave up */
+    FMAP_ERR_WORKSPACE = 7      /* workspace pointer NULL, too small or misaligned */
+};
+
+/* Feature precision of a batch. */
+enum fmap_precision {
+    FMAP_PREC_FP32 = 0,  /* F is FP32; projection error ~1e-6 relative */
+    FMAP_PREC_BF16 = 1   /* F is BF16 (its values are exact inputs); FP32 accumulation */
+};
+
+typedef struct fmap_options {
+    int32_t precision;          /* enum fmap_precision */
+    int32_t ir_steps;           /* iterative-refinement steps after the FP32 Cholesky solve (0..3, default 1) */
+    int32_t hi_gram_min_k;      /* pairs with k >= this accumulate A A^T in FP64 (default 200) */
+    int32_t store_factors_max_k;/* fmap_solve saves Cholesky factors for pairs with k <= this when a
+                                   `saved` buffer is given; larger pairs are refactored in the
+                                   backward pass (default 256: store everything) */
+} fmap_options;
+
+typedef struct fmap_shape_desc {
+    int64_t n;             /* vertices, >= 1 */
+    int32_t k;             /* basis size, 1..256 */
+    int32_t d;             /* feature dimension, multiple of 16, <= 4096 */
+    const float* phi;      /* device, n x ld_phi FP32, columns 0..k-1 used (M-orthonormal basis) */
+    int64_t ld_phi;        /* >= k, multiple of 4 (16-byte rows) */
+    const float* mass;     /* device, n FP32: the diagonal of M */
+    const float* evals;    /* device, k FP32 eigenvalues, or NULL if every pair using the
+                              shape passes an explicit mask */
+    const void* feat;      /* device, n x ld_feat, FP32 or BF16 per the batch precision */
+    int64_t ld_feat;       /* >= d, multiple of 8 */
+    void* dfeat;           /* device, same layout and type as feat: receives dL/dF in
+                              fmap_solve_backward; NULL = do not compute it */
+} fmap_shape_desc;
+
+typedef struct fmap_pair_desc {
+    int32_t shape_x;       /* source shape (basis of the columns of C) */
+    int32_t shape_y;       /* target shape (basis of the rows of C); k_x == k_y, d_x == d_y */
+    float lambda;          /* regularisation weight, >= 0 */
+    const float* mask;     /* device k x k FP32 mask D (row i = target basis index), or NULL:
+                              D_ij = (evals_y[i] - evals_x[j])^2 */
+} fmap_pair_desc;
+
+/* Sizes of a batch's buffers. Offsets: A of shape s starts at float a_offset(s) of
+ * the flat A buffer (k_s x d_s, row-major); C of pair p at float c_offset(p) of the
+ * flat C buffer (k_p x k_p, row-major). Offsets are prefix sums in input order. */
+typedef struct fmap_sizes {
+    int64_t a_floats;        /* length of the flat A buffer (also dA) */
+    int64_t c_floats;        /* length of the flat C buffer (also dC, mask gradients) */
+    int64_t ws_bytes;        /* workspace for fmap_project and fmap_solve */
+    int64_t ws_bwd_bytes;    /* workspace for fmap_solve_backward (and everything else) */
+    int64_t saved_bytes;     /* factor storage for pairs with k <= store_factors_max_k */
+    int32_t n_shapes;
+    int32_t n_pairs;
+} fmap_sizes;
+
+typedef struct fmap_ctx fmap_ctx;
+typedef struct fmap_batch fmap_batch;
+
+/* Library version string (static storage). */
+FMAP_API const char* fmap_version(void);
+
+/* Human-readable text of a return or status code (static storage). */
+FMAP_API const char* fmap_error_string(int32_t code);
+
+/* Text of the last CUDA error seen by this thread's calls (static thread-local storage). */
+FMAP_API const char* fmap_last_cuda_error(void);
+
+/* Fill *opt with the defaults: FP32, ir_steps 1, hi_gram_min_k 200, store_factors_max_k 256. */
+FMAP_API int32_t fmap_default_options(fmap_options* opt);
+
+/* Create a context on CUDA device `device` (host only; no device memory is touched
+ * until a batch is created). opt may be NULL for the defaults. */
+FMAP_API int32_t fmap_create(fmap_ctx** out, int32_t device, const fmap_options* opt);
+FMAP_API int32_t fmap_destroy(fmap_ctx* ctx);
+
+/* Host-only planning: validate shapes and pairs against `opt` and report buffer
+ * sizes, without touching the GPU. Returns INVALID_ARG / UNSUPPORTED on bad input. */
+FMAP_API int32_t fmap_plan_sizes(const fmap_options* opt, const fmap_shape_desc* shapes, int32_t n_shapes,
+                        const fmap_pair_desc* pairs, int32_t n_pairs, fmap_sizes* out);
+
+/* Create a batch: validates like fmap_plan_sizes, then builds the device descriptor
+ * tables (the only device memory the library owns, freed by fmap_batch_destroy).
+ * Every device pointer in `shapes` and `pairs` is recorded and read by later calls.
+ * n_pairs == 0 is allowed (all calls are then no-ops). Host arrays are copied. */
+FMAP_API int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t n_shapes,
+                          const fmap_pair_desc* pairs, int32_t n_pairs, fmap_batch** out);
+FMAP_API int32_t fmap_batch_destroy(fmap_batch* batch);
+FMAP_API int32_t fmap_batch_sizes(const fmap_batch* batch, fmap_sizes* out);
+
+/* Host copies of the offsets: a_offsets[n_shapes + 1], c_offsets[n_pairs + 1] (floats). */
+FMAP_API int32_t fmap_batch_offsets(const fmap_batch* batch, int64_t* a_offsets, int64_t* c_offsets);
+
+/* Eq. 1: A_s = Phi_s^T diag(M_s) F_s for every shape s into the flat buffer a_out
+ * (device, sizes.a_floats FP32). ws: device workspace of >= sizes.ws_bytes bytes,
+ * 256-byte aligned. Summation order is fixed, so results are bitwise reproducible. */
+FMAP_API int32_t fmap_project(fmap_batch* batch, float* a_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Eq. 4-9: for every pair p and row i, solve (A_x A_x^T + lambda diag(D_i)) c_i = (A_y A_x^T)_i
+ * by Cholesky in FP32 (the Gram matrix accumulated in FP64 when k >= hi_gram_min_k),
+ * followed by opt.ir_steps steps of iterative refinement, and write C_p (device flat
+ * buffer, sizes.c_floats FP32).
+ *   a      device flat A buffer as written by fmap_project
+ *   saved  device buffer of sizes.saved_bytes for the factors, or NULL
+ *   status device int32[n_pairs]: overwritten with 0 or an fmap_status | row << 8.
+ *          A failed pair's C is filled with NaN. */
+FMAP_API int32_t fmap_solve(fmap_batch* batch, const float* a, float* c_out, void* saved, int32_t* status,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of fmap_solve and fmap_project, given G = dL/dC (flat, c_offsets):
+ *   gamma_i = S_i^{-1} G_i                    (S_i the row system of Eq. 5)
+ *   dL/dA_y += Gamma A_x
+ *   dL/dA_x += Gamma^T A_y - (Gamma^T C + C^T Gamma) A_x
+ *   dL/dD    = -lambda Gamma o C              (d_mask, optional, c_offsets layout)
+ *   dL/dlambda = -sum(D o Gamma o C)         (d_lambda[n_pairs], optional)
+ *   dL/dF_s  = diag(M_s) Phi_s dL/dA_s        written to shapes[s].dfeat when non-NULL
+ * Contributions of a shape used by several pairs add up (fixed order).
+ *   d_c, a, c  device, as in fmap_solve (c = its output)
+ *   saved      the buffer fmap_solve filled, or NULL to refactor every pair
+ *   d_a        device flat buffer (a_floats) receiving dL/dA, or NULL
+ *   status     device int32[n_pairs], as in fmap_solve
+ *   ws         >= sizes.ws_bwd_bytes */
+FMAP_API int32_t fmap_solve_backward(fmap_batch* batch, const float* d_c, const float* a, const float* c,
+                            const void* saved, float* d_a, float* d_mask, float* d_lambda,
+                            int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* The training loss of the differentiable workloads, per pair:
+ *   L_p = ||C C^T - I||_F^2 + ||C - C_gt||_F^2,  dL/dC = 4 (C C^T - I) C + 2 (C - C_gt).
+ * c, c_gt, d_c: device flat buffers (c_offsets); loss: device float[n_pairs]. ws as fmap_solve. */
+FMAP_API int32_t fmap_loss_orth(fmap_batch* batch, const float* c, const float* c_gt, float* loss, float* d_c,
+                       void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMAP_H_ */

@@ -1,0 +1,287 @@
+"""Python front end of the functional-map library.
+
+A batch of shape pairs lives in a handful of flat device buffers (bases, masses,
+eigenvalues, features, feature gradients), laid out by :class:`BatchLayout`.
+:class:`FmapBatch` binds those buffers to a C-ABI batch once; every later call
+(project, solve, solve_backward, loss) only enqueues kernels of libfmap.so on the
+current torch stream. Torch provides the memory and the stream, nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FmapError, check
+
+
+def _round_up(x: int, a: int) -> int:
+    return (x + a - 1) // a * a
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class BatchLayout:
+    """Offsets of every shape inside the flat buffers (128-byte aligned blocks).
+
+    phi: n x ld_phi FP32 with ld_phi = k rounded up to 4; mass: n FP32; evals: k FP32;
+    feat / dfeat: n x d in the feature dtype."""
+
+    def __init__(self, ns: Sequence[int], ks: Sequence[int], ds: Sequence[int], feat_dtype: str):
+        assert len(ns) == len(ks) == len(ds)
+        self.ns, self.ks, self.ds = [int(x) for x in ns], [int(x) for x in ks], [int(x) for x in ds]
+        self.feat_dtype = feat_dtype
+        self.ld_phi = [_round_up(k, 4) for k in self.ks]
+        self.phi_off, self.mass_off, self.evals_off, self.feat_off = [], [], [], []
+        p = m = e = f = 0
+        for n, k, d, ld in zip(self.ns, self.ks, self.ds, self.ld_phi):
+            self.phi_off.append(p); p = _round_up(p + n * ld, 32)
+            self.mass_off.append(m); m = _round_up(m + n, 32)
+            self.evals_off.append(e); e = _round_up(e + k, 32)
+            self.feat_off.append(f); f = _round_up(f + n * d, 64)
+        self.phi_len, self.mass_len, self.evals_len, self.feat_len = p, m, e, f
+
+    @property
+    def n_shapes(self):
+        return len(self.ns)
+
+    def torch_feat_dtype(self):
+        return torch.bfloat16 if self.feat_dtype == "bf16" else torch.float32
+
+    def pack_host(self, shapes) -> dict:
+        """Flat host arrays (NumPy) for a list of synth.Shape-like objects."""
+        phi = np.zeros(self.phi_len, np.float32)
+        mass = np.zeros(self.mass_len, np.float32)
+        evals = np.zeros(self.evals_len, np.float32)
+        fdt = np.uint16 if self.feat_dtype == "bf16" else np.float32
+        feat = np.zeros(self.feat_len, fdt)
+        for i, s in enumerate(shapes):
+            n, k, d, ld = self.ns[i], self.ks[i], self.ds[i], self.ld_phi[i]
+            blk = phi[self.phi_off[i]:self.phi_off[i] + n * ld].reshape(n, ld)
+            blk[:, :k] = s.phi
+            mass[self.mass_off[i]:self.mass_off[i] + n] = s.mass
+            evals[self.evals_off[i]:self.evals_off[i] + k] = s.evals
+            feat[self.feat_off[i]:self.feat_off[i] + n * d] = np.asarray(s.feat, dtype=fdt).reshape(-1)
+        return dict(phi=phi, mass=mass, evals=evals, feat=feat)
+
+    def feat_view(self, flat: torch.Tensor, s: int) -> torch.Tensor:
+        o, n, d = self.feat_off[s], self.ns[s], self.ds[s]
+        return flat[o:o + n * d].view(n, d)
+
+
+def host_to_torch(arr: np.ndarray, dtype_name: str = "") -> torch.Tensor:
+    t = torch.from_numpy(arr)
+    if arr.dtype == np.uint16:
+        t = t.view(torch.int16).view(torch.bfloat16)
+    return t
+
+
+class FmapBatch:
+    """A ragged batch of shape pairs bound to flat device buffers.
+
+    pairs: list of (x, y, lam); masks: optional list (per pair) of k x k arrays or None."""
+
+    def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
+                 with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
+                 store_factors_max_k: int = 256):
+        self.layout = layout
+        self.device = torch.device(device)
+        self.precision = precision
+        lay = layout
+        dev = self.device
+        self.phi = torch.zeros(lay.phi_len, dtype=torch.float32, device=dev)
+        self.mass = torch.zeros(lay.mass_len, dtype=torch.float32, device=dev)
+        self.evals = torch.zeros(lay.evals_len, dtype=torch.float32, device=dev)
+        self.feat = torch.zeros(lay.feat_len, dtype=lay.torch_feat_dtype(), device=dev)
+        self.dfeat = torch.zeros_like(self.feat) if with_grad else None
+        self.pairs = [(int(x), int(y), float(lam)) for (x, y, lam) in pairs]
+        self.ks = [lay.ks[x] for (x, _, _) in self.pairs]
+        self.c_off_host = np.concatenate([[0], np.cumsum([k * k for k in self.ks])]).astype(np.int64)
+        self.mask = None
+        if masks is not None and any(m is not None for m in masks):
+            host = np.zeros(int(self.c_off_host[-1]), np.float32)
+            for p, m in enumerate(masks):
+                if m is not None:
+                    host[self.c_off_host[p]:self.c_off_host[p + 1]] = np.asarray(m, np.float32).reshape(-1)
+            self.mask = torch.from_numpy(host).to(dev)
+        self._masks_present = [m is not None for m in masks] if masks is not None else [False] * len(self.pairs)
+
+        L = _lib.lib()
+        opt = _lib.default_options()
+        opt.precision = _lib.FMAP_PREC_BF16 if precision == "bf16" else _lib.FMAP_PREC_FP32
+        opt.ir_steps = ir_steps
+        opt.hi_gram_min_k = hi_gram_min_k
+        opt.store_factors_max_k = store_factors_max_k
+        self.options = opt
+        ctx = ctypes.c_void_p()
+        check(L.fmap_create(ctypes.byref(ctx), self.device.index or 0, ctypes.byref(opt)), "fmap_create")
+        self._ctx = ctx
+        self._batch = None
+        self._build()
+
+    # ------------------------------------------------------------------ setup
+    def _descs(self):
+        lay = self.layout
+        fel = 2 if lay.feat_dtype == "bf16" else 4
+        sd = (_lib.ShapeDesc * max(1, lay.n_shapes))()
+        for s in range(lay.n_shapes):
+            d = sd[s]
+            d.n, d.k, d.d = lay.ns[s], lay.ks[s], lay.ds[s]
+            d.phi = self.phi.data_ptr() + 4 * lay.phi_off[s]
+            d.ld_phi = lay.ld_phi[s]
+            d.mass = self.mass.data_ptr() + 4 * lay.mass_off[s]
+            d.evals = self.evals.data_ptr() + 4 * lay.evals_off[s]
+            d.feat = self.feat.data_ptr() + fel * lay.feat_off[s]
+            d.ld_feat = lay.ds[s]
+            d.dfeat = (self.dfeat.data_ptr() + fel * lay.feat_off[s]) if self.dfeat is not None else None
+        pd = (_lib.PairDesc * max(1, len(self.pairs)))()
+        for p, (x, y, lam) in enumerate(self.pairs):
+            pd[p].shape_x, pd[p].shape_y, pd[p].lam = x, y, lam
+            pd[p].mask = (self.mask.data_ptr() + 4 * int(self.c_off_host[p])) if self._masks_present[p] else None
+        return sd, pd
+
+    def _build(self):
+        L = _lib.lib()
+        sd, pd = self._descs()
+        b = ctypes.c_void_p()
+        check(L.fmap_batch_create(self._ctx, sd, self.layout.n_shapes, pd, len(self.pairs), ctypes.byref(b)),
+              "fmap_batch_create")
+        self._batch = b
+        sz = _lib.Sizes()
+        check(L.fmap_batch_sizes(b, ctypes.byref(sz)), "fmap_batch_sizes")
+        self.sizes = sz
+        a_off = (ctypes.c_int64 * (self.layout.n_shapes + 1))()
+        c_off = (ctypes.c_int64 * (len(self.pairs) + 1))()
+        check(L.fmap_batch_offsets(b, a_off, c_off), "fmap_batch_offsets")
+        self.a_off = np.array(a_off[:], dtype=np.int64)
+        self.c_off = np.array(c_off[:], dtype=np.int64)
+        dev = self.device
+        self.ws = torch.empty(max(256, sz.ws_bwd_bytes), dtype=torch.uint8, device=dev)
+        self.saved = torch.empty(max(256, sz.saved_bytes), dtype=torch.uint8, device=dev) if sz.saved_bytes else None
+        self.A = torch.empty(max(1, sz.a_floats), dtype=torch.float32, device=dev)
+        self.C = torch.empty(max(1, sz.c_floats), dtype=torch.float32, device=dev)
+        self.dA = torch.empty_like(self.A)
+        self.status = torch.zeros(max(1, len(self.pairs)), dtype=torch.int32, device=dev)
+
+    def close(self):
+        L = _lib.lib()
+        if self._batch is not None:
+            L.fmap_batch_destroy(self._batch)
+            self._batch = None
+        if self._ctx is not None:
+            L.fmap_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ data
+    def upload(self, host: dict, non_blocking: bool = False):
+        """Copy flat host arrays (from BatchLayout.pack_host, or pinned torch tensors) to the device."""
+        for name in ("phi", "mass", "evals", "feat"):
+            src = host[name]
+            if isinstance(src, np.ndarray):
+                src = host_to_torch(src)
+            getattr(self, name).copy_(src, non_blocking=non_blocking)
+
+    def a_view(self, flat: torch.Tensor, s: int) -> torch.Tensor:
+        k, d = self.layout.ks[s], self.layout.ds[s]
+        return flat[int(self.a_off[s]):int(self.a_off[s + 1])].view(k, d)
+
+    def c_view(self, flat: torch.Tensor, p: int) -> torch.Tensor:
+        k = self.ks[p]
+        return flat[int(self.c_off[p]):int(self.c_off[p + 1])].view(k, k)
+
+    # ------------------------------------------------------------------ calls
+    def project(self, a_out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        a = self.A if a_out is None else a_out
+        check(_lib.lib().fmap_project(self._batch, _ptr(a), _ptr(self.ws), self.ws.numel(), _stream(self.device)),
+              "fmap_project")
+        return a
+
+    def solve(self, a: Optional[torch.Tensor] = None, c_out: Optional[torch.Tensor] = None,
+              keep_factors: bool = True) -> torch.Tensor:
+        a = self.A if a is None else a
+        c = self.C if c_out is None else c_out
+        saved = self.saved if keep_factors else None
+        check(_lib.lib().fmap_solve(self._batch, _ptr(a), _ptr(c), _ptr(saved), _ptr(self.status), _ptr(self.ws),
+                                    self.ws.numel(), _stream(self.device)), "fmap_solve")
+        return c
+
+    def solve_backward(self, d_c: torch.Tensor, a: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
+                       use_saved: bool = True, d_a: Optional[torch.Tensor] = None, d_mask: Optional[torch.Tensor] = None,
+                       d_lambda: Optional[torch.Tensor] = None):
+        a = self.A if a is None else a
+        c = self.C if c is None else c
+        d_a = self.dA if d_a is None else d_a
+        saved = self.saved if use_saved else None
+        check(_lib.lib().fmap_solve_backward(self._batch, _ptr(d_c), _ptr(a), _ptr(c), _ptr(saved), _ptr(d_a),
+                                             _ptr(d_mask), _ptr(d_lambda), _ptr(self.status), _ptr(self.ws),
+                                             self.ws.numel(), _stream(self.device)), "fmap_solve_backward")
+        return d_a
+
+    def loss_orth(self, c: torch.Tensor, c_gt: torch.Tensor, loss: Optional[torch.Tensor] = None,
+                  d_c: Optional[torch.Tensor] = None):
+        if loss is None:
+            loss = torch.empty(max(1, len(self.pairs)), dtype=torch.float32, device=self.device)
+        if d_c is None:
+            d_c = torch.empty_like(c)
+        check(_lib.lib().fmap_loss_orth(self._batch, _ptr(c), _ptr(c_gt), _ptr(loss), _ptr(d_c), _ptr(self.ws),
+                                        self.ws.numel(), _stream(self.device)), "fmap_loss_orth")
+        return loss, d_c
+
+
+def batch_from_workload(wl, device="cuda:0", with_grad=True, **kw) -> FmapBatch:
+    """Allocate a batch for a synth.Workload and upload its inputs."""
+    lay = BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)
+    masks = [p.mask for p in wl.pairs]
+    b = FmapBatch(lay, [(p.x, p.y, p.lam) for p in wl.pairs], device=device, precision=wl.feat_dtype,
+                  with_grad=with_grad, masks=masks, **kw)
+    b.upload(lay.pack_host(wl.shapes))
+    return b
+
+
+def flat_c(batch: FmapBatch, mats: List[np.ndarray]) -> torch.Tensor:
+    """Pack per-pair k x k matrices into the flat C layout of `batch`."""
+    host = np.zeros(int(batch.c_off[-1]), np.float32)
+    for p, m in enumerate(mats):
+        host[batch.c_off[p]:batch.c_off[p + 1]] = np.asarray(m, np.float32).reshape(-1)
+    return torch.from_numpy(host).to(batch.device)
+
+
+class FmapFunction(torch.autograd.Function):
+    """C = fmap(F) for a bound batch: forward runs fmap_project + fmap_solve, backward
+    runs fmap_solve_backward and returns dL/dF in the batch's flat feature layout."""
+
+    @staticmethod
+    def forward(ctx, feat: torch.Tensor, batch: FmapBatch):
+        if feat.data_ptr() != batch.feat.data_ptr():
+            batch.feat.copy_(feat.reshape(-1))
+        a = batch.project().clone()
+        c = batch.solve(a)
+        batch._gen = getattr(batch, "_gen", 0) + 1
+        ctx.gen = batch._gen
+        ctx.batch = batch
+        c = c.clone()
+        ctx.save_for_backward(a, c)
+        return c
+
+    @staticmethod
+    def backward(ctx, d_c):
+        a, c = ctx.saved_tensors
+        batch = ctx.batch
+        use_saved = getattr(batch, "_gen", 0) == ctx.gen
+        batch.solve_backward(d_c.contiguous(), a, c, use_saved=use_saved)
+        return batch.dfeat.clone(), None

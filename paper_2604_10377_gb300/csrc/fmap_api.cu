@@ -1,0 +1,467 @@
+// Host runtime of the functional-map library: argument validation, the batch
+// plan (offsets, work lists), the device descriptor tables, and the launch
+// sequence of every C ABI entry point declared in include/fmap.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fmap_internal.cuh"
+
+using namespace fmap;
+
+namespace {
+
+thread_local char g_last_cuda_error[256] = "no error";
+
+int32_t cuda_fail(cudaError_t e, const char* where) {
+  std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", where, cudaGetErrorString(e));
+  return FMAP_ERR_CUDA;
+}
+
+constexpr int64_t kAlignFloats = 64;   // 256-byte alignment of workspace regions
+constexpr int64_t kChunkV = 4096;      // vertices per split-K chunk of the projection
+constexpr int kTile = 64;
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// RAII switch of the calling thread's current device.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct Plan {
+  fmap_options opt{};
+  std::vector<ShapeDev> shapes;
+  std::vector<PairDev> pairs;
+  std::vector<int64_t> a_off, c_off, slot_list;
+  std::vector<ProjTile> ptiles;
+  std::vector<BwdTile> btiles;
+  std::vector<int2> systems;
+  std::vector<SolveGroup> groups;
+  int max_k = 0, max_d = 0;
+  int64_t max_kd = 0;
+  int64_t da_int_off = 0;
+  fmap_sizes sizes{};
+};
+
+int32_t validate_options(const fmap_options& o) {
+  if (o.precision != FMAP_PREC_FP32 && o.precision != FMAP_PREC_BF16) return FMAP_ERR_INVALID_ARG;
+  if (o.ir_steps < 0 || o.ir_steps > 3) return FMAP_ERR_INVALID_ARG;
+  if (o.hi_gram_min_k < 1 || o.store_factors_max_k < 0) return FMAP_ERR_INVALID_ARG;
+  return FMAP_OK;
+}
+
+int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_t n_shapes,
+                  const fmap_pair_desc* pairs, int32_t n_pairs, Plan& P) {
+  int32_t rc = validate_options(opt);
+  if (rc) return rc;
+  if (n_shapes < 0 || n_pairs < 0 || n_shapes > 65535 || n_pairs > 65535) return FMAP_ERR_INVALID_ARG;
+  if ((n_shapes > 0 && !shapes) || (n_pairs > 0 && !pairs)) return FMAP_ERR_INVALID_ARG;
+  P.opt = opt;
+  const size_t fsz = opt.precision == FMAP_PREC_BF16 ? 2 : 4;
+
+  P.shapes.resize(n_shapes);
+  P.a_off.assign(n_shapes + 1, 0);
+  for (int s = 0; s < n_shapes; ++s) {
+    const fmap_shape_desc& d = shapes[s];
+    if (!d.phi || !d.mass || !d.feat) return FMAP_ERR_INVALID_ARG;
+    if (d.n < 1 || d.k < 1 || d.d < 1) return FMAP_ERR_INVALID_ARG;
+    if (d.k > kMaxK || d.d > kMaxD || d.d % 16 != 0) return FMAP_ERR_UNSUPPORTED;
+    if (d.ld_phi < d.k || d.ld_feat < d.d) return FMAP_ERR_INVALID_ARG;
+    if (d.ld_phi % 4 != 0 || d.ld_feat % 8 != 0) return FMAP_ERR_UNSUPPORTED;
+    if (!aligned(d.phi, 16) || !aligned(d.feat, 16) || !aligned(d.mass, 4)) return FMAP_ERR_UNSUPPORTED;
+    if (d.dfeat && !aligned(d.dfeat, 16)) return FMAP_ERR_UNSUPPORTED;
+    if (d.evals && !aligned(d.evals, 4)) return FMAP_ERR_UNSUPPORTED;
+    ShapeDev& sd = P.shapes[s];
+    std::memset(&sd, 0, sizeof(sd));
+    sd.n = d.n; sd.k = d.k; sd.d = d.d;
+    sd.phi = d.phi; sd.ld_phi = d.ld_phi; sd.mass = d.mass; sd.evals = d.evals;
+    sd.feat = d.feat; sd.ld_feat = d.ld_feat; sd.dfeat = d.dfeat;
+    sd.a_off = P.a_off[s];
+    sd.nchunk = (int32_t)((d.n + kChunkV - 1) / kChunkV);
+    P.a_off[s + 1] = P.a_off[s] + (int64_t)d.k * d.d;
+    P.max_k = std::max(P.max_k, d.k);
+    P.max_d = std::max(P.max_d, d.d);
+    P.max_kd = std::max(P.max_kd, (int64_t)d.k * d.d);
+  }
+  (void)fsz;
+
+  P.pairs.resize(n_pairs);
+  P.c_off.assign(n_pairs + 1, 0);
+  for (int p = 0; p < n_pairs; ++p) {
+    const fmap_pair_desc& q = pairs[p];
+    if (q.shape_x < 0 || q.shape_x >= n_shapes || q.shape_y < 0 || q.shape_y >= n_shapes) return FMAP_ERR_INVALID_ARG;
+    const fmap_shape_desc& sx = shapes[q.shape_x];
+    const fmap_shape_desc& sy = shapes[q.shape_y];
+    if (sx.k != sy.k || sx.d != sy.d) return FMAP_ERR_INVALID_ARG;
+    if (!(q.lambda >= 0.f) || !std::isfinite(q.lambda)) return FMAP_ERR_INVALID_ARG;
+    if (!q.mask && (!sx.evals || !sy.evals)) return FMAP_ERR_INVALID_ARG;
+    if (q.mask && !aligned(q.mask, 4)) return FMAP_ERR_UNSUPPORTED;
+    PairDev& pd = P.pairs[p];
+    std::memset(&pd, 0, sizeof(pd));
+    pd.x = q.shape_x; pd.y = q.shape_y; pd.k = sx.k; pd.d = sx.d;
+    pd.lam = q.lambda; pd.mask = q.mask;
+    pd.hi_gram = sx.k >= opt.hi_gram_min_k ? 1 : 0;
+    pd.c_off = P.c_off[p];
+    P.c_off[p + 1] = P.c_off[p] + (int64_t)sx.k * sx.k;
+  }
+
+  // ---- workspace layout (floats, 256-byte aligned regions)
+  int64_t cur = 0;
+  for (auto& sd : P.shapes) {
+    sd.part_off = cur;
+    cur = align_up(cur + (int64_t)sd.nchunk * sd.k * sd.d, kAlignFloats);
+  }
+  for (auto& pd : P.pairs) {
+    const int64_t kk = (int64_t)pd.k * pd.k;
+    pd.g_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    pd.r_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    pd.e_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    if (pd.hi_gram) {
+      pd.g64_off = cur / 2;
+      cur = align_up(cur + 2 * kk, kAlignFloats);
+    } else {
+      pd.g64_off = -1;
+    }
+  }
+  const int64_t ws_fwd = cur;
+  for (auto& pd : P.pairs) {
+    const int64_t kk = (int64_t)pd.k * pd.k, kd = (int64_t)pd.k * pd.d;
+    pd.gam_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    pd.w_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    pd.sx_off = cur; cur = align_up(cur + kd, kAlignFloats);
+    pd.sy_off = cur; cur = align_up(cur + kd, kAlignFloats);
+  }
+  P.da_int_off = cur;
+  cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
+  const int64_t ws_bwd = std::max(cur, ws_fwd);
+
+  // ---- saved factors
+  int64_t fac = 0;
+  for (auto& pd : P.pairs) {
+    if (pd.k <= opt.store_factors_max_k) {
+      pd.fac_off = fac;
+      fac = align_up(fac + (int64_t)pd.k * tri(pd.k), kAlignFloats);
+    } else {
+      pd.fac_off = -1;
+    }
+  }
+
+  // ---- dA contributions per shape, in pair order
+  for (int s = 0; s < n_shapes; ++s) {
+    P.shapes[s].slot_beg = (int32_t)P.slot_list.size();
+    for (const auto& pd : P.pairs) {
+      if (pd.x == s) P.slot_list.push_back(pd.sx_off);
+      if (pd.y == s) P.slot_list.push_back(pd.sy_off);
+    }
+    P.shapes[s].slot_end = (int32_t)P.slot_list.size();
+  }
+
+  // ---- projection work lists
+  for (int s = 0; s < n_shapes; ++s) {
+    const ShapeDev& sd = P.shapes[s];
+    for (int c = 0; c < sd.nchunk; ++c)
+      for (int kk0 = 0; kk0 < sd.k; kk0 += kTile)
+        for (int f0 = 0; f0 < sd.d; f0 += kTile) {
+          ProjTile t;
+          t.shape = s; t.chunk = c; t.kk0 = kk0; t.f0 = f0;
+          t.v0 = (int64_t)c * kChunkV;
+          t.v1 = std::min<int64_t>(sd.n, t.v0 + kChunkV);
+          P.ptiles.push_back(t);
+        }
+    if (sd.dfeat)
+      for (int64_t v0 = 0; v0 < sd.n; v0 += kTile)
+        for (int f0 = 0; f0 < sd.d; f0 += kTile) {
+          BwdTile t;
+          t.shape = s; t.f0 = f0; t.v0 = v0;
+          P.btiles.push_back(t);
+        }
+  }
+
+  // ---- row systems, grouped by block size, largest k first
+  const int bounds[3] = {64, 128, 256};
+  for (int gi = 0; gi < 3; ++gi) {
+    SolveGroup g{};
+    g.first = (int32_t)P.systems.size();
+    g.threads = bounds[gi];
+    std::vector<int> members;
+    for (int p = 0; p < n_pairs; ++p) {
+      const int k = P.pairs[p].k;
+      const int lo = gi == 0 ? 0 : bounds[gi - 1];
+      if (k > lo && k <= bounds[gi]) members.push_back(p);
+    }
+    std::stable_sort(members.begin(), members.end(), [&](int a, int b) { return P.pairs[a].k > P.pairs[b].k; });
+    for (int p : members) {
+      g.kmax = std::max(g.kmax, P.pairs[p].k);
+      for (int i = 0; i < P.pairs[p].k; ++i) P.systems.push_back(make_int2(p, i));
+    }
+    g.count = (int32_t)P.systems.size() - g.first;
+    if (g.count > 0) P.groups.push_back(g);
+  }
+
+  P.sizes.a_floats = P.a_off[n_shapes];
+  P.sizes.c_floats = P.c_off[n_pairs];
+  P.sizes.ws_bytes = ws_fwd * 4;
+  P.sizes.ws_bwd_bytes = ws_bwd * 4;
+  P.sizes.saved_bytes = fac * 4;
+  P.sizes.n_shapes = n_shapes;
+  P.sizes.n_pairs = n_pairs;
+  return FMAP_OK;
+}
+
+}  // namespace
+
+struct fmap_ctx {
+  int device;
+  fmap_options opt;
+};
+
+struct fmap_batch {
+  fmap_ctx* ctx;
+  Plan plan;
+  void* dev_mem = nullptr;
+  BatchDev dev{};
+  const ProjTile* d_ptiles = nullptr;
+  const BwdTile* d_btiles = nullptr;
+  const int2* d_systems = nullptr;
+};
+
+extern "C" {
+
+const char* fmap_version(void) { return "fmap-gb300 0.1 (sm_103a)"; }
+
+const char* fmap_error_string(int32_t code) {
+  switch (code & 0xff) {
+    case FMAP_OK: return "ok";
+    case FMAP_ERR_INVALID_ARG: return "invalid argument";
+    case FMAP_ERR_UNSUPPORTED: return "unsupported size or alignment";
+    case FMAP_ERR_CUDA: return "CUDA error";
+    case FMAP_ERR_NOT_SPD: return "row system not positive definite";
+    case FMAP_ERR_NONFINITE: return "non-finite result";
+    case FMAP_ERR_TIMEOUT: return "device-side wait timed out";
+    case FMAP_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    default: return "unknown error";
+  }
+}
+
+const char* fmap_last_cuda_error(void) { return g_last_cuda_error; }
+
+int32_t fmap_default_options(fmap_options* opt) {
+  if (!opt) return FMAP_ERR_INVALID_ARG;
+  opt->precision = FMAP_PREC_FP32;
+  opt->ir_steps = 1;
+  opt->hi_gram_min_k = 200;
+  opt->store_factors_max_k = 256;
+  return FMAP_OK;
+}
+
+int32_t fmap_create(fmap_ctx** out, int32_t device, const fmap_options* opt) {
+  if (!out) return FMAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (device < 0) return FMAP_ERR_INVALID_ARG;
+  fmap_options o;
+  if (opt) o = *opt; else fmap_default_options(&o);
+  int32_t rc = validate_options(o);
+  if (rc) return rc;
+  fmap_ctx* c = new (std::nothrow) fmap_ctx;
+  if (!c) return FMAP_ERR_INVALID_ARG;
+  c->device = device;
+  c->opt = o;
+  *out = c;
+  return FMAP_OK;
+}
+
+int32_t fmap_destroy(fmap_ctx* ctx) {
+  delete ctx;
+  return FMAP_OK;
+}
+
+int32_t fmap_plan_sizes(const fmap_options* opt, const fmap_shape_desc* shapes, int32_t n_shapes,
+                        const fmap_pair_desc* pairs, int32_t n_pairs, fmap_sizes* out) {
+  if (!out) return FMAP_ERR_INVALID_ARG;
+  fmap_options o;
+  if (opt) o = *opt; else fmap_default_options(&o);
+  Plan P;
+  int32_t rc = make_plan(o, shapes, n_shapes, pairs, n_pairs, P);
+  if (rc) return rc;
+  *out = P.sizes;
+  return FMAP_OK;
+}
+
+int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t n_shapes,
+                          const fmap_pair_desc* pairs, int32_t n_pairs, fmap_batch** out) {
+  if (!ctx || !out) return FMAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  fmap_batch* b = new (std::nothrow) fmap_batch;
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  b->ctx = ctx;
+  int32_t rc = make_plan(ctx->opt, shapes, n_shapes, pairs, n_pairs, b->plan);
+  if (rc) { delete b; return rc; }
+  Plan& P = b->plan;
+  DeviceGuard dg(ctx->device);
+  if (!dg.ok) { delete b; return cuda_fail(cudaErrorInvalidDevice, "cudaSetDevice"); }
+  cudaError_t e = solve_set_smem_limits();
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaFuncSetAttribute"); }
+
+  // one allocation for every table
+  auto bytes_of = [](size_t n, size_t sz) { return (int64_t)align_up((int64_t)(n * sz), 256); };
+  const int64_t o_sh = 0;
+  const int64_t o_pr = o_sh + bytes_of(P.shapes.size(), sizeof(ShapeDev));
+  const int64_t o_sl = o_pr + bytes_of(P.pairs.size(), sizeof(PairDev));
+  const int64_t o_pt = o_sl + bytes_of(P.slot_list.size(), sizeof(int64_t));
+  const int64_t o_bt = o_pt + bytes_of(P.ptiles.size(), sizeof(ProjTile));
+  const int64_t o_sy = o_bt + bytes_of(P.btiles.size(), sizeof(BwdTile));
+  const int64_t total = o_sy + bytes_of(P.systems.size(), sizeof(int2)) + 256;
+  e = cudaMalloc(&b->dev_mem, (size_t)total);
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch tables)"); }
+  char* base = static_cast<char*>(b->dev_mem);
+  std::vector<char> host((size_t)total, 0);
+  auto put = [&](int64_t off, const void* src, size_t n) { if (n) std::memcpy(host.data() + off, src, n); };
+  put(o_sh, P.shapes.data(), P.shapes.size() * sizeof(ShapeDev));
+  put(o_pr, P.pairs.data(), P.pairs.size() * sizeof(PairDev));
+  put(o_sl, P.slot_list.data(), P.slot_list.size() * sizeof(int64_t));
+  put(o_pt, P.ptiles.data(), P.ptiles.size() * sizeof(ProjTile));
+  put(o_bt, P.btiles.data(), P.btiles.size() * sizeof(BwdTile));
+  put(o_sy, P.systems.data(), P.systems.size() * sizeof(int2));
+  e = cudaMemcpy(b->dev_mem, host.data(), (size_t)total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaMemcpy(batch tables)"); }
+  b->dev.shapes = reinterpret_cast<const ShapeDev*>(base + o_sh);
+  b->dev.pairs = reinterpret_cast<const PairDev*>(base + o_pr);
+  b->dev.slot_list = reinterpret_cast<const int64_t*>(base + o_sl);
+  b->dev.n_shapes = n_shapes;
+  b->dev.n_pairs = n_pairs;
+  b->dev.feat_bf16 = ctx->opt.precision == FMAP_PREC_BF16 ? 1 : 0;
+  b->dev.ir_steps = ctx->opt.ir_steps;
+  b->d_ptiles = reinterpret_cast<const ProjTile*>(base + o_pt);
+  b->d_btiles = reinterpret_cast<const BwdTile*>(base + o_bt);
+  b->d_systems = reinterpret_cast<const int2*>(base + o_sy);
+  *out = b;
+  return FMAP_OK;
+}
+
+int32_t fmap_batch_destroy(fmap_batch* b) {
+  if (!b) return FMAP_OK;
+  if (b->dev_mem) {
+    DeviceGuard dg(b->ctx->device);
+    cudaFree(b->dev_mem);
+  }
+  delete b;
+  return FMAP_OK;
+}
+
+int32_t fmap_batch_sizes(const fmap_batch* b, fmap_sizes* out) {
+  if (!b || !out) return FMAP_ERR_INVALID_ARG;
+  *out = b->plan.sizes;
+  return FMAP_OK;
+}
+
+int32_t fmap_batch_offsets(const fmap_batch* b, int64_t* a_offsets, int64_t* c_offsets) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (a_offsets) std::memcpy(a_offsets, b->plan.a_off.data(), b->plan.a_off.size() * sizeof(int64_t));
+  if (c_offsets) std::memcpy(c_offsets, b->plan.c_off.data(), b->plan.c_off.size() * sizeof(int64_t));
+  return FMAP_OK;
+}
+
+static int32_t check_ws(void* ws, size_t ws_bytes, int64_t need) {
+  if (need == 0) return FMAP_OK;
+  if (!ws || !aligned(ws, 256) || (int64_t)ws_bytes < need) return FMAP_ERR_WORKSPACE;
+  return FMAP_OK;
+}
+
+int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_shapes == 0) return FMAP_OK;
+  if (!a_out) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bytes);
+  if (rc) return rc;
+  DeviceGuard dg(b->ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* w = static_cast<float*>(ws);
+  cudaError_t e = launch_project_simt(b->dev, b->d_ptiles, (int)b->plan.ptiles.size(), w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "project");
+  e = launch_project_reduce(b->dev, (int)b->plan.max_kd, a_out, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "project_reduce");
+  return FMAP_OK;
+}
+
+int32_t fmap_solve(fmap_batch* b, const float* a, float* c_out, void* saved, int32_t* status, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
+  if (!a || !c_out) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bytes);
+  if (rc) return rc;
+  if (saved && !aligned(saved, 256)) return FMAP_ERR_WORKSPACE;
+  DeviceGuard dg(b->ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* w = static_cast<float*>(ws);
+  cudaError_t e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "status_clear");
+  e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gram");
+  for (const auto& g : b->plan.groups) {
+    e = launch_solve(b->dev, g, b->d_systems, kSolveForward, nullptr, c_out, static_cast<float*>(saved), status, w, st);
+    if (e != cudaSuccess) return cuda_fail(e, "solve");
+  }
+  return FMAP_OK;
+}
+
+int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved,
+                            float* d_a, float* d_mask, float* d_lambda, int32_t* status, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
+  if (!d_c || !a || !c) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bwd_bytes);
+  if (rc) return rc;
+  if (saved && !aligned(saved, 256)) return FMAP_ERR_WORKSPACE;
+  DeviceGuard dg(b->ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* w = static_cast<float*>(ws);
+  cudaError_t e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "status_clear");
+  e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gram");
+  for (const auto& g : b->plan.groups) {
+    e = launch_solve(b->dev, g, b->d_systems, kSolveAdjoint, d_c, nullptr,
+                     const_cast<float*>(static_cast<const float*>(saved)), status, w, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint solve");
+  }
+  e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint gemms");
+  float* da = d_a ? d_a : w + b->plan.da_int_off;
+  e = launch_gather_da(b->dev, (int)b->plan.max_kd, da, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gather dA");
+  e = launch_project_bwd_simt(b->dev, b->d_btiles, (int)b->plan.btiles.size(), da, st);
+  if (e != cudaSuccess) return cuda_fail(e, "project backward");
+  return FMAP_OK;
+}
+
+int32_t fmap_loss_orth(fmap_batch* b, const float* c, const float* c_gt, float* loss, float* d_c, void* ws,
+                       size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
+  if (!c || !c_gt || (!loss && !d_c)) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bytes);
+  if (rc) return rc;
+  DeviceGuard dg(b->ctx->device);
+  cudaError_t e = launch_loss_orth(b->dev, c, c_gt, loss, d_c, static_cast<float*>(ws), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "loss");
+  return FMAP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations shared by the functional-map CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/fmap.h"
+
+namespace fmap {
+
+constexpr int kMaxK = 256;
+constexpr int kMaxD = 4096;
+
+// Device copy of a shape descriptor plus the offsets the library assigns to it.
+struct ShapeDev {
+  int64_t n;
+  int32_t k, d;
+  const float* phi;
+  int64_t ld_phi;
+  const float* mass;
+  const float* evals;
+  const void* feat;
+  int64_t ld_feat;
+  void* dfeat;
+  int64_t a_off;       // float offset of A_s in the flat A buffer
+  int64_t part_off;    // float offset of this shape's split-K partials in the workspace
+  int32_t nchunk;      // number of vertex chunks (split-K slices)
+  int32_t slot_beg;    // [slot_beg, slot_end): entries of slot_list holding dA contributions
+  int32_t slot_end;
+  int32_t pad_;
+};
+
+// Device copy of a pair descriptor plus workspace offsets.
+struct PairDev {
+  int32_t x, y;
+  int32_t k, d;
+  float lam;
+  int32_t hi_gram;     // 1: Gram matrix accumulated in FP64
+  const float* mask;   // k x k or nullptr (use eigenvalues)
+  int64_t c_off;       // float offset of C_p / dC_p in the flat k x k buffers
+  int64_t g_off;       // float offset (workspace) of G = A_x A_x^T  (k x k)
+  int64_t r_off;       // float offset (workspace) of R = A_y A_x^T  (k x k)
+  int64_t g64_off;     // double offset (workspace) of the FP64 Gram, or -1
+  int64_t gam_off;     // float offset (workspace) of Gamma (k x k)
+  int64_t w_off;       // float offset (workspace) of W = Gamma^T C + C^T Gamma (k x k)
+  int64_t e_off;       // float offset (workspace) of E = C C^T - I (k x k)
+  int64_t sx_off;      // float offset (workspace) of this pair's dA_x contribution (k x d)
+  int64_t sy_off;      // float offset (workspace) of this pair's dA_y contribution (k x d)
+  int64_t fac_off;     // float offset of saved factors (k packed triangles), or -1
+};
+
+// Work item of the projection kernels: a vertex range of one shape and an
+// output tile of A (rows kk0.., cols f0..).
+struct ProjTile {
+  int32_t shape;
+  int32_t chunk;
+  int32_t kk0;
+  int32_t f0;
+  int64_t v0, v1;
+};
+
+// Work item of the backward projection: a vertex tile and a feature tile of dF.
+struct BwdTile {
+  int32_t shape;
+  int32_t f0;
+  int64_t v0;
+};
+
+struct BatchDev {
+  const ShapeDev* shapes;
+  const PairDev* pairs;
+  const int64_t* slot_list;     // workspace float offsets of dA contributions, grouped per shape
+  int32_t n_shapes, n_pairs;
+  int32_t feat_bf16;
+  int32_t ir_steps;
+};
+
+__host__ __device__ inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
+
+// ---- launchers (each enqueues on `st`; return cudaError_t of the launch) ----
+cudaError_t launch_project_simt(const BatchDev& b, const ProjTile* tiles, int ntiles, float* ws,
+                                cudaStream_t st);
+cudaError_t launch_project_reduce(const BatchDev& b, int max_kd, float* a_out, const float* ws,
+                                  cudaStream_t st);
+cudaError_t launch_gram(const BatchDev& b, int max_k, const float* a, float* ws, cudaStream_t st);
+
+struct SolveGroup {
+  int32_t first;     // index into the system list
+  int32_t count;     // systems in this group
+  int32_t kmax;      // largest k in the group
+  int32_t threads;
+};
+
+enum SolveMode { kSolveForward = 0, kSolveAdjoint = 1 };
+
+cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode,
+                         const float* rhs_flat, float* out_flat, float* saved_rw, int32_t* status,
+                         float* ws, cudaStream_t st);
+cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
+                                 float* d_mask, float* d_lambda, float* ws, cudaStream_t st);
+cudaError_t launch_gather_da(const BatchDev& b, int max_kd, float* d_a, const float* ws, cudaStream_t st);
+cudaError_t launch_project_bwd_simt(const BatchDev& b, const BwdTile* tiles, int ntiles, const float* d_a,
+                                    cudaStream_t st);
+cudaError_t launch_loss_orth(const BatchDev& b, const float* c, const float* c_gt, float* loss, float* d_c,
+                             float* ws, cudaStream_t st);
+cudaError_t launch_status_clear(int32_t* status, int n, cudaStream_t st);
+cudaError_t solve_set_smem_limits();
+
+}  // namespace fmap

@@ -17,3 +17,16 @@ def rel_fro(x, ref):
     ref = np.asarray(ref, dtype=np.float64)
     den = np.linalg.norm(ref)
     return float(np.linalg.norm(x - ref) / (den if den > 0 else 1.0))
+
+
+def gpu_forward(wl, **kw):
+    """Run fmap_project + fmap_solve on the GPU; returns (batch, A list, C list, status)."""
+    import torch
+    from paper_2604_10377_gb300 import api
+    b = api.batch_from_workload(wl, **kw)
+    a = b.project()
+    c = b.solve(a)
+    torch.cuda.synchronize()
+    a_list = [b.a_view(a, s).cpu().numpy().astype(np.float64) for s in range(len(wl.shapes))]
+    c_list = [b.c_view(c, p).cpu().numpy().astype(np.float64) for p in range(len(wl.pairs))]
+    return b, a_list, c_list, b.status[:len(wl.pairs)].cpu().numpy()

@@ -1,0 +1,162 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, exports every
+symbol include/*.h declares, and validates / plans batches on the host."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_10377_gb300 import _lib, build
+    build.build()
+    return _lib.lib()
+
+
+def declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names += re.findall(r"^FMAP_API\s+[\w\s\*]+?\b(fmap_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ("fmap_project", "fmap_solve", "fmap_solve_backward", "fmap_batch_create", "fmap_create"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_2604_10377_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_version_and_errors(lib):
+    from paper_2604_10377_gb300 import _lib
+    assert b"sm_103a" in lib.fmap_version()
+    assert _lib.error_string(_lib.FMAP_ERR_NOT_SPD) == "row system not positive definite"
+    assert _lib.error_string(_lib.FMAP_ERR_NOT_SPD | (7 << 8)) == "row system not positive definite"
+
+
+def _descs(specs, pairs):
+    from paper_2604_10377_gb300 import _lib
+    sd = (_lib.ShapeDesc * max(1, len(specs)))()
+    for i, sp in enumerate(specs):
+        n, k, d = sp["n"], sp["k"], sp["d"]
+        sd[i].n, sd[i].k, sd[i].d = n, k, d
+        sd[i].phi = sp.get("phi", 0x10000)
+        sd[i].ld_phi = sp.get("ld_phi", (k + 3) // 4 * 4)
+        sd[i].mass = 0x20000
+        sd[i].evals = sp.get("evals", 0x30000)
+        sd[i].feat = sp.get("feat", 0x40000)
+        sd[i].ld_feat = sp.get("ld_feat", d)
+        sd[i].dfeat = None
+    pd = (_lib.PairDesc * max(1, len(pairs)))()
+    for i, (x, y, lam) in enumerate(pairs):
+        pd[i].shape_x, pd[i].shape_y, pd[i].lam = x, y, lam
+        pd[i].mask = None
+    return sd, pd
+
+
+def _plan(lib, specs, pairs, opt=None):
+    from paper_2604_10377_gb300 import _lib
+    sd, pd = _descs(specs, pairs)
+    sz = _lib.Sizes()
+    rc = lib.fmap_plan_sizes(None if opt is None else ctypes.byref(opt), sd, len(specs), pd, len(pairs),
+                             ctypes.byref(sz))
+    return rc, sz
+
+
+def test_plan_sizes(lib):
+    specs = [dict(n=5000, k=30, d=128), dict(n=7000, k=30, d=128), dict(n=100, k=200, d=512), dict(n=90, k=200, d=512)]
+    rc, sz = _plan(lib, specs, [(0, 1, 1e-3), (2, 3, 1e-3), (1, 0, 0.0)])
+    assert rc == 0
+    assert sz.a_floats == 2 * 30 * 128 + 2 * 200 * 512
+    assert sz.c_floats == 30 * 30 * 2 + 200 * 200
+    assert sz.n_pairs == 3 and sz.n_shapes == 4
+    assert sz.ws_bwd_bytes >= sz.ws_bytes > 0
+    assert sz.saved_bytes >= 4 * (2 * 30 * 30 * 31 // 2 + 200 * 200 * 201 // 2)
+
+
+def test_plan_sizes_empty(lib):
+    rc, sz = _plan(lib, [dict(n=10, k=4, d=16)], [])
+    assert rc == 0 and sz.c_floats == 0 and sz.n_pairs == 0
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(k=0), 1), (dict(k=257), 2), (dict(d=24), 2), (dict(n=0), 1),
+    (dict(ld_phi=30), 1), (dict(ld_phi=34), 2), (dict(ld_feat=132), 2),
+    (dict(phi=0x10004), 2), (dict(feat=0x40008), 2),
+])
+def test_plan_rejects_bad_shapes(lib, bad, code):
+    good = dict(n=5000, k=32, d=128)
+    spec = dict(good, **bad)
+    rc, _ = _plan(lib, [spec, good], [(0, 1, 1e-3)])
+    assert rc == code, (bad, rc)
+
+
+@pytest.mark.parametrize("pair,code", [((0, 2, 1e-3), 1), ((0, 1, -1.0), 1), ((0, 1, float("nan")), 1),
+                                       ((-1, 1, 1e-3), 1)])
+def test_plan_rejects_bad_pairs(lib, pair, code):
+    specs = [dict(n=100, k=8, d=16), dict(n=100, k=8, d=16)]
+    rc, _ = _plan(lib, specs, [pair])
+    assert rc == code
+
+
+def test_plan_rejects_k_mismatch_and_missing_evals(lib):
+    rc, _ = _plan(lib, [dict(n=100, k=8, d=16), dict(n=100, k=9, d=16)], [(0, 1, 1e-3)])
+    assert rc == 1
+    rc, _ = _plan(lib, [dict(n=100, k=8, d=16, evals=None), dict(n=100, k=8, d=16)], [(0, 1, 1e-3)])
+    assert rc == 1
+
+
+def test_options_validation(lib):
+    from paper_2604_10377_gb300 import _lib
+    o = _lib.default_options()
+    assert (o.precision, o.ir_steps, o.hi_gram_min_k, o.store_factors_max_k) == (0, 1, 200, 256)
+    ctx = ctypes.c_void_p()
+    assert lib.fmap_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == 0
+    assert lib.fmap_destroy(ctx) == 0
+    o.ir_steps = 9
+    assert lib.fmap_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == 1
+    o.ir_steps = 1
+    o.precision = 5
+    assert lib.fmap_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == 1
+
+
+def test_store_factor_threshold(lib):
+    from paper_2604_10377_gb300 import _lib
+    o = _lib.default_options()
+    o.store_factors_max_k = 100
+    specs = [dict(n=300, k=30, d=64), dict(n=300, k=30, d=64), dict(n=300, k=200, d=512), dict(n=300, k=200, d=512)]
+    rc, sz = _plan(lib, specs, [(0, 1, 1e-3), (2, 3, 1e-3)], o)
+    assert rc == 0
+    assert sz.saved_bytes == 4 * ((30 * 30 * 31 // 2 + 63) // 64 * 64)
+
+
+def test_calls_without_batch_are_rejected(lib):
+    assert lib.fmap_project(None, None, None, 0, None) == 1
+    assert lib.fmap_solve(None, None, None, None, None, None, 0, None) == 1
+
+
+# ------------------------------------------------------------ independence of oracle and CUDA path
+def test_oracle_and_cuda_path_share_no_code():
+    pkg = os.path.join(ROOT, "paper_2604_10377_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            text = open(path, errors="ignore").read()
+            assert not re.search(r"\boracle\b\s*(import|\.)|from\s+oracle|import\s+oracle|fmap_oracle", text), path
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        text = open(path).read()
+        assert "paper_2604_10377_gb300" not in text and "libfmap" not in text, path

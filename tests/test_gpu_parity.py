@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the GPU.
+
+Tolerances (relative Frobenius error per shape / pair):
+  FP32 features: A, C within 1e-5; dL/dF within 1e-4.
+  BF16 features: A, C within 3e-3; dL/dF (stored in BF16) within 3e-3.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import fmap_oracle as orc
+from paper_2604_10377_gb300 import synth
+from _bridge import gpu_forward, oracle_inputs, rel_fro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16": 3e-3}
+GTOL = {"fp32": 1e-4, "bf16": 3e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_built():
+    import os
+    from paper_2604_10377_gb300 import _lib, build
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    _lib.lib()
+
+
+def _check_forward(wl, tol=None, **kw):
+    tol = tol or TOL[wl.feat_dtype]
+    b, a_gpu, c_gpu, status = gpu_forward(wl, **kw)
+    shapes, pairs = oracle_inputs(wl)
+    ref = orc.forward_batch(shapes, pairs)
+    assert np.all(status == 0), status
+    ea = [rel_fro(x, r) for x, r in zip(a_gpu, ref["A"])]
+    ec = [rel_fro(x, r) for x, r in zip(c_gpu, ref["C"])]
+    assert max(ea) <= tol, ea
+    assert max(ec) <= tol, ec
+    return b, ea, ec
+
+
+def _shape(rng, n, k, d, feat_dtype="fp32", orthonormal=False):
+    phi = rng.standard_normal((n, k))
+    mass = rng.uniform(0.5, 1.5, n) / n
+    if orthonormal:
+        phi = synth.m_orthonormalize(phi, mass)
+    else:
+        phi = phi / np.sqrt(n * mass.mean())
+    feat = rng.standard_normal((n, d), dtype=np.float32)
+    if feat_dtype == "bf16":
+        feat = synth.f32_to_bf16_bits(feat)
+    return synth.Shape(n=n, k=k, d=d, phi=phi.astype(np.float32), mass=mass.astype(np.float32),
+                       evals=np.sort(rng.uniform(0, 100, k)).astype(np.float32), feat=feat, feat_dtype=feat_dtype)
+
+
+# ------------------------------------------------------------------ forward
+@pytest.mark.parametrize("feat_dtype", ["fp32", "bf16"])
+def test_small_ragged_batch(feat_dtype):
+    """Several tiles and ragged tails in every dimension: n across chunk edges, k not a
+    multiple of the tile, mixed k in one batch."""
+    wl = synth.make_small(1, 6, (300, 9000), [3, 17, 30, 50, 64, 100], 256, feat_dtype=feat_dtype)
+    _check_forward(wl)
+
+
+def test_edge_sizes():
+    """n = 1 and n just past a chunk edge, k = 1 and k = 256, d = 16 and a large d
+    (d >= 2k throughout, so that the FP32 solve is well conditioned)."""
+    rng = np.random.default_rng(5)
+    shapes = [
+        _shape(rng, 1, 1, 16), _shape(rng, 1, 1, 16),
+        _shape(rng, 4097, 256, 512), _shape(rng, 4095, 256, 512),
+        _shape(rng, 129, 5, 1040), _shape(rng, 64, 5, 1040),
+        _shape(rng, 8193, 8, 16), _shape(rng, 333, 8, 16),
+    ]
+    pairs = [synth.Pair(x=0, y=1, lam=0.5), synth.Pair(x=2, y=3, lam=1e-3),
+             synth.Pair(x=4, y=5, lam=1e-2), synth.Pair(x=6, y=7, lam=1e-1)]
+    wl = synth.Workload("edges", shapes, pairs, "fp32")
+    _check_forward(wl)
+
+
+def test_identity_case_gives_identity():
+    wl = synth.make_small(2, 3, (2000, 6000), [30, 50, 100], 256, identity=True)
+    b, a_gpu, c_gpu, status = gpu_forward(wl)
+    for c in c_gpu:
+        assert rel_fro(c, np.eye(c.shape[0])) < 1e-5
+
+
+def test_explicit_mask():
+    wl = synth.make_small(3, 4, (500, 3000), [8, 40], 128, with_mask=True)
+    _check_forward(wl)
+
+
+def test_shared_shape_and_self_pair():
+    """A shape used by several pairs, and a pair mapping a shape onto itself."""
+    rng = np.random.default_rng(11)
+    shapes = [_shape(rng, 700, 20, 64, orthonormal=True) for _ in range(3)]
+    pairs = [synth.Pair(0, 1, 1e-3), synth.Pair(1, 2, 1e-2), synth.Pair(2, 0, 1e-1), synth.Pair(1, 1, 1e-3)]
+    _check_forward(synth.Workload("shared", shapes, pairs, "fp32"))
+
+
+def test_not_spd_reports_row_and_nan():
+    """A negative mask entry makes row system 3 of pair 1 indefinite: status NOT_SPD | 3 << 8,
+    its row of C is NaN, and the other pair is unaffected."""
+    wl = synth.make_small(4, 2, (400, 800), [10], 32, with_mask=True)
+    wl.pairs[1].mask[3, 4] = -1e9
+    b, a_gpu, c_gpu, status = gpu_forward(wl)
+    assert status[0] == 0
+    assert status[1] == (4 | (3 << 8)), hex(int(status[1]))
+    assert np.all(np.isnan(c_gpu[1][3]))
+    assert np.all(np.isfinite(np.delete(c_gpu[1], 3, axis=0)))
+    shapes, pairs = oracle_inputs(wl)
+    ref = orc.forward_batch(shapes, pairs[:1])
+    assert rel_fro(c_gpu[0], ref["C"][0]) < 1e-5
+
+
+def test_empty_batch():
+    from paper_2604_10377_gb300 import api
+    lay = api.BatchLayout([100], [10], [16], "fp32")
+    b = api.FmapBatch(lay, [], with_grad=True)
+    b.project(); b.solve(); b.solve_backward(torch.zeros(1, device="cuda"))
+    torch.cuda.synchronize()
+
+
+def test_ir_steps_and_hi_gram():
+    """FP64 Gram (hi_gram_min_k low) and 0..2 refinement steps all meet the FP32 tolerance."""
+    wl = synth.make_small(6, 3, (1000, 4000), [20, 60, 120], 256)
+    for ir in (0, 1, 2):
+        _check_forward(wl, ir_steps=ir, hi_gram_min_k=50)
+
+
+def test_bitwise_reproducible():
+    wl = synth.make_small(7, 3, (3000, 20000), [30, 64, 100], 64)
+    from paper_2604_10377_gb300 import api
+    b = api.batch_from_workload(wl)
+    a1 = b.project().clone(); c1 = b.solve(a1).clone()
+    a2 = b.project().clone(); c2 = b.solve(a2).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2) and torch.equal(c1, c2)
+
+
+# ------------------------------------------------------------------ backward
+def _gpu_backward(wl, use_saved=True, **kw):
+    from paper_2604_10377_gb300 import api
+    b = api.batch_from_workload(wl, with_grad=True, **kw)
+    a = b.project()
+    c = b.solve(a)
+    gt = api.flat_c(b, [p.c_gt for p in wl.pairs])
+    loss, dc = b.loss_orth(c, gt)
+    d_mask = torch.empty_like(c)
+    d_lam = torch.empty(len(wl.pairs), device=b.device)
+    b.solve_backward(dc, a, c, use_saved=use_saved, d_mask=d_mask, d_lambda=d_lam)
+    torch.cuda.synchronize()
+    out = dict(
+        loss=loss[:len(wl.pairs)].cpu().numpy(),
+        dC=[b.c_view(dc, p).cpu().numpy() for p in range(len(wl.pairs))],
+        dA=[b.a_view(b.dA, s).cpu().numpy() for s in range(len(wl.shapes))],
+        dF=[b.layout.feat_view(b.dfeat, s).float().cpu().numpy() for s in range(len(wl.shapes))],
+        dD=[b.c_view(d_mask, p).cpu().numpy() for p in range(len(wl.pairs))],
+        dlam=d_lam.cpu().numpy(),
+        C=[b.c_view(c, p).cpu().numpy() for p in range(len(wl.pairs))],
+        status=b.status[:len(wl.pairs)].cpu().numpy(),
+    )
+    return out
+
+
+def _oracle_backward(wl):
+    shapes, pairs = oracle_inputs(wl)
+    fwd = orc.forward_batch(shapes, pairs)
+    losses, dcs = [], []
+    for c, p in zip(fwd["C"], wl.pairs):
+        l, dc = orc.loss_orth_gt(c, p.c_gt)
+        losses.append(l); dcs.append(dc)
+    g = orc.backward_batch(shapes, pairs, fwd, dcs)
+    return shapes, pairs, fwd, losses, dcs, g
+
+
+@pytest.mark.parametrize("feat_dtype,use_saved", [("fp32", True), ("fp32", False), ("bf16", True)])
+def test_backward_against_oracle(feat_dtype, use_saved):
+    wl = synth.make_small(8, 4, (500, 6000), [12, 30, 64, 100], 256, feat_dtype=feat_dtype)
+    out = _gpu_backward(wl, use_saved=use_saved)
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    tol, gtol = TOL[feat_dtype], GTOL[feat_dtype]
+    assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert abs(out["loss"][p] - losses[p]) <= tol * max(1.0, abs(losses[p]))
+        assert rel_fro(out["dC"][p], dcs[p]) <= 10 * tol
+        assert rel_fro(out["dD"][p], g["pair"][p]["dD"]) <= gtol
+        assert abs(out["dlam"][p] - g["pair"][p]["dlam"]) <= gtol * max(1.0, abs(g["pair"][p]["dlam"]))
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= gtol
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= gtol
+
+
+def test_gradient_against_finite_differences():
+    """GPU dL/dF (FP32 mode) against central differences (h = 1e-3) of the FP64
+    pipeline along 8 seeded random directions per shape."""
+    wl = synth.make_small(9, 2, (300, 900), [10, 24], 64)
+    out = _gpu_backward(wl)
+    shapes, pairs, *_ = _oracle_backward(wl)
+    gts = [p.c_gt for p in wl.pairs]
+
+    def total_loss(sh):
+        f = orc.forward_batch(sh, pairs)
+        return sum(orc.loss_orth_gt(c, gt)[0] for c, gt in zip(f["C"], gts))
+
+    rng = np.random.default_rng(0)
+    h = 1e-3
+    for s in range(len(shapes)):
+        for _ in range(8):
+            v = rng.standard_normal(shapes[s]["feat"].shape)
+            sp = [dict(x) for x in shapes]; sp[s] = dict(shapes[s], feat=shapes[s]["feat"] + h * v)
+            sm = [dict(x) for x in shapes]; sm[s] = dict(shapes[s], feat=shapes[s]["feat"] - h * v)
+            fd = (total_loss(sp) - total_loss(sm)) / (2 * h)
+            an = float(np.sum(out["dF"][s].astype(np.float64) * v))
+            assert abs(an - fd) <= 1e-4 * max(abs(fd), 1e-3 * np.linalg.norm(v)), (s, an, fd)
+
+
+def test_autograd_function():
+    from paper_2604_10377_gb300 import api
+    wl = synth.make_small(10, 2, (400, 1200), [16], 32)
+    b = api.batch_from_workload(wl, with_grad=True)
+    feat = b.feat.clone().requires_grad_(True)
+    c = api.FmapFunction.apply(feat, b)
+    gt = api.flat_c(b, [p.c_gt for p in wl.pairs])
+    loss = 0
+    for p in range(len(wl.pairs)):
+        cp, gp = b.c_view(c, p), b.c_view(gt, p)
+        e = cp @ cp.T - torch.eye(cp.shape[0], device=cp.device)
+        loss = loss + (e * e).sum() + ((cp - gp) ** 2).sum()
+    loss.backward()
+    _, _, _, _, _, g = _oracle_backward(wl)
+    for s in range(len(wl.shapes)):
+        grad = b.layout.feat_view(feat.grad, s).cpu().numpy()
+        assert rel_fro(grad, g["dF"][s]) <= 1e-4
+
+
+# ------------------------------------------------------------------ full-size workloads
+@pytest.mark.parametrize("config", [0, 1, 2])
+def test_config_full_size(config):
+    wl = synth.make_config(config)
+    _check_forward(wl)
+
+
+def test_config3_full_size():
+    wl = synth.make_config(3)
+    _check_forward(wl, hi_gram_min_k=200, store_factors_max_k=0)
+
+
+def test_config4_sampled_pairs():
+    """The 256-pair ragged batch runs whole on the GPU; 8 sampled pairs (covering every k)
+    are recomputed by the oracle one by one."""
+    wl = synth.make_config(4)
+    b, a_gpu, c_gpu, status = gpu_forward(wl)
+    assert np.all(status == 0)
+    ks = wl.k_of_pair
+    sample = []
+    for kk in (30, 50, 100, 200):
+        idx = [p for p in range(len(ks)) if ks[p] == kk]
+        sample += idx[:2]
+    shapes, pairs = oracle_inputs(wl)
+    for p in sample:
+        pr = pairs[p]
+        sx, sy = shapes[pr["x"]], shapes[pr["y"]]
+        ax = orc.project(sx["phi"], sx["mass"], sx["feat"])
+        ay = orc.project(sy["phi"], sy["mass"], sy["feat"])
+        c = orc.solve(ax, ay, orc.mask_from_evals(sx["evals"], sy["evals"]), pr["lam"])
+        assert rel_fro(a_gpu[pr["x"]], ax) <= TOL["bf16"]
+        assert rel_fro(c_gpu[p], c) <= TOL["bf16"], (p, ks[p])
