@@ -1,0 +1,384 @@
+"""Benchmark of the functional-map hot path on GB300.
+
+One step = one pass of the whole hot path over the ragged batch: fmap_project,
+fmap_solve, the training loss and fmap_solve_backward (projection backward
+included). The default workload is the ragged mixed batch: 256 shape pairs, n
+log-uniform in 1k..100k, k drawn from {30, 50, 100, 200}, d = 256 BF16 features
+(about 10 GB of inputs per step, so every step streams from HBM, not L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs its own batch of
+pairs (weak scaling, no collective on the data path); the time is the max over
+ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fmap solves/sec (fwd+bwd, pairs/s) vs plain fwd solve; % of tensor/HBM roofline"
+WORKLOADS = {
+    4: "ragged mixed batch: 256 pairs, n log-uniform 1k-100k, k in {30,50,100,200}, d=256 BF16 features",
+    3: "large spectrum: 4 pairs, n=200k, k=200, d=512 BF16 features, FP64 Gram, factors recomputed",
+    2: "differentiable: 8 pairs, n=20k, k=100, d=384 BF16 features",
+    1: "batched: 32 pairs, n log-uniform 5k-50k, k=50, d=256 FP32 features",
+    0: "single pair: n=5000, k=30, d=128 FP32 features",
+}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), bf16_tflops=float(p["bf16_tflops"]),
+                    bf16_tflops_sustained=float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                    sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+                    source="fallback")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------- clocks sampler
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--id={self.uuid}", "--query-gpu=" + ",".join(self.FIELDS),
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic work
+def algorithmic_work(wl, ir_steps, saved_k_max):
+    """Bytes (HBM) and flops per launch of each kernel kind, from the sizes alone."""
+    fsz = 2 if wl.feat_dtype == "bf16" else 4
+    proj_bytes = sum(s.n * (4 * s.k + 4 + fsz * s.d) + 4 * s.k * s.d for s in wl.shapes)
+    proj_flops = sum(2.0 * s.n * s.k * s.d for s in wl.shapes)
+    bwd_bytes = sum(s.n * (4 * s.k + 4 + fsz * s.d) + 4 * s.k * s.d for s in wl.shapes)
+    solve_flops, adj_flops, loss_flops = 0.0, 0.0, 0.0
+    for p in wl.pairs:
+        k = wl.shapes[p.x].k
+        solve_flops += k ** 4 / 3.0 + (2.0 + 4.0 * ir_steps) * k ** 3
+        adj_flops += (0.0 if k <= saved_k_max else k ** 4 / 3.0) + (2.0 + 4.0 * ir_steps) * k ** 3
+        loss_flops += 4.0 * k ** 3
+    return dict(project=dict(bytes=proj_bytes, flops=proj_flops), project_bwd=dict(bytes=bwd_bytes, flops=proj_flops),
+                solve=dict(flops=solve_flops), adj_solve=dict(flops=adj_flops), loss=dict(flops=loss_flops))
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_pairs_per_s(wl, budget_s: float, pair_offset: int = 0, max_pairs=None):
+    """Oracle fwd+bwd, pair by pair from `pair_offset`, until `budget_s` is spent."""
+    import numpy as np
+    from oracle import fmap_oracle as orc
+    t0 = time.perf_counter()
+    done, ks = 0, []
+    npairs = len(wl.pairs)
+    while True:
+        p = wl.pairs[(pair_offset + done) % npairs]
+        sx, sy = wl.shapes[p.x], wl.shapes[p.y]
+        ax = orc.project(sx.phi, sx.mass, sx.feat_f64())
+        ay = orc.project(sy.phi, sy.mass, sy.feat_f64())
+        dm = orc.mask_from_evals(sx.evals, sy.evals)
+        c = orc.solve(ax, ay, dm, float(np.float32(p.lam)))
+        _, dc = orc.loss_orth_gt(c, p.c_gt)
+        g = orc.solve_backward(ax, ay, c, dm, float(np.float32(p.lam)), dc)
+        orc.project_backward(sx.phi, sx.mass, g["dA"])
+        orc.project_backward(sy.phi, sy.mass, g["dB"])
+        done += 1
+        ks.append(sx.k)
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_pairs is not None and done >= max_pairs):
+            return done / el, done, el, ks
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2604_10377_gb300 import synth
+    wl = synth.make_config(args.workload)
+    per_step = []
+    total_pairs = 0
+    ks = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, n, el, kk = oracle_pairs_per_s(wl, 0.0, pair_offset=it, max_pairs=1)
+        if it >= args.warmup:
+            per_step.append(el)
+            total_pairs += n
+            ks += kk
+    tot = sum(per_step)
+    value = total_pairs / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / len(per_step),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "pairs_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"one pair of the workload per step (pairs {args.warmup}..{args.warmup + args.steps - 1}, k={ks})"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_10377_gb300 import api, synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = load_peaks()
+
+    t_gen = time.time()
+    wl = synth.make_config(args.workload, replica=rank)
+    t_gen = time.time() - t_gen
+    lay = api.BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)
+    host = lay.pack_host(wl.shapes)
+    b = api.FmapBatch(lay, [(p.x, p.y, p.lam) for p in wl.pairs], device=dev, precision=wl.feat_dtype,
+                      with_grad=True, masks=[p.mask for p in wl.pairs], ir_steps=args.ir_steps,
+                      store_factors_max_k=args.store_factors_max_k)
+    b.upload(host)
+    gt_host = np.zeros(int(b.c_off[-1]), np.float32)
+    for p, pr in enumerate(wl.pairs):
+        gt_host[b.c_off[p]:b.c_off[p + 1]] = pr.c_gt.reshape(-1)
+    gt = torch.from_numpy(gt_host).to(dev)
+    loss = torch.empty(len(wl.pairs), dtype=torch.float32, device=dev)
+    dc = torch.empty_like(b.C)
+    npairs = len(wl.pairs)
+
+    def step():
+        a = b.project()
+        c = b.solve(a)
+        b.loss_orth(c, gt, loss=loss, d_c=dc)
+        b.solve_backward(dc, a, c)
+
+    def fwd_step():
+        a = b.project()
+        b.solve(a)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps, sampler=None, timing=False):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(); barrier(); torch.cuda.synchronize()
+        if timing:
+            b.set_timing(True)
+        if sampler:
+            sampler.start()
+        st = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        kt = b.read_timing() if timing else None
+        if timing:
+            b.set_timing(False)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        return ms, clocks, kt
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    sampler = ClockSampler(uuid) if uuid else None
+
+    ms_step, clocks, ktime = timed(step, args.steps, sampler=sampler, timing=True)
+    ms_fwd, _, _ = timed(fwd_step, args.steps)
+    status = b.status[:npairs].cpu().numpy()
+
+    # ---- end to end: host inputs -> device, step, loss and C back to the host
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: api.host_to_torch(v).pin_memory() for k, v in host.items()}
+        gt_pin = torch.from_numpy(gt_host).pin_memory()
+        loss_host = torch.empty(npairs, dtype=torch.float32).pin_memory()
+        c_host = torch.empty(b.C.numel(), dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in pinned.values()) + gt_pin.numel() * 4
+        d2h = loss_host.numel() * 4 + c_host.numel() * 4
+
+        def e2e_step():
+            b.upload(pinned, non_blocking=True)
+            gt.copy_(gt_pin, non_blocking=True)
+            step()
+            loss_host.copy_(loss, non_blocking=True)
+            c_host.copy_(b.C, non_blocking=True)
+
+        ms_e2e, _, _ = timed(e2e_step, max(1, args.steps // 2))
+        e2e = {"value": world * npairs / (ms_e2e / 1000.0), "unit": "pairs/s", "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel
+    work = algorithmic_work(wl, args.ir_steps, args.store_factors_max_k)
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+               for k, v in ktime.items() if v[1] > 0}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    launches_total = sum(v[1] for v in ktime.values())
+    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+
+    def roof_for(kind):
+        per_launch_ms = ktime[kind][0] / ktime[kind][1]
+        if kind in ("project", "project_bwd"):
+            ach = work[kind]["bytes"] / (per_launch_ms / 1000.0) / 1e9
+            return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": f"{peaks['source']} HBM copy bandwidth"}
+        flops = work.get(kind, {}).get("flops")
+        if flops is None:
+            return {"kernel": kind, "bound": "alu", "achieved": None, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None}
+        # solve kernels: the sum of all launches of the kind per step is the unit
+        per_step_ms = ktime[kind][0] / args.steps
+        ach = flops / (per_step_ms / 1000.0) / 1e12
+        return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak_tflops, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+
+    roofline = roof_for(dom)
+    others = {k: roof_for(k) for k in ("project", "project_bwd", "solve", "adj_solve") if k in kernels and k != dom}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, n, el, ks = oracle_pairs_per_s(wl, args.cpu_budget)
+        cpu = {"value": v, "unit": "pairs/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"fwd+bwd of the first {n} pairs of the same workload (k={ks}), {el:.1f} s, NumPy FP64"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * npairs / (ms_step / 1000.0), "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": npairs, "global_batch": world * npairs,
+                       "parallelism": f"pairs sharded over {world} GPU(s), no collective",
+                       "l2": "inputs larger than L2 (%.1f GB streamed per step)" % (work["project"]["bytes"] / 1e9)},
+            "fwd_only": {"value": world * npairs / (ms_fwd / 1000.0), "unit": "pairs/s", "ms_per_step": ms_fwd},
+            "roofline": roofline,
+            "roofline_other": others,
+            "kernels": kernels,
+            "gpu_launches": int(launches_total),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "status_ok": bool((status == 0).all()),
+            "gen_s": round(t_gen, 1),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=4, choices=sorted(WORKLOADS))
+    ap.add_argument("--ir-steps", type=int, default=1)
+    ap.add_argument("--store-factors-max-k", type=int, default=256)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

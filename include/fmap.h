@@ -181,6 +181,29 @@ FMAP_API int32_t fmap_solve_backward(fmap_batch* batch, const float* d_c, const 
 FMAP_API int32_t fmap_loss_orth(fmap_batch* batch, const float* c, const float* c_gt, float* loss, float* d_c,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Instrumentation (no counterpart in the paper) -------------------------------
+ * When timing is enabled on a batch, every kernel the library launches for it is
+ * bracketed by two CUDA events recorded on the launch stream (at most 65536 launches
+ * between reads). fmap_batch_read_timing synchronises on the last event, adds the
+ * elapsed times per kernel kind into ms[kind] and the launch counts into launches[kind]
+ * (arrays of n_kinds >= FMAP_KIND_COUNT entries, caller-owned host memory), and starts
+ * a new accumulation. Enabling or disabling also starts a new accumulation. */
+enum fmap_kernel_kind {
+    FMAP_KIND_PROJECT = 0,        /* projection main kernel (Eq. 1) */
+    FMAP_KIND_PROJECT_REDUCE = 1, /* fixed-order sum of the projection's split-K partials */
+    FMAP_KIND_GRAM = 2,           /* A_x A_x^T and A_y A_x^T (Eq. 4) */
+    FMAP_KIND_SOLVE = 3,          /* row-system Cholesky solve (Eq. 5-9) */
+    FMAP_KIND_ADJ_SOLVE = 4,      /* adjoint row solves */
+    FMAP_KIND_ADJ_GEMM = 5,       /* dA, dB, dD, dlambda from Gamma */
+    FMAP_KIND_GATHER = 6,         /* per-shape sum of dA contributions */
+    FMAP_KIND_PROJECT_BWD = 7,    /* dF = diag(M) Phi dA */
+    FMAP_KIND_LOSS = 8,           /* training loss and dL/dC */
+    FMAP_KIND_STATUS = 9,         /* status clear */
+    FMAP_KIND_COUNT = 10
+};
+FMAP_API int32_t fmap_batch_set_timing(fmap_batch* batch, int32_t enable);
+FMAP_API int32_t fmap_batch_read_timing(fmap_batch* batch, float* ms, int32_t* launches, int32_t n_kinds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,7 +76,12 @@ _PROTOS = {
     "fmap_solve_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_loss_orth": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "fmap_batch_set_timing": (c_int32, [c_void_p, c_int32]),
+    "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),
 }
+
+KIND_NAMES = ["project", "project_reduce", "gram", "solve", "adj_solve", "adj_gemm", "gather", "project_bwd",
+              "loss", "status"]
 
 
 def lib():

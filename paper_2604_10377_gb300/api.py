@@ -187,6 +187,18 @@ class FmapBatch:
         except Exception:
             pass
 
+    # ------------------------------------------------------------------ instrumentation
+    def set_timing(self, enable: bool):
+        check(_lib.lib().fmap_batch_set_timing(self._batch, 1 if enable else 0), "fmap_batch_set_timing")
+
+    def read_timing(self) -> dict:
+        """{kernel kind: (total ms, launches)} since the last read (synchronises)."""
+        n = len(_lib.KIND_NAMES)
+        ms = (ctypes.c_float * n)()
+        cnt = (ctypes.c_int32 * n)()
+        check(_lib.lib().fmap_batch_read_timing(self._batch, ms, cnt, n), "fmap_batch_read_timing")
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(_lib.KIND_NAMES)}
+
     # ------------------------------------------------------------------ data
     def upload(self, host: dict, non_blocking: bool = False):
         """Copy flat host arrays (from BatchLayout.pack_host, or pinned torch tensors) to the device."""

@@ -230,15 +230,53 @@ struct fmap_ctx {
   fmap_options opt;
 };
 
+struct Timing {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // start/stop pairs
+  std::vector<int> kind;
+  int used = 0;
+};
+constexpr int kMaxTimedLaunches = 16384;
+
 struct fmap_batch {
   fmap_ctx* ctx;
   Plan plan;
+  Timing timing;
   void* dev_mem = nullptr;
   BatchDev dev{};
   const ProjTile* d_ptiles = nullptr;
   const BwdTile* d_btiles = nullptr;
   const int2* d_systems = nullptr;
 };
+
+namespace {
+
+// Brackets one kernel launch with CUDA events on its stream when timing is on.
+struct TimedScope {
+  fmap_batch* b;
+  cudaStream_t st;
+  int idx = -1;
+  TimedScope(fmap_batch* batch, int kind, cudaStream_t stream) : b(batch), st(stream) {
+    Timing& t = b->timing;
+    if (!t.on || t.used >= kMaxTimedLaunches) return;
+    const int i = t.used;
+    while ((int)t.ev.size() < 2 * (i + 1)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      t.ev.push_back(e);
+    }
+    if ((int)t.kind.size() < i + 1) t.kind.resize(i + 1);
+    t.kind[i] = kind;
+    if (cudaEventRecord(t.ev[2 * i], st) != cudaSuccess) return;
+    idx = i;
+    t.used = i + 1;
+  }
+  ~TimedScope() {
+    if (idx >= 0) cudaEventRecord(b->timing.ev[2 * idx + 1], st);
+  }
+};
+
+}  // namespace
 
 extern "C" {
 
@@ -355,9 +393,10 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
 
 int32_t fmap_batch_destroy(fmap_batch* b) {
   if (!b) return FMAP_OK;
-  if (b->dev_mem) {
+  if (b->dev_mem || !b->timing.ev.empty()) {
     DeviceGuard dg(b->ctx->device);
-    cudaFree(b->dev_mem);
+    if (b->dev_mem) cudaFree(b->dev_mem);
+    for (cudaEvent_t e : b->timing.ev) cudaEventDestroy(e);
   }
   delete b;
   return FMAP_OK;
@@ -376,6 +415,32 @@ int32_t fmap_batch_offsets(const fmap_batch* b, int64_t* a_offsets, int64_t* c_o
   return FMAP_OK;
 }
 
+int32_t fmap_batch_set_timing(fmap_batch* b, int32_t enable) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  b->timing.on = enable != 0;
+  b->timing.used = 0;
+  return FMAP_OK;
+}
+
+int32_t fmap_batch_read_timing(fmap_batch* b, float* ms, int32_t* launches, int32_t n_kinds) {
+  if (!b || !ms || !launches || n_kinds < FMAP_KIND_COUNT) return FMAP_ERR_INVALID_ARG;
+  for (int i = 0; i < n_kinds; ++i) { ms[i] = 0.f; launches[i] = 0; }
+  Timing& t = b->timing;
+  if (t.used == 0) return FMAP_OK;
+  DeviceGuard dg(b->ctx->device);
+  cudaError_t e = cudaEventSynchronize(t.ev[2 * t.used - 1]);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize(timing)");
+  for (int i = 0; i < t.used; ++i) {
+    float x = 0.f;
+    e = cudaEventElapsedTime(&x, t.ev[2 * i], t.ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    ms[t.kind[i]] += x;
+    launches[t.kind[i]] += 1;
+  }
+  t.used = 0;
+  return FMAP_OK;
+}
+
 static int32_t check_ws(void* ws, size_t ws_bytes, int64_t need) {
   if (need == 0) return FMAP_OK;
   if (!ws || !aligned(ws, 256) || (int64_t)ws_bytes < need) return FMAP_ERR_WORKSPACE;
@@ -391,9 +456,16 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
   DeviceGuard dg(b->ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* w = static_cast<float*>(ws);
-  cudaError_t e = launch_project_simt(b->dev, b->d_ptiles, (int)b->plan.ptiles.size(), w, st);
+  cudaError_t e;
+  {
+    TimedScope ts(b, FMAP_KIND_PROJECT, st);
+    e = launch_project_simt(b->dev, b->d_ptiles, (int)b->plan.ptiles.size(), w, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "project");
-  e = launch_project_reduce(b->dev, (int)b->plan.max_kd, a_out, w, st);
+  {
+    TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
+    e = launch_project_reduce(b->dev, (int)b->plan.max_kd, a_out, w, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "project_reduce");
   return FMAP_OK;
 }
@@ -409,11 +481,19 @@ int32_t fmap_solve(fmap_batch* b, const float* a, float* c_out, void* saved, int
   DeviceGuard dg(b->ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* w = static_cast<float*>(ws);
-  cudaError_t e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
+  cudaError_t e = cudaSuccess;
+  if (status) {
+    TimedScope ts(b, FMAP_KIND_STATUS, st);
+    e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "status_clear");
-  e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+  {
+    TimedScope ts(b, FMAP_KIND_GRAM, st);
+    e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "gram");
   for (const auto& g : b->plan.groups) {
+    TimedScope ts(b, FMAP_KIND_SOLVE, st);
     e = launch_solve(b->dev, g, b->d_systems, kSolveForward, nullptr, c_out, static_cast<float*>(saved), status, w, st);
     if (e != cudaSuccess) return cuda_fail(e, "solve");
   }
@@ -432,21 +512,38 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
   DeviceGuard dg(b->ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* w = static_cast<float*>(ws);
-  cudaError_t e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
+  cudaError_t e = cudaSuccess;
+  if (status) {
+    TimedScope ts(b, FMAP_KIND_STATUS, st);
+    e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "status_clear");
-  e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+  {
+    TimedScope ts(b, FMAP_KIND_GRAM, st);
+    e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "gram");
   for (const auto& g : b->plan.groups) {
+    TimedScope ts(b, FMAP_KIND_ADJ_SOLVE, st);
     e = launch_solve(b->dev, g, b->d_systems, kSolveAdjoint, d_c, nullptr,
                      const_cast<float*>(static_cast<const float*>(saved)), status, w, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint solve");
   }
-  e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, st);
+  {
+    TimedScope ts(b, FMAP_KIND_ADJ_GEMM, st);
+    e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint gemms");
   float* da = d_a ? d_a : w + b->plan.da_int_off;
-  e = launch_gather_da(b->dev, (int)b->plan.max_kd, da, w, st);
+  {
+    TimedScope ts(b, FMAP_KIND_GATHER, st);
+    e = launch_gather_da(b->dev, (int)b->plan.max_kd, da, w, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "gather dA");
-  e = launch_project_bwd_simt(b->dev, b->d_btiles, (int)b->plan.btiles.size(), da, st);
+  if (!b->plan.btiles.empty()) {
+    TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
+    e = launch_project_bwd_simt(b->dev, b->d_btiles, (int)b->plan.btiles.size(), da, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "project backward");
   return FMAP_OK;
 }
@@ -459,7 +556,11 @@ int32_t fmap_loss_orth(fmap_batch* b, const float* c, const float* c_gt, float* 
   int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bytes);
   if (rc) return rc;
   DeviceGuard dg(b->ctx->device);
-  cudaError_t e = launch_loss_orth(b->dev, c, c_gt, loss, d_c, static_cast<float*>(ws), static_cast<cudaStream_t>(stream));
+  cudaError_t e;
+  {
+    TimedScope ts(b, FMAP_KIND_LOSS, static_cast<cudaStream_t>(stream));
+    e = launch_loss_orth(b->dev, c, c_gt, loss, d_c, static_cast<float*>(ws), static_cast<cudaStream_t>(stream));
+  }
   if (e != cudaSuccess) return cuda_fail(e, "loss");
   return FMAP_OK;
 }

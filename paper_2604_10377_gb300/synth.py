@@ -134,14 +134,17 @@ def random_orthogonal(seed: int, k: int) -> np.ndarray:
 
 
 def make_config(config: int, pairs: Optional[Sequence[int]] = None, n_scale: float = 1.0,
-                with_gt: bool = True) -> Workload:
+                with_gt: bool = True, replica: int = 0) -> Workload:
     """Draw workload `config` (0..4). `pairs` selects a subset of pair indices
     (each pair's draws do not depend on the others, so a subset is identical to
     the same pairs of the full batch). `n_scale` < 1 shrinks every n for quick
-    tests (the draws are otherwise unchanged)."""
+    tests (the draws are otherwise unchanged). `replica` r > 0 draws an
+    independent batch of the same recipe (all seeds shifted by 10^6 r), one per
+    GPU when pairs are sharded over several GPUs."""
     cfg = CONFIGS[config]
     npairs = cfg["pairs"]
-    brng = np.random.Generator(np.random.PCG64(BASE_SEED + 1000 * config + 999))
+    base = BASE_SEED + 1000000 * replica
+    brng = np.random.Generator(np.random.PCG64(base + 1000 * config + 999))
     ks, lams = [], []
     for _ in range(npairs):
         kk = cfg["k"]
@@ -154,10 +157,10 @@ def make_config(config: int, pairs: Optional[Sequence[int]] = None, n_scale: flo
     lo, hi = cfg["n"]
     n_range = (max(8, int(lo * n_scale)), max(8, int(hi * n_scale)))
     for p in sel:
-        sx = make_shape(BASE_SEED + 1000 * config + 2 * p + 0, n_range, ks[p], cfg["d"], cfg["feat"])
-        sy = make_shape(BASE_SEED + 1000 * config + 2 * p + 1, n_range, ks[p], cfg["d"], cfg["feat"])
+        sx = make_shape(base + 1000 * config + 2 * p + 0, n_range, ks[p], cfg["d"], cfg["feat"])
+        sy = make_shape(base + 1000 * config + 2 * p + 1, n_range, ks[p], cfg["d"], cfg["feat"])
         shapes += [sx, sy]
-        gt = random_orthogonal(BASE_SEED + 1000 * config + 500 + p, ks[p]) if with_gt else None
+        gt = random_orthogonal(base + 1000 * config + 500 + p, ks[p]) if with_gt else None
         plist.append(Pair(x=len(shapes) - 2, y=len(shapes) - 1, lam=lams[p], c_gt=gt))
     return Workload(name=f"config{config}", shapes=shapes, pairs=plist, feat_dtype=cfg["feat"])
 
