@@ -18,6 +18,7 @@ LIB = os.path.join(HERE, "libfmap.so")
 SOURCES = [
     "fmap_api.cu",
     "k_project_simt.cu",
+    "k_project_tc.cu",
     "k_gram.cu",
     "k_solve.cu",
 ]

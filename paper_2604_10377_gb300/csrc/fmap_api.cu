@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "fmap_internal.cuh"
 
 using namespace fmap;
@@ -24,6 +26,8 @@ int32_t cuda_fail(cudaError_t e, const char* where) {
 constexpr int64_t kAlignFloats = 64;   // 256-byte alignment of workspace regions
 constexpr int64_t kChunkV = 4096;      // vertices per split-K chunk of the projection
 constexpr int kTile = 64;
+constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core projection
+constexpr int kSmemBudget = 227 * 1024;
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -43,6 +47,19 @@ struct DeviceGuard {
   }
 };
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
 struct Plan {
   fmap_options opt{};
   std::vector<ShapeDev> shapes;
@@ -55,6 +72,14 @@ struct Plan {
   int max_k = 0, max_d = 0;
   int64_t max_kd = 0;
   int64_t da_int_off = 0;
+  // tensor-core projection (BF16 features)
+  bool tc = false;
+  std::vector<TcItem> tc_items;
+  std::vector<int32_t> tc_order;
+  std::vector<TcRedGroup> tc_groups;
+  int64_t tc_max_group_elems = 0;
+  int tc_stages = 0, tc_smem = 0;
+  uint32_t tc_f_stage = 0, tc_p_stage = 0, tc_tmem_cols = 0;
   fmap_sizes sizes{};
 };
 
@@ -120,11 +145,73 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     P.c_off[p + 1] = P.c_off[p] + (int64_t)sx.k * sx.k;
   }
 
-  // ---- workspace layout (floats, 256-byte aligned regions)
-  int64_t cur = 0;
-  for (auto& sd : P.shapes) {
-    sd.part_off = cur;
-    cur = align_up(cur + (int64_t)sd.nchunk * sd.k * sd.d, kAlignFloats);
+  // ---- workspace layout (floats, 256-byte aligned regions); the first 256 bytes
+  // hold control words (word 0: error raised by a device-side wait that timed out)
+  int64_t cur = kAlignFloats;
+  P.tc = opt.precision == FMAP_PREC_BF16;
+  if (!P.tc) {
+    for (auto& sd : P.shapes) {
+      sd.part_off = cur;
+      cur = align_up(cur + (int64_t)sd.nchunk * sd.k * sd.d, kAlignFloats);
+    }
+  } else {
+    uint32_t fmax = 0, pmax = 0, tmax = 0;
+    for (int s = 0; s < n_shapes; ++s) {
+      const ShapeDev& sd = P.shapes[s];
+      const int npad = (sd.k + 15) / 16 * 16;
+      const int mt = (sd.d + 127) / 128;
+      const int fg_cap = std::max(1, std::min(4, 512 / npad));
+      const int groups = (mt + fg_cap - 1) / fg_cap;
+      const int fg_s = (mt + groups - 1) / groups;
+      for (int g = 0; g < groups; ++g) {
+        TcRedGroup rg{};
+        rg.shape = s;
+        rg.f0 = g * fg_s * 128;
+        const int fg = std::min(fg_s, mt - g * fg_s);
+        rg.stride = fg * 128;
+        rg.dspan = std::min(fg * 128, sd.d - rg.f0);
+        rg.it_beg = (int32_t)P.tc_items.size();
+        for (int64_t v0 = 0; v0 < sd.n; v0 += kTcChunkV) {
+          TcItem it{};
+          it.shape = s; it.f0 = rg.f0; it.fg = fg; it.npad = npad;
+          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + kTcChunkV);
+          it.part_off = cur;
+          cur = align_up(cur + (int64_t)sd.k * rg.stride, kAlignFloats);
+          P.tc_items.push_back(it);
+        }
+        rg.it_end = (int32_t)P.tc_items.size();
+        P.tc_groups.push_back(rg);
+        P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)sd.k * rg.dspan);
+        fmax = std::max<uint32_t>(fmax, (uint32_t)fg * 16384u);
+        pmax = std::max<uint32_t>(pmax, (uint32_t)npad * 128u);
+        tmax = std::max<uint32_t>(tmax, (uint32_t)(fg * npad));
+      }
+    }
+    // schedule: most expensive items first; items of one chunk (different feature
+    // groups) stay adjacent so that they run at the same time and share Phi in L2
+    P.tc_order.resize(P.tc_items.size());
+    for (size_t i = 0; i < P.tc_items.size(); ++i) P.tc_order[i] = (int32_t)i;
+    auto cost = [&](const TcItem& it) {
+      const ShapeDev& sd = P.shapes[it.shape];
+      return (double)(it.v1 - it.v0) * (4.0 * sd.k + 4.0 + 2.0 * it.fg * 128);
+    };
+    std::stable_sort(P.tc_order.begin(), P.tc_order.end(), [&](int32_t a, int32_t b) {
+      const TcItem &x = P.tc_items[a], &y = P.tc_items[b];
+      const double cx = cost(x), cy = cost(y);
+      if (cx != cy) return cx > cy;
+      if (x.shape != y.shape) return x.shape < y.shape;
+      if (x.v0 != y.v0) return x.v0 < y.v0;
+      return x.f0 < y.f0;
+    });
+    P.tc_f_stage = std::max<uint32_t>(fmax, 16384u);
+    P.tc_p_stage = std::max<uint32_t>(pmax, 2048u);
+    uint32_t cols = 32;
+    while (cols < tmax) cols <<= 1;
+    P.tc_tmem_cols = cols;
+    const int fixed = 1024 + 512;
+    P.tc_stages = std::min(6, (int)((kSmemBudget - fixed) / (P.tc_f_stage + 2 * P.tc_p_stage)));
+    if (n_shapes > 0 && P.tc_stages < 2) return FMAP_ERR_UNSUPPORTED;
+    P.tc_smem = fixed + P.tc_stages * (int)(P.tc_f_stage + 2 * P.tc_p_stage);
   }
   for (auto& pd : P.pairs) {
     const int64_t kk = (int64_t)pd.k * pd.k;
@@ -174,7 +261,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   // ---- projection work lists
   for (int s = 0; s < n_shapes; ++s) {
     const ShapeDev& sd = P.shapes[s];
-    for (int c = 0; c < sd.nchunk; ++c)
+    for (int c = 0; c < (P.tc ? 0 : sd.nchunk); ++c)
       for (int kk0 = 0; kk0 < sd.k; kk0 += kTile)
         for (int f0 = 0; f0 < sd.d; f0 += kTile) {
           ProjTile t;
@@ -247,6 +334,11 @@ struct fmap_batch {
   const ProjTile* d_ptiles = nullptr;
   const BwdTile* d_btiles = nullptr;
   const int2* d_systems = nullptr;
+  const CUtensorMap* d_fmaps = nullptr;
+  const TcItem* d_tc_items = nullptr;
+  const int32_t* d_tc_order = nullptr;
+  const TcRedGroup* d_tc_groups = nullptr;
+  int sm_count = 148;
 };
 
 namespace {
@@ -363,7 +455,11 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_pt = o_sl + bytes_of(P.slot_list.size(), sizeof(int64_t));
   const int64_t o_bt = o_pt + bytes_of(P.ptiles.size(), sizeof(ProjTile));
   const int64_t o_sy = o_bt + bytes_of(P.btiles.size(), sizeof(BwdTile));
-  const int64_t total = o_sy + bytes_of(P.systems.size(), sizeof(int2)) + 256;
+  const int64_t o_tm = o_sy + bytes_of(P.systems.size(), sizeof(int2));
+  const int64_t o_ti = o_tm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_to = o_ti + bytes_of(P.tc_items.size(), sizeof(TcItem));
+  const int64_t o_tg = o_to + bytes_of(P.tc_order.size(), sizeof(int32_t));
+  const int64_t total = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup)) + 256;
   e = cudaMalloc(&b->dev_mem, (size_t)total);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch tables)"); }
   char* base = static_cast<char*>(b->dev_mem);
@@ -375,6 +471,35 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   put(o_pt, P.ptiles.data(), P.ptiles.size() * sizeof(ProjTile));
   put(o_bt, P.btiles.data(), P.btiles.size() * sizeof(BwdTile));
   put(o_sy, P.systems.data(), P.systems.size() * sizeof(int2));
+  if (P.tc && n_shapes > 0) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) { cudaFree(b->dev_mem); delete b; return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
+    for (int s = 0; s < n_shapes; ++s) {
+      const ShapeDev& sd = P.shapes[s];
+      CUtensorMap m;
+      cuuint64_t gdim[2] = {(cuuint64_t)sd.d, (cuuint64_t)sd.n};
+      cuuint64_t gstride[1] = {(cuuint64_t)sd.ld_feat * 2};
+      cuuint32_t box[2] = {64, 64};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(sd.feat), gdim, gstride, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        cudaFree(b->dev_mem); delete b;
+        std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return FMAP_ERR_CUDA;
+      }
+      put(o_tm + s * (int64_t)sizeof(CUtensorMap), &m, sizeof(m));
+    }
+    put(o_ti, P.tc_items.data(), P.tc_items.size() * sizeof(TcItem));
+    put(o_to, P.tc_order.data(), P.tc_order.size() * sizeof(int32_t));
+    put(o_tg, P.tc_groups.data(), P.tc_groups.size() * sizeof(TcRedGroup));
+    e = project_tc_set_smem(P.tc_smem);
+    if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project)"); }
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    b->sm_count = dev_sms > 0 ? dev_sms : 148;
+  }
   e = cudaMemcpy(b->dev_mem, host.data(), (size_t)total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaMemcpy(batch tables)"); }
   b->dev.shapes = reinterpret_cast<const ShapeDev*>(base + o_sh);
@@ -387,6 +512,10 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_ptiles = reinterpret_cast<const ProjTile*>(base + o_pt);
   b->d_btiles = reinterpret_cast<const BwdTile*>(base + o_bt);
   b->d_systems = reinterpret_cast<const int2*>(base + o_sy);
+  b->d_fmaps = reinterpret_cast<const CUtensorMap*>(base + o_tm);
+  b->d_tc_items = reinterpret_cast<const TcItem*>(base + o_ti);
+  b->d_tc_order = reinterpret_cast<const int32_t*>(base + o_to);
+  b->d_tc_groups = reinterpret_cast<const TcRedGroup*>(base + o_tg);
   *out = b;
   return FMAP_OK;
 }
@@ -456,15 +585,43 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
   DeviceGuard dg(b->ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* w = static_cast<float*>(ws);
-  cudaError_t e;
-  {
-    TimedScope ts(b, FMAP_KIND_PROJECT, st);
-    e = launch_project_simt(b->dev, b->d_ptiles, (int)b->plan.ptiles.size(), w, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "project");
-  {
-    TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
-    e = launch_project_reduce(b->dev, (int)b->plan.max_kd, a_out, w, st);
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256, st);   // control words
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control)");
+  const Plan& P = b->plan;
+  if (P.tc) {
+    TcProjParams tp{};
+    tp.shapes = b->dev.shapes;
+    tp.fmaps = b->d_fmaps;
+    tp.items = b->d_tc_items;
+    tp.order = b->d_tc_order;
+    tp.n_items = (int32_t)P.tc_items.size();
+    tp.stages = P.tc_stages;
+    tp.f_stage_bytes = P.tc_f_stage;
+    tp.p_stage_bytes = P.tc_p_stage;
+    tp.tmem_cols = P.tc_tmem_cols;
+    tp.ws = w;
+    tp.err = static_cast<int*>(ws);
+    const int grid = (int)std::min<int64_t>((int64_t)P.tc_items.size(), b->sm_count);
+    {
+      TimedScope ts(b, FMAP_KIND_PROJECT, st);
+      e = launch_project_tc(tp, grid, P.tc_smem, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
+    {
+      TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
+      e = launch_project_tc_reduce(b->dev.shapes, b->d_tc_items, b->d_tc_groups, (int)P.tc_groups.size(),
+                                   P.tc_max_group_elems, a_out, w, st);
+    }
+  } else {
+    {
+      TimedScope ts(b, FMAP_KIND_PROJECT, st);
+      e = launch_project_simt(b->dev, b->d_ptiles, (int)P.ptiles.size(), w, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "project");
+    {
+      TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
+      e = launch_project_reduce(b->dev, (int)P.max_kd, a_out, w, st);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e, "project_reduce");
   return FMAP_OK;

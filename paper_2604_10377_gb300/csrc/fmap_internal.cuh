@@ -1,9 +1,12 @@
 // Internal declarations shared by the functional-map CUDA sources.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "../../include/fmap.h"
 
@@ -77,6 +80,41 @@ struct BatchDev {
 };
 
 __host__ __device__ inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
+
+// Work item of the tensor-core projection: one vertex chunk of one feature group
+// (fg M-tiles of 128 features starting at feature f0) of one shape.
+struct TcItem {
+  int32_t shape, f0, fg, npad;
+  int64_t v0, v1;
+  int64_t part_off;    // float offset (workspace) of the item's partial, k x (fg*128)
+};
+
+// Items [it_beg, it_end) hold the partials of features f0 .. f0+dspan of one shape.
+struct TcRedGroup {
+  int32_t shape, f0, dspan, stride;
+  int32_t it_beg, it_end;
+};
+
+struct TcProjParams {
+  const ShapeDev* shapes;
+  const CUtensorMap* fmaps;   // per shape: BF16 features, box 64 x 64, 128-byte swizzle
+  const TcItem* items;
+  const int32_t* order;       // schedule: item indices, most expensive first
+  int32_t n_items;
+  int32_t stages;
+  uint32_t f_stage_bytes;
+  uint32_t p_stage_bytes;
+  uint32_t tmem_cols;
+  float* ws;
+  int* err;                   // workspace error word
+};
+
+cudaError_t project_tc_set_smem(int bytes);
+int project_tc_threads();
+cudaError_t launch_project_tc(const TcProjParams& p, int grid, int smem_bytes, cudaStream_t st);
+cudaError_t launch_project_tc_reduce(const ShapeDev* shapes, const TcItem* items, const TcRedGroup* groups,
+                                     int n_groups, int64_t max_elems, float* a_out, const float* ws,
+                                     cudaStream_t st);
 
 // ---- launchers (each enqueues on `st`; return cudaError_t of the launch) ----
 cudaError_t launch_project_simt(const BatchDev& b, const ProjTile* tiles, int ntiles, float* ws,

@@ -1,0 +1,269 @@
+// Spectral projection on the 5th-generation tensor cores (Eq. 1), BF16 features.
+//
+//   A_s^T (d x k) = F_s^T (d x n) . P_s (n x k),   P_s = diag(M_s) Phi_s
+//
+// One persistent CTA per SM walks a list of work items (shape, feature group,
+// vertex chunk). Per 64-vertex stage:
+//   warp 0      TMA-loads the F tile (MN-major, 128-byte swizzle) straight from HBM;
+//   warps 2-9   read Phi and M, form P = M * Phi in FP32 and split it into
+//               BF16 hi + lo (P = hi + lo to ~2^-17), written as K-major
+//               128-byte-swizzled B tiles: the mass is fused into the operand load;
+//   warp 1      issues tcgen05.mma (M = 128 features, N = k rounded up to 16,
+//               K = 16 vertices) for hi and lo into FP32 accumulators in TMEM.
+// At the end of an item warps 2-9 read the accumulators back (tcgen05.ld) and
+// write the item's partial A; a second kernel adds the partials of each shape
+// in a fixed order. F is exact in BF16, so A carries only the ~2^-17 error of
+// the hi/lo split and FP32 accumulation.
+//
+// Every mbarrier wait is bounded (tc::kWaitTimeoutNs); a wait that gives up
+// raises a CTA-wide abort flag, every role stops, TMEM is freed, and the
+// workspace error word is set to FMAP_ERR_TIMEOUT (reported per pair by the solve).
+#include "fmap_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fmap {
+namespace {
+
+constexpr int kConvWarps = 8;
+constexpr int kThreads = 32 * (2 + kConvWarps);
+constexpr int kStageV = 64;            // vertices per pipeline stage (= one 128-byte K row of bf16)
+constexpr uint32_t kBoxBytes = 64 * 64 * 2;   // one TMA box: 64 vertices x 64 features bf16
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+}
+
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+  hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+  lo = pack_bf16(a - __bfloat162float(ha), b - __bfloat162float(hb));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = P.stages;
+  uint8_t* sF = smem;
+  uint8_t* sPh = sF + (size_t)S * P.f_stage_bytes;
+  uint8_t* sPl = sPh + (size_t)S * P.p_stage_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sPl + (size_t)S * P.p_stage_bytes);
+  uint64_t* full_f = bars;
+  uint64_t* full_p = bars + S;
+  uint64_t* empty = bars + 2 * S;
+  uint64_t* acc_full = bars + 3 * S;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full_f[s], 1);
+      tc::mbar_init(&full_p[s], kConvWarps);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, kConvWarps);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, P.tmem_cols);
+    tc::tmem_relinquish();
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+        const TcItem item = P.items[P.order[it]];
+        const CUtensorMap* map = P.fmaps + item.shape;
+        tc::prefetch_tmap(map);
+        const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
+        for (int st = 0; st < nst; ++st) {
+          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag)) goto producer_done;
+          tc::mbar_arrive_expect_tx(&full_f[stage], (uint32_t)item.fg * 2 * kBoxBytes);
+          uint8_t* dst = sF + (size_t)stage * P.f_stage_bytes;
+          const int y = (int)(item.v0 + (int64_t)st * kStageV);
+          for (int m = 0; m < item.fg; ++m)
+            for (int h = 0; h < 2; ++h)
+              tc::tma_load_2d(dst + (m * 2 + h) * kBoxBytes, map, &full_f[stage], item.f0 + m * 128 + h * 64, y);
+          if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
+        }
+      }
+    producer_done:
+      if (*abort_flag) {
+        // let copies already in flight land before the CTA's shared memory goes away
+        const uint64_t t0 = tc::globaltimer();
+        while (tc::globaltimer() - t0 < 2000000ull) {}
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, acc_phase = 0;
+      for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+        const TcItem item = P.items[P.order[it]];
+        if (!tc::mbar_wait(acc_empty, acc_phase ^ 1, abort_flag)) break;
+        tc::tc_fence_after();
+        const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)item.npad, 1, 0);
+        const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
+        bool ok = true;
+        for (int st = 0; st < nst && ok; ++st) {
+          ok = tc::mbar_wait(&full_f[stage], phase, abort_flag) && tc::mbar_wait(&full_p[stage], phase, abort_flag);
+          if (!ok) break;
+          tc::tc_fence_after();
+          const uint32_t a_base = tc::smem_u32(sF + (size_t)stage * P.f_stage_bytes);
+          const uint32_t ph = tc::smem_u32(sPh + (size_t)stage * P.p_stage_bytes);
+          const uint32_t pl = tc::smem_u32(sPl + (size_t)stage * P.p_stage_bytes);
+#pragma unroll
+          for (int kk = 0; kk < kStageV / 16; ++kk) {
+            const uint64_t bh = tc::smem_desc(ph + kk * 32, 16, 1024, tc::kLayoutSW128);
+            const uint64_t bl = tc::smem_desc(pl + kk * 32, 16, 1024, tc::kLayoutSW128);
+            for (int m = 0; m < item.fg; ++m) {
+              const uint64_t ad = tc::smem_desc(a_base + m * 2 * kBoxBytes + kk * 2048, kBoxBytes, 1024,
+                                                tc::kLayoutSW128);
+              const uint32_t d = tmem_base + (uint32_t)(m * item.npad);
+              tc::mma_bf16(d, ad, bh, idesc, (st | kk) != 0 ? 1u : 0u);
+              tc::mma_bf16(d, ad, bl, idesc, 1u);
+            }
+          }
+          tc::mma_commit(&empty[stage]);
+          if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
+        tc::mma_commit(acc_full);
+        acc_phase ^= 1;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ converters + epilogue
+    const int cw = warp - 2;
+    uint32_t stage = 0, phase = 0, acc_phase = 0;
+    for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+      const TcItem item = P.items[P.order[it]];
+      const ShapeDev s = P.shapes[item.shape];
+      const int k = s.k;
+      const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
+      const int nqb = item.npad / 16;
+      const int c = lane & 7;
+      for (int st = 0; st < nst; ++st) {
+        if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag)) goto conv_done;
+        uint8_t* th = sPh + (size_t)stage * P.p_stage_bytes;
+        uint8_t* tl = sPl + (size_t)stage * P.p_stage_bytes;
+        const int64_t vb = item.v0 + (int64_t)st * kStageV + 8 * c;
+        for (int qb = cw; qb < nqb; qb += kConvWarps) {
+          const int n0 = 4 * (qb * 4 + (lane >> 3));
+          float p[8][4];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int64_t v = vb + i;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            float m = 0.f;
+            if (v < item.v1) {
+              m = __ldg(s.mass + v);
+              if (n0 < k) x = __ldg(reinterpret_cast<const float4*>(s.phi + v * s.ld_phi + n0));
+            }
+            p[i][0] = (n0 + 0 < k) ? x.x * m : 0.f;
+            p[i][1] = (n0 + 1 < k) ? x.y * m : 0.f;
+            p[i][2] = (n0 + 2 < k) ? x.z * m : 0.f;
+            p[i][3] = (n0 + 3 < k) ? x.w * m : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int n = n0 + j;
+            uint4 hv, lv;
+            split_pair(p[0][j], p[1][j], hv.x, lv.x);
+            split_pair(p[2][j], p[3][j], hv.y, lv.y);
+            split_pair(p[4][j], p[5][j], hv.z, lv.z);
+            split_pair(p[6][j], p[7][j], hv.w, lv.w);
+            const uint32_t off = (uint32_t)n * 128u + ((uint32_t)(c ^ (n & 7)) << 4);
+            *reinterpret_cast<uint4*>(th + off) = hv;
+            *reinterpret_cast<uint4*>(tl + off) = lv;
+          }
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&full_p[stage]);
+        if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
+      }
+      // epilogue: accumulators -> this item's partial A (k x stride, row-major)
+      if (!tc::mbar_wait(acc_full, acc_phase, abort_flag)) goto conv_done;
+      tc::tc_fence_after();
+      {
+        const int quarter = warp & 3, half = cw >> 2;
+        const int stride = item.fg * 128;
+        float* part = P.ws + item.part_off;
+        for (int m = 0; m < item.fg; ++m) {
+          const int fl = m * 128 + quarter * 32 + lane;
+          const bool fok = item.f0 + fl < s.d;
+          for (int ch = half; ch < item.npad / 16; ch += 2) {
+            float v[16];
+            tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(m * item.npad + ch * 16), v);
+            if (fok) {
+#pragma unroll
+              for (int t = 0; t < 16; ++t) {
+                const int n = ch * 16 + t;
+                if (n < k) part[(int64_t)n * stride + fl] = v[t];
+              }
+            }
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty);
+      acc_phase ^= 1;
+    }
+  conv_done:;
+  }
+
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem_base, P.tmem_cols);
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(P.err, (int)FMAP_ERR_TIMEOUT);
+}
+
+// A_s[n][f0 + f] = sum over the group's items (in order) of partial[n][f].
+__global__ void project_tc_reduce_kernel(const ShapeDev* shapes, const TcItem* items, const TcRedGroup* groups,
+                                         float* a_out, const float* ws) {
+  const TcRedGroup g = groups[blockIdx.y];
+  const ShapeDev s = shapes[g.shape];
+  const int64_t total = (int64_t)s.k * g.dspan;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / g.dspan, f = e % g.dspan;
+    float acc = 0.f;
+    for (int i = g.it_beg; i < g.it_end; ++i) acc += ws[items[i].part_off + n * g.stride + f];
+    a_out[s.a_off + n * s.d + g.f0 + f] = acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t project_tc_set_smem(int bytes) {
+  return cudaFuncSetAttribute(project_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int project_tc_threads() { return kThreads; }
+
+cudaError_t launch_project_tc(const TcProjParams& p, int grid, int smem_bytes, cudaStream_t st) {
+  if (p.n_items <= 0) return cudaSuccess;
+  project_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_tc_reduce(const ShapeDev* shapes, const TcItem* items, const TcRedGroup* groups,
+                                     int n_groups, int64_t max_elems, float* a_out, const float* ws,
+                                     cudaStream_t st) {
+  if (n_groups <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<int64_t>((max_elems + 255) / 256, 4096), (unsigned)n_groups);
+  project_tc_reduce_kernel<<<grid, 256, 0, st>>>(shapes, items, groups, a_out, ws);
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

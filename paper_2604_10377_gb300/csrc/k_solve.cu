@@ -69,7 +69,11 @@ __global__ void __launch_bounds__(NT) solve_kernel(BatchDev b, const int2* syste
   float* fac = (saved != nullptr && pd.fac_off >= 0) ? saved + pd.fac_off + (int64_t)i * tri(k) : nullptr;
   const float lam = pd.lam;
 
-  if (tid == 0) s_bad = 0;
+  if (tid == 0) {
+    s_bad = 0;
+    // a projection wait that timed out leaves its error in the workspace's first word
+    if (i == 0 && reinterpret_cast<const int*>(ws)[0] != 0) set_status(status, p, FMAP_ERR_TIMEOUT);
+  }
   for (int a = tid; a < k; a += NT) rh[a] = rhs[a];
 
   if (mode == kSolveAdjoint && fac != nullptr) {
