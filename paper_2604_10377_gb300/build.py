@@ -21,6 +21,7 @@ SOURCES = [
     "k_project_tc.cu",
     "k_gram.cu",
     "k_solve.cu",
+    "k_chol.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -242,7 +242,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   for (auto& pd : P.pairs) {
     if (pd.k <= opt.store_factors_max_k) {
       pd.fac_off = fac;
-      fac = align_up(fac + (int64_t)pd.k * tri(pd.k), kAlignFloats);
+      fac = align_up(fac + (int64_t)pd.k * chol_factor_floats(pd.k), kAlignFloats);
     } else {
       pd.fac_off = -1;
     }

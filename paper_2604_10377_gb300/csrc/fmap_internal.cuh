@@ -44,7 +44,7 @@ struct PairDev {
   int64_t c_off;       // float offset of C_p / dC_p in the flat k x k buffers
   int64_t g_off;       // float offset (workspace) of G = A_x A_x^T  (k x k)
   int64_t r_off;       // float offset (workspace) of R = A_y A_x^T  (k x k)
-  int64_t g64_off;     // double offset (workspace) of the FP64 Gram, or -1
+  int64_t g64_off;     // float2 offset (workspace) of the double-float (hi, lo) Gram, or -1
   int64_t gam_off;     // float offset (workspace) of Gamma (k x k)
   int64_t w_off;       // float offset (workspace) of W = Gamma^T C + C^T Gamma (k x k)
   int64_t e_off;       // float offset (workspace) of E = C C^T - I (k x k)
@@ -144,5 +144,6 @@ cudaError_t launch_loss_orth(const BatchDev& b, const float* c, const float* c_g
                              float* ws, cudaStream_t st);
 cudaError_t launch_status_clear(int32_t* status, int n, cudaStream_t st);
 cudaError_t solve_set_smem_limits();
+int64_t chol_factor_floats(int k);   // saved factor size of one row system (padded packed rows)
 
 }  // namespace fmap

@@ -1,11 +1,7 @@
-// Row-wise regularised solve (Eq. 5-9) and its adjoint.
-//
-// One thread block per row system S_i = G + lambda diag(D_i): the packed lower
-// triangle of S_i lives in shared memory, is factorised in place by a
-// right-looking Cholesky in FP32, and the solve is followed by iterative
-// refinement with the residual taken against G (FP64 G for hi_gram pairs).
-// The same kernel solves the adjoint systems S_i gamma_i = dL/dc_i, reusing saved
-// factors when the caller kept them.
+// Adjoint of the row-wise solve (given Gamma from the adjoint row solves):
+// W = Gamma^T C + C^T Gamma, dA_x = Gamma^T A_y - W A_x, dA_y = Gamma A_x,
+// dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C); the per-shape gather of
+// dA contributions; the training loss; the status clear.
 #include <math.h>
 
 #include "fmap_internal.cuh"
@@ -19,165 +15,10 @@ __device__ __forceinline__ float mask_entry(const PairDev& pd, const float* evx,
   return t * t;
 }
 
-__device__ __forceinline__ void set_status(int32_t* status, int p, int32_t code) {
-  if (status) atomicCAS(status + p, 0, code);
-}
-
-// In-place solve of L L^T x = v by warp 0 (v in shared memory, overwritten with x).
-__device__ __forceinline__ void warp_chol_solve(const float* L, const float* dg, float* v, int k, int lane) {
-  __syncwarp();
-  for (int j = 0; j < k; ++j) {           // L y = v
-    const float yj = v[j] / dg[j];
-    __syncwarp();
-    if (lane == 0) v[j] = yj;
-    for (int a = j + 1 + lane; a < k; a += 32) v[a] = fmaf(-L[tri(a) + j], yj, v[a]);
-    __syncwarp();
-  }
-  for (int j = k - 1; j >= 0; --j) {      // L^T x = y
-    const float xj = v[j] / dg[j];
-    __syncwarp();
-    if (lane == 0) v[j] = xj;
-    const float* row = L + tri(j);
-    for (int a = lane; a < j; a += 32) v[a] = fmaf(-row[a], xj, v[a]);
-    __syncwarp();
-  }
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) solve_kernel(BatchDev b, const int2* systems, int first, int count, int mode,
-                                                  const float* rhs_flat, float* out_flat, float* saved,
-                                                  int32_t* status, float* ws) {
-  constexpr int NW = NT / 32;
-  extern __shared__ float smem[];
-  __shared__ int s_bad;
-  if ((int)blockIdx.x >= count) return;
-  const int2 sys = systems[first + blockIdx.x];
-  const int p = sys.x, i = sys.y;
-  const PairDev pd = b.pairs[p];
-  const int k = pd.k;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const float* evx = b.shapes[pd.x].evals;
-  const float* evy = b.shapes[pd.y].evals;
-  float* L = smem;                                  // packed lower triangle, tri(k)
-  float* dg = smem + ((tri(k) + 3) & ~3LL);         // sqrt pivots, k
-  float* v = dg + k;                                // working vector, k
-  float* xs = v + k;                                // solution, k
-  float* rh = xs + k;                               // right-hand side, k
-  const float* G = ws + pd.g_off;
-  const float* rhs = (mode == kSolveForward) ? ws + pd.r_off + (int64_t)i * k : rhs_flat + pd.c_off + (int64_t)i * k;
-  float* out = (mode == kSolveForward) ? out_flat + pd.c_off + (int64_t)i * k : ws + pd.gam_off + (int64_t)i * k;
-  float* fac = (saved != nullptr && pd.fac_off >= 0) ? saved + pd.fac_off + (int64_t)i * tri(k) : nullptr;
-  const float lam = pd.lam;
-
-  if (tid == 0) {
-    s_bad = 0;
-    // a projection wait that timed out leaves its error in the workspace's first word
-    if (i == 0 && reinterpret_cast<const int*>(ws)[0] != 0) set_status(status, p, FMAP_ERR_TIMEOUT);
-  }
-  for (int a = tid; a < k; a += NT) rh[a] = rhs[a];
-
-  if (mode == kSolveAdjoint && fac != nullptr) {
-    // factors saved by the forward solve (diagonal entries hold the sqrt pivots)
-    for (int64_t e = tid; e < tri(k); e += NT) L[e] = fac[e];
-    __syncthreads();
-    for (int a = tid; a < k; a += NT) dg[a] = L[tri(a) + a];
-    __syncthreads();
-  } else {
-    for (int a = warp; a < k; a += NW) {
-      const float* grow = G + (int64_t)a * k;
-      float* lrow = L + tri(a);
-      for (int c = lane; c <= a; c += 32) lrow[c] = grow[c];
-      if (lane == 0) lrow[a] = grow[a] + lam * mask_entry(pd, evx, evy, i, a);
-    }
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-      const float piv = L[tri(j) + j];
-      if (!(piv > 0.f) || !(piv < INFINITY)) {
-        if (tid == 0) s_bad = j + 1;
-        break;
-      }
-      const float dj = sqrtf(piv);
-      const float inv = 1.f / dj;
-      if (tid == 0) dg[j] = dj;
-      for (int a = j + 1 + tid; a < k; a += NT) L[tri(a) + j] *= inv;
-      __syncthreads();
-      for (int a = j + 1 + warp; a < k; a += NW) {
-        const float la = L[tri(a) + j];
-        float* row = L + tri(a);
-        for (int c = j + 1 + lane; c <= a; c += 32) row[c] = fmaf(-la, L[tri(c) + j], row[c]);
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    if (s_bad) {
-      if (tid == 0) set_status(status, p, FMAP_ERR_NOT_SPD | (i << 8));
-      for (int a = tid; a < k; a += NT) out[a] = __int_as_float(0x7fc00000);
-      return;
-    }
-    if (mode == kSolveForward && fac != nullptr) {
-      for (int64_t e = tid; e < tri(k); e += NT) fac[e] = L[e];
-      __syncthreads();
-      for (int a = tid; a < k; a += NT) fac[tri(a) + a] = dg[a];
-    }
-  }
-
-  // x = S^{-1} rhs
-  for (int a = tid; a < k; a += NT) v[a] = rh[a];
-  __syncthreads();
-  if (warp == 0) warp_chol_solve(L, dg, v, k, lane);
-  __syncthreads();
-  for (int a = tid; a < k; a += NT) xs[a] = v[a];
-  __syncthreads();
-
-  // iterative refinement: x += S^{-1} (rhs - S x)
-  const double* G64 = pd.g64_off >= 0 ? reinterpret_cast<const double*>(ws) + pd.g64_off : nullptr;
-  for (int it = 0; it < b.ir_steps; ++it) {
-    for (int a = warp; a < k; a += NW) {
-      float r;
-      if (G64) {
-        const double* grow = G64 + (int64_t)a * k;
-        double sum = 0.0;
-        for (int c = lane; c < k; c += 32) sum += grow[c] * (double)xs[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        sum += (double)lam * (double)mask_entry(pd, evx, evy, i, a) * (double)xs[a];
-        r = (float)((double)rh[a] - sum);
-      } else {
-        const float* grow = G + (int64_t)a * k;
-        float sum = 0.f;
-        for (int c = lane; c < k; c += 32) sum = fmaf(grow[c], xs[c], sum);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        sum = fmaf(lam * mask_entry(pd, evx, evy, i, a), xs[a], sum);
-        r = rh[a] - sum;
-      }
-      if (lane == 0) v[a] = r;
-    }
-    __syncthreads();
-    if (warp == 0) warp_chol_solve(L, dg, v, k, lane);
-    __syncthreads();
-    for (int a = tid; a < k; a += NT) xs[a] += v[a];
-    __syncthreads();
-  }
-
-  bool finite = true;
-  for (int a = tid; a < k; a += NT) {
-    const float xv = xs[a];
-    out[a] = xv;
-    if (!isfinite(xv)) finite = false;
-  }
-  if (!finite) set_status(status, p, FMAP_ERR_NONFINITE | (i << 8));
-}
-
-template <int NT>
-cudaError_t set_limit() {
-  const int bytes = (int)((tri(kMaxK) + 4 + 4 * kMaxK) * sizeof(float));
-  return cudaFuncSetAttribute(solve_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 // ---------------------------------------------------------------- adjoint GEMMs
 constexpr int kTile = 64;
 constexpr int kStage = 16;
+
 
 // W = Gamma^T C + C^T Gamma (k x k), and the mask gradient dD = -lambda Gamma o C.
 __global__ void __launch_bounds__(256) adjoint_w_kernel(BatchDev b, const float* c_flat, float* d_mask, float* ws) {
@@ -391,31 +232,6 @@ __global__ void status_clear_kernel(int32_t* status, int n) {
 }
 
 }  // namespace
-
-cudaError_t solve_set_smem_limits() {
-  cudaError_t e;
-  if ((e = set_limit<64>()) != cudaSuccess) return e;
-  if ((e = set_limit<128>()) != cudaSuccess) return e;
-  return set_limit<256>();
-}
-
-cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode, const float* rhs_flat,
-                         float* out_flat, float* saved, int32_t* status, float* ws, cudaStream_t st) {
-  if (g.count <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(((tri(g.kmax) + 3) & ~3LL) + 4 * g.kmax) * sizeof(float);
-  switch (g.threads) {
-    case 64:
-      solve_kernel<64><<<g.count, 64, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat, saved, status, ws);
-      break;
-    case 128:
-      solve_kernel<128><<<g.count, 128, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat, saved, status, ws);
-      break;
-    default:
-      solve_kernel<256><<<g.count, 256, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat, saved, status, ws);
-      break;
-  }
-  return cudaGetLastError();
-}
 
 cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
                                  float* d_mask, float* d_lambda, float* ws, cudaStream_t st) {
