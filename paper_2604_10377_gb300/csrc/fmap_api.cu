@@ -72,6 +72,7 @@ struct Plan {
   int max_k = 0, max_d = 0;
   int64_t max_kd = 0;
   int64_t da_int_off = 0;
+  int64_t loss_part_off = 0;
   // tensor-core projection (BF16 features)
   bool tc = false;
   std::vector<TcItem> tc_items;
@@ -80,6 +81,12 @@ struct Plan {
   int64_t tc_max_group_elems = 0;
   int tc_stages = 0, tc_smem = 0;
   uint32_t tc_f_stage = 0, tc_p_stage = 0, tc_tmem_cols = 0;
+  // tensor-core backward projection
+  std::vector<TcBwdItem> bw_items;
+  std::vector<int32_t> bw_order;
+  std::vector<TcBwdGroup> bw_groups;
+  int bw_max_img = 0, bw_stages = 0, bw_smem = 0;
+  uint32_t bw_b_bytes = 0;
   fmap_sizes sizes{};
 };
 
@@ -225,6 +232,8 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       pd.g64_off = -1;
     }
   }
+  P.loss_part_off = cur;   // per-pair, per-tile partial sums of the training loss
+  cur = align_up(cur + (int64_t)n_pairs * 16, kAlignFloats);
   const int64_t ws_fwd = cur;
   for (auto& pd : P.pairs) {
     const int64_t kk = (int64_t)pd.k * pd.k, kd = (int64_t)pd.k * pd.d;
@@ -235,6 +244,49 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   }
   P.da_int_off = cur;
   cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
+  if (P.tc) {
+    for (int s = 0; s < n_shapes; ++s) {
+      const ShapeDev& sd = P.shapes[s];
+      if (!sd.dfeat) continue;
+      const int kb = (sd.k + 31) / 32;
+      const int ngroups = (sd.d + 127) / 128;
+      const int nf_s = ((sd.d + ngroups - 1) / ngroups + 15) / 16 * 16;
+      for (int g = 0; g < ngroups; ++g) {
+        TcBwdGroup bg{};
+        bg.shape = s; bg.f0 = g * nf_s; bg.nf = std::min(nf_s, sd.d - bg.f0); bg.kb = kb;
+        if (bg.nf <= 0) continue;
+        bg.img_off = cur;
+        cur = align_up(cur + (int64_t)kb * bg.nf * 32, kAlignFloats);
+        P.bw_groups.push_back(bg);
+        P.bw_max_img = std::max(P.bw_max_img, kb * bg.nf * 32);
+        P.bw_b_bytes = std::max<uint32_t>(P.bw_b_bytes, (uint32_t)(kb * bg.nf * 128));
+        for (int64_t v0 = 0; v0 < sd.n; v0 += kTcChunkV) {
+          TcBwdItem it{};
+          it.shape = s; it.f0 = bg.f0; it.nf = bg.nf; it.kb = kb;
+          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + kTcChunkV);
+          it.img_off = bg.img_off;
+          P.bw_items.push_back(it);
+        }
+      }
+    }
+    P.bw_order.resize(P.bw_items.size());
+    for (size_t i = 0; i < P.bw_items.size(); ++i) P.bw_order[i] = (int32_t)i;
+    auto bcost = [&](const TcBwdItem& it) {
+      return (double)(it.v1 - it.v0) * (4.0 * P.shapes[it.shape].k + 2.0 * it.nf);
+    };
+    std::stable_sort(P.bw_order.begin(), P.bw_order.end(), [&](int32_t a, int32_t b) {
+      const TcBwdItem &x = P.bw_items[a], &y = P.bw_items[b];
+      const double cx = bcost(x), cy = bcost(y);
+      if (cx != cy) return cx > cy;
+      if (x.shape != y.shape) return x.shape < y.shape;
+      if (x.v0 != y.v0) return x.v0 < y.v0;
+      return x.f0 < y.f0;
+    });
+    const int fixed = 1024 + 512;
+    P.bw_stages = std::min(6, (kSmemBudget - fixed - (int)P.bw_b_bytes) / 16384);
+    if (!P.bw_items.empty() && P.bw_stages < 2) return FMAP_ERR_UNSUPPORTED;
+    P.bw_smem = fixed + (int)P.bw_b_bytes + P.bw_stages * 16384;
+  }
   const int64_t ws_bwd = std::max(cur, ws_fwd);
 
   // ---- saved factors
@@ -270,7 +322,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
           t.v1 = std::min<int64_t>(sd.n, t.v0 + kChunkV);
           P.ptiles.push_back(t);
         }
-    if (sd.dfeat)
+    if (sd.dfeat && !P.tc)
       for (int64_t v0 = 0; v0 < sd.n; v0 += kTile)
         for (int f0 = 0; f0 < sd.d; f0 += kTile) {
           BwdTile t;
@@ -338,6 +390,10 @@ struct fmap_batch {
   const TcItem* d_tc_items = nullptr;
   const int32_t* d_tc_order = nullptr;
   const TcRedGroup* d_tc_groups = nullptr;
+  const CUtensorMap* d_phimaps = nullptr;
+  const TcBwdItem* d_bw_items = nullptr;
+  const int32_t* d_bw_order = nullptr;
+  const TcBwdGroup* d_bw_groups = nullptr;
   int sm_count = 148;
 };
 
@@ -459,7 +515,11 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_ti = o_tm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_to = o_ti + bytes_of(P.tc_items.size(), sizeof(TcItem));
   const int64_t o_tg = o_to + bytes_of(P.tc_order.size(), sizeof(int32_t));
-  const int64_t total = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup)) + 256;
+  const int64_t o_pm = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
+  const int64_t o_bi = o_pm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
+  const int64_t o_bg = o_bo + bytes_of(P.bw_order.size(), sizeof(int32_t));
+  const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
   e = cudaMalloc(&b->dev_mem, (size_t)total);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch tables)"); }
   char* base = static_cast<char*>(b->dev_mem);
@@ -490,6 +550,27 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
         return FMAP_ERR_CUDA;
       }
       put(o_tm + s * (int64_t)sizeof(CUtensorMap), &m, sizeof(m));
+      // FP32 basis for the backward projection: box 32 basis x 128 vertices
+      CUtensorMap pm;
+      cuuint64_t pdim[2] = {(cuuint64_t)sd.k, (cuuint64_t)sd.n};
+      cuuint64_t pstride[1] = {(cuuint64_t)sd.ld_phi * 4};
+      cuuint32_t pbox[2] = {32, 128};
+      r = encode(&pm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sd.phi), pdim, pstride, pbox, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        cudaFree(b->dev_mem); delete b;
+        std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled(phi) failed (%d)", (int)r);
+        return FMAP_ERR_CUDA;
+      }
+      put(o_pm + s * (int64_t)sizeof(CUtensorMap), &pm, sizeof(pm));
+    }
+    put(o_bi, P.bw_items.data(), P.bw_items.size() * sizeof(TcBwdItem));
+    put(o_bo, P.bw_order.data(), P.bw_order.size() * sizeof(int32_t));
+    put(o_bg, P.bw_groups.data(), P.bw_groups.size() * sizeof(TcBwdGroup));
+    if (!P.bw_items.empty()) {
+      e = project_bwd_tc_set_smem(P.bw_smem);
+      if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project bwd)"); }
     }
     put(o_ti, P.tc_items.data(), P.tc_items.size() * sizeof(TcItem));
     put(o_to, P.tc_order.data(), P.tc_order.size() * sizeof(int32_t));
@@ -516,6 +597,10 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_tc_items = reinterpret_cast<const TcItem*>(base + o_ti);
   b->d_tc_order = reinterpret_cast<const int32_t*>(base + o_to);
   b->d_tc_groups = reinterpret_cast<const TcRedGroup*>(base + o_tg);
+  b->d_phimaps = reinterpret_cast<const CUtensorMap*>(base + o_pm);
+  b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
+  b->d_bw_order = reinterpret_cast<const int32_t*>(base + o_bo);
+  b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
   *out = b;
   return FMAP_OK;
 }
@@ -701,6 +786,28 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
     e = launch_project_bwd_simt(b->dev, b->d_btiles, (int)b->plan.btiles.size(), da, st);
   }
+  if (e == cudaSuccess && !b->plan.bw_items.empty()) {
+    const Plan& P = b->plan;
+    {
+      TimedScope ts(b, FMAP_KIND_GATHER, st);
+      e = launch_build_dat_image(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "dA image");
+    TcBwdParams bp{};
+    bp.shapes = b->dev.shapes;
+    bp.phimaps = b->d_phimaps;
+    bp.items = b->d_bw_items;
+    bp.order = b->d_bw_order;
+    bp.n_items = (int32_t)P.bw_items.size();
+    bp.stages = P.bw_stages;
+    bp.b_bytes_max = P.bw_b_bytes;
+    bp.tmem_cols = 256;
+    bp.ws = w;
+    bp.err = static_cast<int*>(ws);
+    const int grid = (int)std::min<int64_t>((int64_t)P.bw_items.size(), b->sm_count);
+    TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
+    e = launch_project_bwd_tc(bp, grid, P.bw_smem, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "project backward");
   return FMAP_OK;
 }
@@ -716,7 +823,8 @@ int32_t fmap_loss_orth(fmap_batch* b, const float* c, const float* c_gt, float* 
   cudaError_t e;
   {
     TimedScope ts(b, FMAP_KIND_LOSS, static_cast<cudaStream_t>(stream));
-    e = launch_loss_orth(b->dev, c, c_gt, loss, d_c, static_cast<float*>(ws), static_cast<cudaStream_t>(stream));
+    e = launch_loss_orth(b->dev, b->plan.max_k, c, c_gt, loss, d_c, static_cast<float*>(ws),
+                         static_cast<float*>(ws) + b->plan.loss_part_off, static_cast<cudaStream_t>(stream));
   }
   if (e != cudaSuccess) return cuda_fail(e, "loss");
   return FMAP_OK;

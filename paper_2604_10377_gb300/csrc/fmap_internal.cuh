@@ -109,6 +109,37 @@ struct TcProjParams {
   int* err;                   // workspace error word
 };
 
+// Work item of the tensor-core backward projection: a vertex chunk of one feature
+// group (nf <= 128 features from f0) of one shape; kb = blocks of 32 basis functions.
+struct TcBwdItem {
+  int32_t shape, f0, nf, kb;
+  int64_t v0, v1;
+  int64_t img_off;     // float offset (workspace) of the group's dA^T image
+};
+
+struct TcBwdGroup {
+  int32_t shape, f0, nf, kb;
+  int64_t img_off;
+};
+
+struct TcBwdParams {
+  const ShapeDev* shapes;
+  const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 128, 128-byte swizzle
+  const TcBwdItem* items;
+  const int32_t* order;
+  int32_t n_items;
+  int32_t stages;
+  uint32_t b_bytes_max;
+  uint32_t tmem_cols;
+  const float* ws;
+  int* err;
+};
+
+cudaError_t project_bwd_tc_set_smem(int bytes);
+cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* groups, int n_groups, int max_elems,
+                                   const float* d_a, float* ws, cudaStream_t st);
+cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st);
+
 cudaError_t project_tc_set_smem(int bytes);
 int project_tc_threads();
 cudaError_t launch_project_tc(const TcProjParams& p, int grid, int smem_bytes, cudaStream_t st);
@@ -140,8 +171,8 @@ cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const 
 cudaError_t launch_gather_da(const BatchDev& b, int max_kd, float* d_a, const float* ws, cudaStream_t st);
 cudaError_t launch_project_bwd_simt(const BatchDev& b, const BwdTile* tiles, int ntiles, const float* d_a,
                                     cudaStream_t st);
-cudaError_t launch_loss_orth(const BatchDev& b, const float* c, const float* c_gt, float* loss, float* d_c,
-                             float* ws, cudaStream_t st);
+cudaError_t launch_loss_orth(const BatchDev& b, int max_k, const float* c, const float* c_gt, float* loss,
+                             float* d_c, float* ws, float* partial, cudaStream_t st);
 cudaError_t launch_status_clear(int32_t* status, int n, cudaStream_t st);
 cudaError_t solve_set_smem_limits();
 int64_t chol_factor_floats(int k);   // saved factor size of one row system (padded packed rows)

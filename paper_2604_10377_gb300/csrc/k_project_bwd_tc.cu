@@ -1,0 +1,260 @@
+// Backward spectral projection on the tensor cores (chain rule of Eq. 1), BF16 features:
+//
+//   dF_s (n x d) = diag(M_s) Phi_s (n x k) . dA_s (k x d)
+//
+// kind::tf32 MMA, M = 128 vertices, N = one feature group (<= 128 features),
+// K = the basis index in blocks of 32. Phi is read straight from HBM by TMA as
+// FP32 tiles (K-major, 128-byte swizzle); the B operand is dA_s^T of the feature
+// group, prepared once per backward pass as a K-major swizzled FP32 image in the
+// workspace and bulk-copied into shared memory per work item. The mass is a
+// per-row (per-TMEM-lane) scale applied in the epilogue, which converts to BF16
+// and writes dF. TF32 keeps ~2^-11 relative accuracy of each operand, far inside
+// the BF16 storage of dF. Accumulators are double-buffered in TMEM so that the
+// epilogue of one vertex tile overlaps the MMAs of the next.
+//
+// Waits are bounded like the forward kernel's; a timeout sets the workspace
+// control word to FMAP_ERR_TIMEOUT.
+#include "fmap_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fmap {
+namespace {
+
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kTileV = 128;                       // vertices per output tile (MMA M)
+constexpr uint32_t kAStageBytes = kTileV * 128;   // 128 rows x 32 fp32
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(tc::smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// kind::tf32, FP32 accumulation, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = P.stages;
+  uint8_t* sB = smem;                                   // resident dA^T image
+  uint8_t* sA = sB + P.b_bytes_max;                     // Phi tiles, S stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * kAStageBytes);
+  uint64_t* a_full = bars;
+  uint64_t* a_empty = bars + S;
+  uint64_t* b_full = bars + 2 * S;
+  uint64_t* b_empty = b_full + 1;
+  uint64_t* acc_full = b_empty + 1;      // [2]
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&a_full[s], 1);
+      tc::mbar_init(&a_empty[s], 1);
+    }
+    tc::mbar_init(b_full, 1);
+    tc::mbar_init(b_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kEpiWarps);
+    }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, P.tmem_cols);
+    tc::tmem_relinquish();
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer (Phi tiles, dA^T image)
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, bphase = 0;
+      for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+        const TcBwdItem item = P.items[P.order[it]];
+        const CUtensorMap* map = P.phimaps + item.shape;
+        tc::prefetch_tmap(map);
+        if (!tc::mbar_wait(b_empty, bphase ^ 1, abort_flag)) goto producer_done;
+        const uint32_t bbytes = (uint32_t)item.kb * (uint32_t)item.nf * 128u;
+        tc::mbar_arrive_expect_tx(b_full, bbytes);
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(P.ws + item.img_off);
+        for (uint32_t off = 0; off < bbytes; off += 16384u)
+          bulk_g2s(sB + off, src + off, (bbytes - off) < 16384u ? (bbytes - off) : 16384u, b_full);
+        bphase ^= 1;
+        const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
+        for (int t = 0; t < ntiles; ++t) {
+          const int y = (int)(item.v0 + (int64_t)t * kTileV);
+          for (int kb = 0; kb < item.kb; ++kb) {
+            if (!tc::mbar_wait(&a_empty[stage], phase ^ 1, abort_flag)) goto producer_done;
+            tc::mbar_arrive_expect_tx(&a_full[stage], kAStageBytes);
+            tc::tma_load_2d(sA + (size_t)stage * kAStageBytes, map, &a_full[stage], kb * 32, y);
+            if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
+          }
+        }
+      }
+    producer_done:
+      if (*abort_flag) {
+        const uint64_t t0 = tc::globaltimer();
+        while (tc::globaltimer() - t0 < 2000000ull) {}
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, bphase = 0;
+      uint32_t acc_phase[2] = {0, 0};
+      int buf = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < P.n_items && ok; it += gridDim.x) {
+        const TcBwdItem item = P.items[P.order[it]];
+        if (!tc::mbar_wait(b_full, bphase, abort_flag)) break;
+        bphase ^= 1;
+        tc::tc_fence_after();
+        const uint32_t idesc = idesc_tf32(128, (uint32_t)item.nf);
+        const uint32_t b_base = tc::smem_u32(sB);
+        const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
+        for (int t = 0; t < ntiles && ok; ++t) {
+          if (!tc::mbar_wait(&acc_empty[buf], acc_phase[buf] ^ 1, abort_flag)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(buf * 128);
+          for (int kb = 0; kb < item.kb; ++kb) {
+            if (!tc::mbar_wait(&a_full[stage], phase, abort_flag)) { ok = false; break; }
+            tc::tc_fence_after();
+            const uint32_t a_base = tc::smem_u32(sA + (size_t)stage * kAStageBytes);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t ad = tc::smem_desc(a_base + ks * 32, 16, 1024, tc::kLayoutSW128);
+              const uint64_t bd = tc::smem_desc(b_base + (uint32_t)(kb * item.nf * 128) + ks * 32, 16, 1024,
+                                                tc::kLayoutSW128);
+              mma_tf32(d, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&a_empty[stage]);
+            if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          tc::mma_commit(&acc_full[buf]);
+          acc_phase[buf] ^= 1;
+          buf ^= 1;
+        }
+        if (!ok) break;
+        tc::mma_commit(b_empty);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue: TMEM -> M * acc -> BF16 dF
+    const int quarter = warp & 3;
+    uint32_t acc_phase[2] = {0, 0};
+    int buf = 0;
+    for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+      const TcBwdItem item = P.items[P.order[it]];
+      const ShapeDev s = P.shapes[item.shape];
+      __nv_bfloat16* df = reinterpret_cast<__nv_bfloat16*>(s.dfeat);
+      const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
+      for (int t = 0; t < ntiles; ++t) {
+        if (!tc::mbar_wait(&acc_full[buf], acc_phase[buf], abort_flag)) goto epi_done;
+        tc::tc_fence_after();
+        const int64_t v = item.v0 + (int64_t)t * kTileV + quarter * 32 + lane;
+        const bool vok = v < item.v1;
+        const float m = vok ? __ldg(s.mass + v) : 0.f;
+        for (int ch = 0; ch < item.nf / 16; ++ch) {
+          float x[16];
+          tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + ch * 16), x);
+          if (vok) {
+            uint4 w0, w1;
+            w0.x = __bfloat16_as_ushort(__float2bfloat16_rn(x[0] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[1] * m)) << 16);
+            w0.y = __bfloat16_as_ushort(__float2bfloat16_rn(x[2] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[3] * m)) << 16);
+            w0.z = __bfloat16_as_ushort(__float2bfloat16_rn(x[4] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[5] * m)) << 16);
+            w0.w = __bfloat16_as_ushort(__float2bfloat16_rn(x[6] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[7] * m)) << 16);
+            w1.x = __bfloat16_as_ushort(__float2bfloat16_rn(x[8] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[9] * m)) << 16);
+            w1.y = __bfloat16_as_ushort(__float2bfloat16_rn(x[10] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[11] * m)) << 16);
+            w1.z = __bfloat16_as_ushort(__float2bfloat16_rn(x[12] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[13] * m)) << 16);
+            w1.w = __bfloat16_as_ushort(__float2bfloat16_rn(x[14] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[15] * m)) << 16);
+            uint4* dst = reinterpret_cast<uint4*>(df + v * s.ld_feat + item.f0 + ch * 16);
+            dst[0] = w0;
+            dst[1] = w1;
+          }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+        acc_phase[buf] ^= 1;
+        buf ^= 1;
+      }
+    }
+  epi_done:;
+  }
+
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem_base, P.tmem_cols);
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(P.err, (int)FMAP_ERR_TIMEOUT);
+}
+
+// dA_s^T of one feature group as the K-major, 128-byte-swizzled FP32 image the MMA
+// reads: block kb (basis 32kb..32kb+31) holds nf rows of 128 bytes (one feature per
+// row), 16-byte chunk c of row f stored at chunk c ^ (f & 7).
+__global__ void build_dat_image_kernel(const ShapeDev* shapes, const TcBwdGroup* groups, const float* d_a,
+                                       float* ws) {
+  const TcBwdGroup g = groups[blockIdx.y];
+  const ShapeDev s = shapes[g.shape];
+  const int total = g.kb * g.nf * 32;
+  float* img = ws + g.img_off;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int kb = e / (g.nf * 32);
+    const int rem = e % (g.nf * 32);
+    const int f = rem / 32, nl = rem % 32;
+    const int n = kb * 32 + nl, fg = g.f0 + f;
+    const float val = (n < s.k && fg < s.d) ? d_a[s.a_off + (int64_t)n * s.d + fg] : 0.f;
+    const int chunk = nl >> 2;
+    img[(int64_t)kb * g.nf * 32 + f * 32 + ((chunk ^ (f & 7)) << 2) + (nl & 3)] = val;
+  }
+}
+
+}  // namespace
+
+cudaError_t project_bwd_tc_set_smem(int bytes) {
+  return cudaFuncSetAttribute(project_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* groups, int n_groups, int max_elems,
+                                   const float* d_a, float* ws, cudaStream_t st) {
+  if (n_groups <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::max(1, std::min((max_elems + 255) / 256, 1024)), (unsigned)n_groups);
+  build_dat_image_kernel<<<grid, 256, 0, st>>>(shapes, groups, d_a, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st) {
+  if (p.n_items <= 0) return cudaSuccess;
+  project_bwd_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace fmap

@@ -187,42 +187,127 @@ __global__ void gather_da_kernel(BatchDev b, float* d_a, const float* ws) {
   }
 }
 
-// Loss ||C C^T - I||^2 + ||C - C_gt||^2 and dL/dC = 4 (C C^T - I) C + 2 (C - C_gt); one block per pair.
-__global__ void __launch_bounds__(256) loss_orth_kernel(BatchDev b, const float* c_flat, const float* gt_flat,
-                                                        float* loss, float* d_c, float* ws) {
+// Training loss ||C C^T - I||^2 + ||C - C_gt||^2 and dL/dC = 4 (C C^T - I) C + 2 (C - C_gt),
+// as two tiled passes over (64 x 64 output tile, pair):
+//   pass 1: E = C C^T - I (into the workspace) and per-tile partial sums of the loss;
+//   pass 2: dC = 4 E C + 2 (C - C_gt); tile 0 of each pair adds the partials in order.
+constexpr int kMaxLossTiles = 16;   // (256 / 64)^2
+
+__global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_flat, const float* gt_flat,
+                                                      float* ws, float* partial) {
+  __shared__ float sX[kTile][kStage + 1];   // C[a][m]
+  __shared__ float sY[kStage][kTile + 4];   // C^T[m][b] = C[b][m]
   __shared__ float red[256];
-  const int p = blockIdx.x;
+  const int p = blockIdx.z;
   const PairDev pd = b.pairs[p];
   const int k = pd.k;
+  const int nt = (k + kTile - 1) / kTile;
+  if ((int)blockIdx.x >= nt * nt) return;
+  const int a0 = (blockIdx.x / nt) * kTile, b0 = (blockIdx.x % nt) * kTile;
   const float* c = c_flat + pd.c_off;
   const float* gt = gt_flat + pd.c_off;
   float* e = ws + pd.e_off;
-  float acc = 0.f;
-  for (int idx = threadIdx.x; idx < k * k; idx += 256) {
-    const int a = idx / k, bb = idx % k;
-    const float* ca = c + (int64_t)a * k;
-    const float* cb = c + (int64_t)bb * k;
-    float s = 0.f;
-    for (int l = 0; l < k; ++l) s = fmaf(ca[l], cb[l], s);
-    if (a == bb) s -= 1.f;
-    e[idx] = s;
-    const float r = c[idx] - gt[idx];
-    acc = fmaf(s, s, fmaf(r, r, acc));
-  }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  for (int m0 = 0; m0 < k; m0 += kStage) {
+    for (int q = tid; q < kTile * kStage; q += 256) {
+      const int r = q / kStage, mm = q % kStage;
+      sX[r][mm] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+    }
+    for (int q = tid; q < kStage * kTile; q += 256) {
+      const int mm = q / kTile, r = q % kTile;
+      sY[mm][r] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mm = 0; mm < kStage; ++mm) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float xa = sX[ty * 4 + i][mm];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa, sY[mm][tx * 4 + j], acc[i][j]);
+      }
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && loss) loss[p] = red[0];
+  float part = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i;
+    if (a >= k) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int bb = b0 + tx * 4 + j;
+      if (bb >= k) continue;
+      const float v = acc[i][j] - (a == bb ? 1.f : 0.f);
+      e[(int64_t)a * k + bb] = v;
+      const float r = c[(int64_t)a * k + bb] - gt[(int64_t)a * k + bb];
+      part = fmaf(v, v, fmaf(r, r, part));
+    }
+  }
+  red[tid] = part;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st) red[tid] += red[tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) partial[(int64_t)p * kMaxLossTiles + blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float* c_flat, const float* gt_flat,
+                                                         float* loss, float* d_c, const float* ws,
+                                                         const float* partial) {
+  __shared__ float sX[kTile][kStage + 1];   // E[a][m]
+  __shared__ float sY[kStage][kTile + 4];   // C[m][b]
+  const int p = blockIdx.z;
+  const PairDev pd = b.pairs[p];
+  const int k = pd.k;
+  const int nt = (k + kTile - 1) / kTile;
+  if ((int)blockIdx.x >= nt * nt) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
+    float total = 0.f;
+    for (int t = 0; t < nt * nt; ++t) total += partial[(int64_t)p * kMaxLossTiles + t];
+    loss[p] = total;
+  }
   if (d_c == nullptr) return;
-  for (int idx = threadIdx.x; idx < k * k; idx += 256) {
-    const int a = idx / k, bb = idx % k;
-    const float* ea = e + (int64_t)a * k;
-    float s = 0.f;
-    for (int l = 0; l < k; ++l) s = fmaf(ea[l], c[(int64_t)l * k + bb], s);
-    d_c[pd.c_off + idx] = 4.f * s + 2.f * (c[idx] - gt[idx]);
+  const int a0 = (blockIdx.x / nt) * kTile, b0 = (blockIdx.x % nt) * kTile;
+  const float* c = c_flat + pd.c_off;
+  const float* gt = gt_flat + pd.c_off;
+  const float* e = ws + pd.e_off;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  for (int m0 = 0; m0 < k; m0 += kStage) {
+    for (int q = tid; q < kTile * kStage; q += 256) {
+      const int r = q / kStage, mm = q % kStage;
+      sX[r][mm] = (a0 + r < k && m0 + mm < k) ? e[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+    }
+    for (int q = tid; q < kStage * kTile; q += 256) {
+      const int mm = q / kTile, r = q % kTile;
+      sY[mm][r] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(m0 + mm) * k + b0 + r] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mm = 0; mm < kStage; ++mm) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float xa = sX[ty * 4 + i][mm];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa, sY[mm][tx * 4 + j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i;
+    if (a >= k) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int bb = b0 + tx * 4 + j;
+      if (bb >= k) continue;
+      const int64_t idx = (int64_t)a * k + bb;
+      d_c[pd.c_off + idx] = 4.f * acc[i][j] + 2.f * (c[idx] - gt[idx]);
+    }
   }
 }
 
@@ -254,10 +339,14 @@ cudaError_t launch_gather_da(const BatchDev& b, int max_kd, float* d_a, const fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_loss_orth(const BatchDev& b, const float* c, const float* c_gt, float* loss, float* d_c, float* ws,
-                             cudaStream_t st) {
+cudaError_t launch_loss_orth(const BatchDev& b, int max_k, const float* c, const float* c_gt, float* loss,
+                             float* d_c, float* ws, float* partial, cudaStream_t st) {
   if (b.n_pairs <= 0) return cudaSuccess;
-  loss_orth_kernel<<<b.n_pairs, 256, 0, st>>>(b, c, c_gt, loss, d_c, ws);
+  const int nt = (max_k + kTile - 1) / kTile;
+  loss_e_kernel<<<dim3(nt * nt, 1, b.n_pairs), 256, 0, st>>>(b, c, c_gt, ws, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  loss_grad_kernel<<<dim3(nt * nt, 1, b.n_pairs), 256, 0, st>>>(b, c, c_gt, loss, d_c, ws, partial);
   return cudaGetLastError();
 }
 
