@@ -26,7 +26,9 @@ int32_t cuda_fail(cudaError_t e, const char* where) {
 constexpr int64_t kAlignFloats = 64;   // 256-byte alignment of workspace regions
 constexpr int64_t kChunkV = 4096;      // vertices per split-K chunk of the projection
 constexpr int kTile = 64;
-constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core projection
+constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core backward projection
+constexpr int kTcCtas = 152;           // persistent CTAs of the projection (one per GB300 SM)
+constexpr int64_t kStageV = 64;        // vertices per projection pipeline stage
 constexpr int kSmemBudget = 227 * 1024;
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -76,7 +78,7 @@ struct Plan {
   // tensor-core projection (BF16 features)
   bool tc = false;
   std::vector<TcItem> tc_items;
-  std::vector<int32_t> tc_order;
+  std::vector<int32_t> tc_cta_first;
   std::vector<TcRedGroup> tc_groups;
   int64_t tc_max_group_elems = 0;
   int tc_stages = 0, tc_smem = 0;
@@ -163,6 +165,11 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     }
   } else {
     uint32_t fmax = 0, pmax = 0, tmax = 0;
+    // (shape, feature group) units, then a stream-K split of their vertex ranges
+    // into kTcCtas ranges of equal cost (64-vertex granularity)
+    struct Unit { int s, f0, fg, npad, dspan; double cpv; };
+    std::vector<Unit> units;
+    double total = 0.0;
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
       const int npad = (sd.k + 15) / 16 * 16;
@@ -171,54 +178,62 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       const int groups = (mt + fg_cap - 1) / fg_cap;
       const int fg_s = (mt + groups - 1) / groups;
       for (int g = 0; g < groups; ++g) {
-        TcRedGroup rg{};
-        rg.shape = s;
-        rg.f0 = g * fg_s * 128;
-        const int fg = std::min(fg_s, mt - g * fg_s);
-        rg.stride = fg * 128;
-        rg.dspan = std::min(fg * 128, sd.d - rg.f0);
-        rg.it_beg = (int32_t)P.tc_items.size();
-        for (int64_t v0 = 0; v0 < sd.n; v0 += kTcChunkV) {
-          TcItem it{};
-          it.shape = s; it.f0 = rg.f0; it.fg = fg; it.npad = npad;
-          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + kTcChunkV);
-          it.part_off = cur;
-          cur = align_up(cur + (int64_t)sd.k * rg.stride, kAlignFloats);
-          P.tc_items.push_back(it);
-        }
-        rg.it_end = (int32_t)P.tc_items.size();
-        P.tc_groups.push_back(rg);
-        P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)sd.k * rg.dspan);
-        fmax = std::max<uint32_t>(fmax, (uint32_t)fg * 16384u);
-        pmax = std::max<uint32_t>(pmax, (uint32_t)npad * 128u);
-        tmax = std::max<uint32_t>(tmax, (uint32_t)(fg * npad));
+        Unit u;
+        u.s = s; u.f0 = g * fg_s * 128; u.fg = std::min(fg_s, mt - g * fg_s); u.npad = npad;
+        u.dspan = std::min(u.fg * 128, sd.d - u.f0);
+        u.cpv = 4.0 * sd.k + 4.0 + 2.0 * u.dspan;   // HBM bytes per vertex
+        units.push_back(u);
+        total += u.cpv * (double)sd.n;
+        fmax = std::max<uint32_t>(fmax, (uint32_t)u.fg * 16384u);
+        const uint32_t pb = std::max<uint32_t>((uint32_t)((npad + 31) / 32) * 8192u, (uint32_t)npad * 256u);
+        pmax = std::max<uint32_t>(pmax, pb);
+        tmax = std::max<uint32_t>(tmax, (uint32_t)(u.fg * npad));
       }
     }
-    // schedule: most expensive items first; items of one chunk (different feature
-    // groups) stay adjacent so that they run at the same time and share Phi in L2
-    P.tc_order.resize(P.tc_items.size());
-    for (size_t i = 0; i < P.tc_items.size(); ++i) P.tc_order[i] = (int32_t)i;
-    auto cost = [&](const TcItem& it) {
-      const ShapeDev& sd = P.shapes[it.shape];
-      return (double)(it.v1 - it.v0) * (4.0 * sd.k + 4.0 + 2.0 * it.fg * 128);
-    };
-    std::stable_sort(P.tc_order.begin(), P.tc_order.end(), [&](int32_t a, int32_t b) {
-      const TcItem &x = P.tc_items[a], &y = P.tc_items[b];
-      const double cx = cost(x), cy = cost(y);
-      if (cx != cy) return cx > cy;
-      if (x.shape != y.shape) return x.shape < y.shape;
-      if (x.v0 != y.v0) return x.v0 < y.v0;
-      return x.f0 < y.f0;
-    });
+    const double per_cta = total / kTcCtas;
+    int cta = 0;
+    double budget = per_cta;
+    P.tc_cta_first.assign(kTcCtas + 1, 0);
+    for (const Unit& u : units) {
+      const ShapeDev& sd = P.shapes[u.s];
+      TcRedGroup rg{};
+      rg.shape = u.s; rg.f0 = u.f0; rg.stride = u.fg * 128; rg.dspan = u.dspan;
+      rg.it_beg = (int32_t)P.tc_items.size();
+      int64_t v = 0;
+      while (v < sd.n) {
+        int64_t take = (int64_t)std::ceil(std::max(budget, 0.0) / u.cpv);
+        take = std::max<int64_t>(kStageV, (take + kStageV - 1) / kStageV * kStageV);
+        if (cta == kTcCtas - 1) take = sd.n - v;
+        take = std::min<int64_t>(take, sd.n - v);
+        TcItem it{};
+        it.shape = u.s; it.f0 = u.f0; it.fg = u.fg; it.npad = u.npad;
+        it.v0 = v; it.v1 = v + take;
+        it.part_off = cur;
+        cur = align_up(cur + (int64_t)sd.k * rg.stride, kAlignFloats);
+        P.tc_items.push_back(it);
+        v += take;
+        budget -= u.cpv * (double)take;
+        if (budget <= 0.0 && cta < kTcCtas - 1) {
+          ++cta;
+          P.tc_cta_first[cta] = (int32_t)P.tc_items.size();
+          budget += per_cta;
+        }
+      }
+      rg.it_end = (int32_t)P.tc_items.size();
+      P.tc_groups.push_back(rg);
+      P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)sd.k * rg.dspan);
+    }
+    for (int c = cta + 1; c <= kTcCtas; ++c) P.tc_cta_first[c] = (int32_t)P.tc_items.size();
     P.tc_f_stage = std::max<uint32_t>(fmax, 16384u);
-    P.tc_p_stage = std::max<uint32_t>(pmax, 2048u);
+    P.tc_p_stage = (std::max<uint32_t>(pmax, 8192u) + 1023u) / 1024u * 1024u;
     uint32_t cols = 32;
     while (cols < tmax) cols <<= 1;
     P.tc_tmem_cols = cols;
     const int fixed = 1024 + 512;
-    P.tc_stages = std::min(6, (int)((kSmemBudget - fixed) / (P.tc_f_stage + 2 * P.tc_p_stage)));
+    const int per_stage = (int)(P.tc_f_stage + P.tc_p_stage) + kStageV * 4;
+    P.tc_stages = std::min(6, (kSmemBudget - fixed) / per_stage);
     if (n_shapes > 0 && P.tc_stages < 2) return FMAP_ERR_UNSUPPORTED;
-    P.tc_smem = fixed + P.tc_stages * (int)(P.tc_f_stage + 2 * P.tc_p_stage);
+    P.tc_smem = fixed + P.tc_stages * per_stage;
   }
   for (auto& pd : P.pairs) {
     const int64_t kk = (int64_t)pd.k * pd.k;
@@ -388,9 +403,11 @@ struct fmap_batch {
   const int2* d_systems = nullptr;
   const CUtensorMap* d_fmaps = nullptr;
   const TcItem* d_tc_items = nullptr;
-  const int32_t* d_tc_order = nullptr;
+  const int32_t* d_tc_cta_first = nullptr;
   const TcRedGroup* d_tc_groups = nullptr;
   const CUtensorMap* d_phimaps = nullptr;
+  const CUtensorMap* d_phimaps_fwd = nullptr;
+  const CUtensorMap* d_massmaps = nullptr;
   const TcBwdItem* d_bw_items = nullptr;
   const int32_t* d_bw_order = nullptr;
   const TcBwdGroup* d_bw_groups = nullptr;
@@ -514,9 +531,11 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_tm = o_sy + bytes_of(P.systems.size(), sizeof(int2));
   const int64_t o_ti = o_tm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_to = o_ti + bytes_of(P.tc_items.size(), sizeof(TcItem));
-  const int64_t o_tg = o_to + bytes_of(P.tc_order.size(), sizeof(int32_t));
+  const int64_t o_tg = o_to + bytes_of(P.tc_cta_first.size(), sizeof(int32_t));
   const int64_t o_pm = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
-  const int64_t o_bi = o_pm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_fp = o_pm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_mm = o_fp + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_bi = o_mm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
   const int64_t o_bg = o_bo + bytes_of(P.bw_order.size(), sizeof(int32_t));
   const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
@@ -564,6 +583,32 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
         return FMAP_ERR_CUDA;
       }
       put(o_pm + s * (int64_t)sizeof(CUtensorMap), &pm, sizeof(pm));
+      // FP32 basis for the forward projection: box 32 basis x 64 vertices
+      cuuint32_t fbox[2] = {32, 64};
+      r = encode(&pm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sd.phi), pdim, pstride, fbox, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        cudaFree(b->dev_mem); delete b;
+        std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled(phi fwd) failed (%d)", (int)r);
+        return FMAP_ERR_CUDA;
+      }
+      put(o_fp + s * (int64_t)sizeof(CUtensorMap), &pm, sizeof(pm));
+      // mass: 1-D, box of 64
+      CUtensorMap mm;
+      cuuint64_t mdim[1] = {(cuuint64_t)sd.n};
+      cuuint64_t mstride[1] = {4};
+      cuuint32_t mbox[1] = {64};
+      cuuint32_t mestr[1] = {1};
+      r = encode(&mm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(sd.mass), mdim, mstride, mbox, mestr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        cudaFree(b->dev_mem); delete b;
+        std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled(mass) failed (%d)", (int)r);
+        return FMAP_ERR_CUDA;
+      }
+      put(o_mm + s * (int64_t)sizeof(CUtensorMap), &mm, sizeof(mm));
     }
     put(o_bi, P.bw_items.data(), P.bw_items.size() * sizeof(TcBwdItem));
     put(o_bo, P.bw_order.data(), P.bw_order.size() * sizeof(int32_t));
@@ -573,7 +618,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
       if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project bwd)"); }
     }
     put(o_ti, P.tc_items.data(), P.tc_items.size() * sizeof(TcItem));
-    put(o_to, P.tc_order.data(), P.tc_order.size() * sizeof(int32_t));
+    put(o_to, P.tc_cta_first.data(), P.tc_cta_first.size() * sizeof(int32_t));
     put(o_tg, P.tc_groups.data(), P.tc_groups.size() * sizeof(TcRedGroup));
     e = project_tc_set_smem(P.tc_smem);
     if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project)"); }
@@ -595,9 +640,11 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_systems = reinterpret_cast<const int2*>(base + o_sy);
   b->d_fmaps = reinterpret_cast<const CUtensorMap*>(base + o_tm);
   b->d_tc_items = reinterpret_cast<const TcItem*>(base + o_ti);
-  b->d_tc_order = reinterpret_cast<const int32_t*>(base + o_to);
+  b->d_tc_cta_first = reinterpret_cast<const int32_t*>(base + o_to);
   b->d_tc_groups = reinterpret_cast<const TcRedGroup*>(base + o_tg);
   b->d_phimaps = reinterpret_cast<const CUtensorMap*>(base + o_pm);
+  b->d_phimaps_fwd = reinterpret_cast<const CUtensorMap*>(base + o_fp);
+  b->d_massmaps = reinterpret_cast<const CUtensorMap*>(base + o_mm);
   b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
   b->d_bw_order = reinterpret_cast<const int32_t*>(base + o_bo);
   b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
@@ -677,16 +724,17 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
     TcProjParams tp{};
     tp.shapes = b->dev.shapes;
     tp.fmaps = b->d_fmaps;
+    tp.phimaps = b->d_phimaps_fwd;
+    tp.massmaps = b->d_massmaps;
     tp.items = b->d_tc_items;
-    tp.order = b->d_tc_order;
-    tp.n_items = (int32_t)P.tc_items.size();
+    tp.cta_first = b->d_tc_cta_first;
     tp.stages = P.tc_stages;
     tp.f_stage_bytes = P.tc_f_stage;
     tp.p_stage_bytes = P.tc_p_stage;
     tp.tmem_cols = P.tc_tmem_cols;
     tp.ws = w;
     tp.err = static_cast<int*>(ws);
-    const int grid = (int)std::min<int64_t>((int64_t)P.tc_items.size(), b->sm_count);
+    const int grid = P.tc_items.empty() ? 0 : kTcCtas;
     {
       TimedScope ts(b, FMAP_KIND_PROJECT, st);
       e = launch_project_tc(tp, grid, P.tc_smem, st);

@@ -81,12 +81,12 @@ struct BatchDev {
 
 __host__ __device__ inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
 
-// Work item of the tensor-core projection: one vertex chunk of one feature group
+// Segment of the tensor-core projection: a vertex range of one feature group
 // (fg M-tiles of 128 features starting at feature f0) of one shape.
 struct TcItem {
   int32_t shape, f0, fg, npad;
   int64_t v0, v1;
-  int64_t part_off;    // float offset (workspace) of the item's partial, k x (fg*128)
+  int64_t part_off;    // float offset (workspace) of the segment's partial, k x (fg*128)
 };
 
 // Items [it_beg, it_end) hold the partials of features f0 .. f0+dspan of one shape.
@@ -97,10 +97,11 @@ struct TcRedGroup {
 
 struct TcProjParams {
   const ShapeDev* shapes;
-  const CUtensorMap* fmaps;   // per shape: BF16 features, box 64 x 64, 128-byte swizzle
-  const TcItem* items;
-  const int32_t* order;       // schedule: item indices, most expensive first
-  int32_t n_items;
+  const CUtensorMap* fmaps;     // per shape: BF16 features, box 64 features x 64 vertices, 128-byte swizzle
+  const CUtensorMap* phimaps;   // per shape: FP32 basis, box 32 basis x 64 vertices, 128-byte swizzle
+  const CUtensorMap* massmaps;  // per shape: FP32 mass, 1-D box of 64
+  const TcItem* items;          // segments, grouped by CTA
+  const int32_t* cta_first;     // CTA c owns segments [cta_first[c], cta_first[c + 1])
   int32_t stages;
   uint32_t f_stage_bytes;
   uint32_t p_stage_bytes;

@@ -2,16 +2,20 @@
 //
 //   A_s^T (d x k) = F_s^T (d x n) . P_s (n x k),   P_s = diag(M_s) Phi_s
 //
-// One persistent CTA per SM walks a list of work items (shape, feature group,
-// vertex chunk). Per 64-vertex stage:
-//   warp 0      TMA-loads the F tile (MN-major, 128-byte swizzle) straight from HBM;
-//   warps 2-9   read Phi and M, form P = M * Phi in FP32 and split it into
-//               BF16 hi + lo (P = hi + lo to ~2^-17), written as K-major
-//               128-byte-swizzled B tiles: the mass is fused into the operand load;
+// One persistent CTA per SM walks its own contiguous range of the batch's
+// (shape, feature group) vertex sequence (stream-K split into equal-cost
+// ranges); a range is cut into segments at shape / group boundaries and every
+// segment writes one partial A. Per 64-vertex stage:
+//   warp 0      TMA-loads the F tile (MN-major, 128-byte swizzle), the Phi tile
+//               (FP32, 32-column boxes, 128-byte swizzle) and the 64 masses;
+//   warps 2-9   read Phi and M from shared memory, form P = M * Phi in FP32 and
+//               split it into BF16 hi + lo (P = hi + lo to ~2^-17), written in place
+//               over the Phi tile as K-major 128-byte-swizzled B tiles: the mass is
+//               fused into the operand load;
 //   warp 1      issues tcgen05.mma (M = 128 features, N = k rounded up to 16,
 //               K = 16 vertices) for hi and lo into FP32 accumulators in TMEM.
-// At the end of an item warps 2-9 read the accumulators back (tcgen05.ld) and
-// write the item's partial A; a second kernel adds the partials of each shape
+// At the end of a segment warps 2-9 read the accumulators back (tcgen05.ld) and
+// write the segment's partial A; a second kernel adds the partials of each shape
 // in a fixed order. F is exact in BF16, so A carries only the ~2^-17 error of
 // the hi/lo split and FP32 accumulation.
 //
@@ -28,6 +32,11 @@ constexpr int kConvWarps = 8;
 constexpr int kThreads = 32 * (2 + kConvWarps);
 constexpr int kStageV = 64;            // vertices per pipeline stage (= one 128-byte K row of bf16)
 constexpr uint32_t kBoxBytes = 64 * 64 * 2;   // one TMA box: 64 vertices x 64 features bf16
+constexpr uint32_t kPhiBoxBytes = 64 * 128;    // one TMA box: 64 vertices x 32 basis functions fp32
+
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
@@ -45,9 +54,9 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = P.stages;
   uint8_t* sF = smem;
-  uint8_t* sPh = sF + (size_t)S * P.f_stage_bytes;
-  uint8_t* sPl = sPh + (size_t)S * P.p_stage_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sPl + (size_t)S * P.p_stage_bytes);
+  uint8_t* sP = sF + (size_t)S * P.f_stage_bytes;       // Phi tile, converted in place into P hi / lo
+  float* sM = reinterpret_cast<float*>(sP + (size_t)S * P.p_stage_bytes);   // 64 masses per stage
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sM + (size_t)S * kStageV);
   uint64_t* full_f = bars;
   uint64_t* full_p = bars + S;
   uint64_t* empty = bars + 2 * S;
@@ -81,19 +90,28 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       uint32_t stage = 0, phase = 0;
-      for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-        const TcItem item = P.items[P.order[it]];
-        const CUtensorMap* map = P.fmaps + item.shape;
-        tc::prefetch_tmap(map);
+      for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
+        const TcItem item = P.items[it];
+        const CUtensorMap* fmap = P.fmaps + item.shape;
+        const CUtensorMap* pmap = P.phimaps + item.shape;
+        const CUtensorMap* mmap = P.massmaps + item.shape;
+        tc::prefetch_tmap(fmap);
+        tc::prefetch_tmap(pmap);
+        tc::prefetch_tmap(mmap);
         const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
+        const int kb = (item.npad + 31) / 32;
+        const uint32_t bytes = (uint32_t)item.fg * 2 * kBoxBytes + (uint32_t)kb * kPhiBoxBytes + kStageV * 4;
         for (int st = 0; st < nst; ++st) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag)) goto producer_done;
-          tc::mbar_arrive_expect_tx(&full_f[stage], (uint32_t)item.fg * 2 * kBoxBytes);
+          tc::mbar_arrive_expect_tx(&full_f[stage], bytes);
           uint8_t* dst = sF + (size_t)stage * P.f_stage_bytes;
+          uint8_t* pdst = sP + (size_t)stage * P.p_stage_bytes;
           const int y = (int)(item.v0 + (int64_t)st * kStageV);
           for (int m = 0; m < item.fg; ++m)
             for (int h = 0; h < 2; ++h)
-              tc::tma_load_2d(dst + (m * 2 + h) * kBoxBytes, map, &full_f[stage], item.f0 + m * 128 + h * 64, y);
+              tc::tma_load_2d(dst + (m * 2 + h) * kBoxBytes, fmap, &full_f[stage], item.f0 + m * 128 + h * 64, y);
+          for (int b = 0; b < kb; ++b) tc::tma_load_2d(pdst + b * kPhiBoxBytes, pmap, &full_f[stage], b * 32, y);
+          tc::tma_load_1d(sM + (size_t)stage * kStageV, mmap, &full_f[stage], y);
           if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
         }
       }
@@ -108,8 +126,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t stage = 0, phase = 0, acc_phase = 0;
-      for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-        const TcItem item = P.items[P.order[it]];
+      for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
+        const TcItem item = P.items[it];
         if (!tc::mbar_wait(acc_empty, acc_phase ^ 1, abort_flag)) break;
         tc::tc_fence_after();
         const uint32_t idesc = tc::idesc_bf16_f32(128, (uint32_t)item.npad, 1, 0);
@@ -120,8 +138,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
           if (!ok) break;
           tc::tc_fence_after();
           const uint32_t a_base = tc::smem_u32(sF + (size_t)stage * P.f_stage_bytes);
-          const uint32_t ph = tc::smem_u32(sPh + (size_t)stage * P.p_stage_bytes);
-          const uint32_t pl = tc::smem_u32(sPl + (size_t)stage * P.p_stage_bytes);
+          const uint32_t ph = tc::smem_u32(sP + (size_t)stage * P.p_stage_bytes);
+          const uint32_t pl = ph + (uint32_t)item.npad * 128u;
 #pragma unroll
           for (int kk = 0; kk < kStageV / 16; ++kk) {
             const uint64_t bh = tc::smem_desc(ph + kk * 32, 16, 1024, tc::kLayoutSW128);
@@ -145,49 +163,69 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
   } else {
     // ------------------------------------------------------------ converters + epilogue
     const int cw = warp - 2;
+    const int qs = lane & 7, csub = lane >> 3;
     uint32_t stage = 0, phase = 0, acc_phase = 0;
-    for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-      const TcItem item = P.items[P.order[it]];
+    for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
+      const TcItem item = P.items[it];
       const ShapeDev s = P.shapes[item.shape];
       const int k = s.k;
       const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
-      const int nqb = item.npad / 16;
-      const int c = lane & 7;
+      const int kb = (item.npad + 31) / 32;
       for (int st = 0; st < nst; ++st) {
-        if (!tc::mbar_wait(&empty[stage], phase ^ 1, abort_flag)) goto conv_done;
-        uint8_t* th = sPh + (size_t)stage * P.p_stage_bytes;
-        uint8_t* tl = sPl + (size_t)stage * P.p_stage_bytes;
-        const int64_t vb = item.v0 + (int64_t)st * kStageV + 8 * c;
-        for (int qb = cw; qb < nqb; qb += kConvWarps) {
-          const int n0 = 4 * (qb * 4 + (lane >> 3));
-          float p[8][4];
+        if (!tc::mbar_wait(&full_f[stage], phase, abort_flag)) goto conv_done;
+        uint8_t* tile = sP + (size_t)stage * P.p_stage_bytes;
+        const float* mst = sM + (size_t)stage * kStageV;
+        const int64_t vbase = item.v0 + (int64_t)st * kStageV;
+        // read phase: unit (box b, row group c = 4 cg + csub, quad qs) = rows 8c..8c+7 x basis 32b+4qs..+3
+        float4 x[2][8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int64_t v = vb + i;
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            float m = 0.f;
-            if (v < item.v1) {
-              m = __ldg(s.mass + v);
-              if (n0 < k) x = __ldg(reinterpret_cast<const float4*>(s.phi + v * s.ld_phi + n0));
+        for (int r = 0; r < 2; ++r) {
+          const int wu = cw + kConvWarps * r;
+          if (wu < 2 * kb) {
+            const int b = wu >> 1, c = 4 * (wu & 1) + csub;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int vl = 8 * c + i;
+              x[r][i] = *reinterpret_cast<const float4*>(tile + b * kPhiBoxBytes + vl * 128 + ((qs ^ (vl & 7)) << 4));
             }
-            p[i][0] = (n0 + 0 < k) ? x.x * m : 0.f;
-            p[i][1] = (n0 + 1 < k) ? x.y * m : 0.f;
-            p[i][2] = (n0 + 2 < k) ? x.z * m : 0.f;
-            p[i][3] = (n0 + 3 < k) ? x.w * m : 0.f;
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int n = n0 + j;
-            uint4 hv, lv;
-            split_pair(p[0][j], p[1][j], hv.x, lv.x);
-            split_pair(p[2][j], p[3][j], hv.y, lv.y);
-            split_pair(p[4][j], p[5][j], hv.z, lv.z);
-            split_pair(p[6][j], p[7][j], hv.w, lv.w);
-            const uint32_t off = (uint32_t)n * 128u + ((uint32_t)(c ^ (n & 7)) << 4);
-            *reinterpret_cast<uint4*>(th + off) = hv;
-            *reinterpret_cast<uint4*>(tl + off) = lv;
           }
         }
+        named_barrier_sync(1, 32 * kConvWarps);
+        // write phase: P hi at [0, npad*128), lo at [npad*128, 2*npad*128), K-major, 128-byte swizzle
+        uint8_t* th = tile;
+        uint8_t* tl = tile + (size_t)item.npad * 128;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int wu = cw + kConvWarps * r;
+          if (wu < 2 * kb) {
+            const int b = wu >> 1, c = 4 * (wu & 1) + csub;
+            float mv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) mv[i] = (vbase + 8 * c + i < item.v1) ? mst[8 * c + i] : 0.f;
+            const int n0 = 32 * b + 4 * qs;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int n = n0 + j;
+              if (n >= item.npad) continue;
+              float pv[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float4 q = x[r][i];
+                const float xv = j == 0 ? q.x : (j == 1 ? q.y : (j == 2 ? q.z : q.w));
+                pv[i] = xv * mv[i];
+              }
+              uint4 hv, lv;
+              split_pair(pv[0], pv[1], hv.x, lv.x);
+              split_pair(pv[2], pv[3], hv.y, lv.y);
+              split_pair(pv[4], pv[5], hv.z, lv.z);
+              split_pair(pv[6], pv[7], hv.w, lv.w);
+              const uint32_t off = (uint32_t)n * 128u + ((uint32_t)(c ^ (n & 7)) << 4);
+              *reinterpret_cast<uint4*>(th + off) = hv;
+              *reinterpret_cast<uint4*>(tl + off) = lv;
+            }
+          }
+        }
+        (void)k;
         tc::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&full_p[stage]);
@@ -252,7 +290,7 @@ cudaError_t project_tc_set_smem(int bytes) {
 int project_tc_threads() { return kThreads; }
 
 cudaError_t launch_project_tc(const TcProjParams& p, int grid, int smem_bytes, cudaStream_t st) {
-  if (p.n_items <= 0) return cudaSuccess;
+  if (grid <= 0) return cudaSuccess;
   project_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
   return cudaGetLastError();
 }
