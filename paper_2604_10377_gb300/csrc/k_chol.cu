@@ -2,17 +2,21 @@
 //
 // One thread block per row system S_i = G + lambda diag(D_i) (row i of pair p).
 // S_i is padded to kp = k rounded up to 8 (identity in the padding) and kept in
-// shared memory as packed lower rows, row a padded to a multiple of 8 entries, so
-// every 8 x 8 tile row segment is two aligned float4. The factorisation is a
-// blocked right-looking Cholesky in FP32 with 8-column panels:
-//   1. warp 0 factors the 8 x 8 diagonal block with shuffles;
-//   2. every thread solves one row of the panel below it (L_aJ = S_aJ L_JJ^-T);
-//   3. every thread updates 8 x 8 register tiles of the trailing matrix,
-//      S_AB -= L_AJ L_BJ^T, reading the panel from a column-major buffer.
+// shared memory as packed lower rows: row a holds 8 (a/8 + 1) + 4 floats, so a
+// row's 8-column tile segment is two aligned float4 and consecutive rows fall on
+// different banks. The factorisation is a blocked right-looking Cholesky in FP32
+// with 8-column panels and one panel of lookahead:
+//   TRSM     every thread solves one row of panel J below its diagonal block,
+//            x = s L_JJ^-T, as a product with the stored inverse block;
+//   (a)      every thread updates one row of the next column block J+1;
+//   (b)      warp 0 factors the diagonal block J+1 in registers and stores its
+//            inverse, while the other warps update the rest of the trailing matrix
+//            in 8 x 8 register tiles, S_AB -= L_AJ L_BJ^T.
 // Three block barriers per panel. Forward and back substitution are done by
-// warp 0 in 8-row blocks; then `ir_steps` steps of iterative refinement with
-// the residual rhs - S x accumulated in FP32, or in double-float (error-free
-// products and sums, ~48 bits) from the (hi, lo) Gram for hi_gram pairs.
+// warp 0 with the inverse diagonal blocks (no dependency chain inside a block);
+// then `ir_steps` steps of iterative refinement with the residual rhs - S x
+// accumulated in FP32, or in double-float (error-free products and sums,
+// ~48 bits) from the (hi, lo) Gram for hi_gram pairs.
 #include <math.h>
 
 #include "fmap_internal.cuh"
@@ -20,10 +24,14 @@
 namespace fmap {
 namespace {
 
+// Offset of row a in the packed, skewed lower storage.
 __host__ __device__ __forceinline__ int rowoff(int a) {
   const int q = a >> 3, s = a & 7;
-  return 8 * (q + 1) * (4 * q + s);
+  return 32 * q * (q + 2) + s * (8 * q + 12);
 }
+
+// Floats of one factor: the packed rows plus the Q inverse diagonal blocks.
+__host__ __device__ __forceinline__ int factor_floats(int Q) { return 32 * Q * (Q + 2) + 64 * Q; }
 
 __device__ __forceinline__ float mask_entry(const PairDev& pd, const float* evx, const float* evy, int i, int a) {
   if (pd.mask) return pd.mask[(int64_t)i * pd.k + a];
@@ -46,55 +54,104 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
   lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
 
-// Warp 0: in-place solve of L L^T v = v (L packed in S, kp = 8 Q).
-__device__ __forceinline__ void warp_subst(const float* S, float* v, int Q, int lane) {
-  for (int J = 0; J < Q; ++J) {                 // L y = v
-    const int r0 = 8 * J;
-    float yv = lane < 8 ? v[r0 + lane] : 0.f;
-    const float* row = S + rowoff(r0 + (lane & 7));
+// Warp 0: factor the 8 x 8 diagonal block J in place (lane 0, registers) and store
+// its inverse (lanes 0-7, one column each). Returns false on a bad pivot.
+__device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lane) {
+  const int r0 = 8 * J;
+  bool bad = false;
+  if (lane == 0) {
+    float a[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) a[i][j] = S[rowoff(r0 + i) + r0 + j];
+    float rinv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      if (lane == j) yv = yv / row[r0 + j];
-      const float yj = __shfl_sync(0xffffffffu, yv, j);
-      if (lane > j && lane < 8) yv = fmaf(-row[r0 + j], yj, yv);
+      const float piv = a[j][j];
+      if (!(piv > 0.f) || !(piv < INFINITY)) bad = true;
+      const float r = rsqrtf(piv);     // 1 / L_jj; iterative refinement absorbs its last-bit error
+      a[j][j] = piv * r;
+      rinv[j] = r;
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i) a[i][j] *= r;
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+        for (int m = j + 1; m <= i; ++m) a[i][m] = fmaf(-a[i][j], a[m][j], a[i][m]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) S[rowoff(r0 + i) + r0 + j] = a[i][j];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) linv[J * 64 + j * 9] = rinv[j];   // diagonal of L_JJ^-1
+  }
+  bad = __shfl_sync(0xffffffffu, bad ? 1 : 0, 0) != 0;
+  __syncwarp();
+  if (lane < 8) {
+    // column `lane` of L_JJ^-1: forward substitution on the unit vector
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float* row = S + rowoff(r0 + i) + r0;
+      float t = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int m = 0; m < i; ++m) t = fmaf(-row[m], x[m], t);
+      x[i] = (i >= lane) ? t * linv[J * 64 + i * 9] : 0.f;
+    }
+    __syncwarp(0xffu);   // lanes 0-7: every diagonal entry is read before any column is stored
+#pragma unroll
+    for (int i = 0; i < 8; ++i) linv[J * 64 + i * 8 + lane] = x[i];
+  }
+  __syncwarp();
+  return !bad;
+}
+
+// Warp 0: in-place solve of L L^T v = v with the inverse diagonal blocks.
+__device__ __forceinline__ void warp_subst(const float* S, const float* linv, float* v, int Q, int lane) {
+  for (int J = 0; J < Q; ++J) {                 // L y = v
+    const int r0 = 8 * J;
+    float y = 0.f;
+    if (lane < 8) {
+      const float* li = linv + J * 64 + lane * 8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) y = fmaf(li[j], v[r0 + j], y);
     }
     __syncwarp();
-    if (lane < 8) v[r0 + lane] = yv;
+    if (lane < 8) v[r0 + lane] = y;
     __syncwarp();
-    float y[8];
+    float yy[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) y[m] = v[r0 + m];
+    for (int m = 0; m < 8; ++m) yy[m] = v[r0 + m];
     for (int a = r0 + 8 + lane; a < 8 * Q; a += 32) {
       const float4* ra = reinterpret_cast<const float4*>(S + rowoff(a) + r0);
       const float4 l0 = ra[0], l1 = ra[1];
       float t = v[a];
-      t = fmaf(-l0.x, y[0], t); t = fmaf(-l0.y, y[1], t); t = fmaf(-l0.z, y[2], t); t = fmaf(-l0.w, y[3], t);
-      t = fmaf(-l1.x, y[4], t); t = fmaf(-l1.y, y[5], t); t = fmaf(-l1.z, y[6], t); t = fmaf(-l1.w, y[7], t);
+      t = fmaf(-l0.x, yy[0], t); t = fmaf(-l0.y, yy[1], t); t = fmaf(-l0.z, yy[2], t); t = fmaf(-l0.w, yy[3], t);
+      t = fmaf(-l1.x, yy[4], t); t = fmaf(-l1.y, yy[5], t); t = fmaf(-l1.z, yy[6], t); t = fmaf(-l1.w, yy[7], t);
       v[a] = t;
     }
     __syncwarp();
   }
-  for (int J = Q - 1; J >= 0; --J) {           // L^T x = y
+  for (int J = Q - 1; J >= 0; --J) {            // L^T x = y
     const int r0 = 8 * J;
-    float xv = lane < 8 ? v[r0 + lane] : 0.f;
+    float x = 0.f;
+    if (lane < 8) {
 #pragma unroll
-    for (int j = 7; j >= 0; --j) {
-      const float* rj = S + rowoff(r0 + j);
-      if (lane == j) xv = xv / rj[r0 + j];
-      const float xj = __shfl_sync(0xffffffffu, xv, j);
-      if (lane < j) xv = fmaf(-rj[r0 + lane], xj, xv);
+      for (int j = 0; j < 8; ++j) x = fmaf(linv[J * 64 + j * 8 + lane], v[r0 + j], x);
     }
     __syncwarp();
-    if (lane < 8) v[r0 + lane] = xv;
+    if (lane < 8) v[r0 + lane] = x;
     __syncwarp();
-    float x[8];
+    float xx[8];
     const float* rr[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) { x[m] = v[r0 + m]; rr[m] = S + rowoff(r0 + m); }
+    for (int m = 0; m < 8; ++m) { xx[m] = v[r0 + m]; rr[m] = S + rowoff(r0 + m); }
     for (int a = lane; a < r0; a += 32) {
       float t = v[a];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) t = fmaf(-rr[m][a], x[m], t);
+      for (int m = 0; m < 8; ++m) t = fmaf(-rr[m][a], xx[m], t);
       v[a] = t;
     }
     __syncwarp();
@@ -102,9 +159,9 @@ __device__ __forceinline__ void warp_subst(const float* S, float* v, int Q, int 
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) chol_solve_kernel(BatchDev b, const int2* systems, int first, int count,
-                                                       int mode, const float* rhs_flat, float* out_flat,
-                                                       float* saved, int32_t* status, float* ws) {
+__global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
+    chol_solve_kernel(BatchDev b, const int2* systems, int first, int count, int mode, const float* rhs_flat,
+                      float* out_flat, float* saved, int32_t* status, float* ws) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_bad;
@@ -118,8 +175,9 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
   const float* evx = b.shapes[pd.x].evals;
   const float* evy = b.shapes[pd.y].evals;
   const int ssz = rowoff(kp);
-  float* S = smem;                 // packed padded lower rows
-  float* pan = S + ssz;            // panel, column-major: pan[c * kp + a]
+  float* S = smem;                 // packed skewed lower rows
+  float* linv = S + ssz;           // inverse diagonal blocks, Q x 64
+  float* pan = linv + 64 * Q;      // current panel, column-major: pan[c * kp + a]
   float* v = pan + 8 * kp;         // working vector
   float* xs = v + kp;              // solution
   float* rh = xs + kp;             // right-hand side
@@ -127,7 +185,8 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
   const float2* Ghl = pd.g64_off >= 0 ? reinterpret_cast<const float2*>(ws) + pd.g64_off : nullptr;
   const float* rhs = (mode == kSolveForward) ? ws + pd.r_off + (int64_t)i * k : rhs_flat + pd.c_off + (int64_t)i * k;
   float* out = (mode == kSolveForward) ? out_flat + pd.c_off + (int64_t)i * k : ws + pd.gam_off + (int64_t)i * k;
-  float* fac = (saved != nullptr && pd.fac_off >= 0) ? saved + pd.fac_off + (int64_t)i * ssz : nullptr;
+  const int fsz = factor_floats(Q);
+  float* fac = (saved != nullptr && pd.fac_off >= 0) ? saved + pd.fac_off + (int64_t)i * fsz : nullptr;
   const float lam = pd.lam;
 
   if (tid == 0) {
@@ -138,73 +197,60 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
   for (int a = tid; a < kp; a += NT) rh[a] = a < k ? rhs[a] : 0.f;
 
   if (mode == kSolveAdjoint && fac != nullptr) {
-    for (int e = tid; e < ssz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
+    for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
     __syncthreads();
   } else {
-    // S = G + lambda diag(D_i), identity in the padding rows
-    for (int a = warp; a < kp; a += NW) {
-      float* row = S + rowoff(a);
-      const int len = (a & ~7) + 8;
-      const float* grow = G + (int64_t)a * k;
-      for (int c = lane; c < len; c += 32) {
-        float val = 0.f;
-        if (a < k) {
-          if (c < a) val = grow[c];
-          else if (c == a) val = grow[a] + lam * mask_entry(pd, evx, evy, i, a);
-        } else if (c == a) {
-          val = 1.f;
+    // S = G + lambda diag(D_i), identity in the padding rows: every row a is written
+    // over its 8 (a/8 + 1) stored columns; 8 independent loads in flight per thread
+    {
+      const int total = 32 * Q * (Q + 1);   // stored (row, column) pairs without the skew
+      for (int e0 = tid; e0 < total; e0 += 8 * NT) {
+        float val[8];
+        int dst[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * NT;
+          val[u] = 0.f;
+          dst[u] = -1;
+          if (e < total) {
+            // row block q holds rows 8q..8q+7 of length 8 (q + 1): 32 q (q + 1) entries before it
+            int q = (int)((sqrtf(1.f + (float)e / 8.f) - 1.f) * 0.5f);
+            while (32 * (q + 1) * (q + 2) <= e) ++q;
+            while (32 * q * (q + 1) > e) --q;
+            const int w = e - 32 * q * (q + 1);
+            const int a = 8 * q + w / (8 * (q + 1)), c = w % (8 * (q + 1));
+            dst[u] = rowoff(a) + c;
+            if (a < k) {
+              if (c < a) val[u] = G[(int64_t)a * k + c];
+              else if (c == a) val[u] = G[(int64_t)a * k + a] + lam * mask_entry(pd, evx, evy, i, a);
+            } else if (c == a) {
+              val[u] = 1.f;
+            }
+          }
         }
-        row[c] = val;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (dst[u] >= 0) S[dst[u]] = val[u];
       }
     }
     __syncthreads();
-    for (int J = 0; J < Q; ++J) {
+    if (warp == 0 && !diag_block(S, linv, 0, lane) && lane == 0) s_bad = 1;
+    __syncthreads();
+    for (int J = 0; J < Q && !s_bad; ++J) {
       const int r0 = 8 * J;
-      // 1. diagonal block
-      if (warp == 0) {
-        float x[8];
-        const float* row = S + rowoff(r0 + (lane & 7)) + r0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) x[c] = lane < 8 ? row[c] : 0.f;
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float piv = __shfl_sync(0xffffffffu, x[j], j);
-          if (!(piv > 0.f) || !(piv < INFINITY)) bad = true;
-          const float d = sqrtf(piv);
-          const float inv = 1.f / d;
-          if (lane == j) x[j] = d;
-          if (lane > j) x[j] *= inv;
-#pragma unroll
-          for (int c = j + 1; c < 8; ++c) {
-            const float lc = __shfl_sync(0xffffffffu, x[j], c);
-            if (lane >= c) x[c] = fmaf(-x[j], lc, x[c]);
-          }
-        }
-        if (lane < 8) {
-          float* wrow = S + rowoff(r0 + lane) + r0;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            wrow[c] = x[c];
-            pan[c * kp + r0 + lane] = c <= lane ? x[c] : 0.f;
-          }
-        }
-        if (lane == 0 && bad) s_bad = r0 + 1;
-      }
-      __syncthreads();
-      if (s_bad) break;
-      // 2. panel rows below the diagonal block: x L_JJ^T = s
+      const float* li = linv + J * 64;
+      // TRSM: rows below the diagonal block, x = s L_JJ^-T
       for (int a = r0 + 8 + tid; a < kp; a += NT) {
         float4* ra = reinterpret_cast<float4*>(S + rowoff(a) + r0);
         const float4 s0 = ra[0], s1 = ra[1];
-        float s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
         float x[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          float t = s[c];
+          float t = 0.f;
 #pragma unroll
-          for (int m = 0; m < c; ++m) t = fmaf(-x[m], pan[m * kp + r0 + c], t);
-          x[c] = t / pan[c * kp + r0 + c];
+          for (int m = 0; m <= c; ++m) t = fmaf(sv[m], li[c * 8 + m], t);
+          x[c] = t;
         }
         ra[0] = make_float4(x[0], x[1], x[2], x[3]);
         ra[1] = make_float4(x[4], x[5], x[6], x[7]);
@@ -212,58 +258,82 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
         for (int c = 0; c < 8; ++c) pan[c * kp + a] = x[c];
       }
       __syncthreads();
-      // 3. trailing update, 8 x 8 tiles (A, B) with J < B <= A < Q
-      const int m = Q - J - 1;
-      const int T = m * (m + 1) / 2;
-      for (int t = tid; t < T; t += NT) {
-        int ai = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-        while ((ai + 1) * (ai + 2) / 2 <= t) ++ai;
-        while (ai * (ai + 1) / 2 > t) --ai;
-        const int bi = t - ai * (ai + 1) / 2;
-        const int A = 8 * (J + 1 + ai), B = 8 * (J + 1 + bi);
-        float acc[8][8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float4* sr = reinterpret_cast<const float4*>(S + rowoff(A + r) + B);
-          const float4 u0 = sr[0], u1 = sr[1];
-          acc[r][0] = u0.x; acc[r][1] = u0.y; acc[r][2] = u0.z; acc[r][3] = u0.w;
-          acc[r][4] = u1.x; acc[r][5] = u1.y; acc[r][6] = u1.z; acc[r][7] = u1.w;
-        }
+      if (J + 1 == Q) break;
+      // (a) the next column block, one row per thread
+      const int n0 = r0 + 8;
+      for (int a = n0 + tid; a < kp; a += NT) {
+        float4* ra = reinterpret_cast<float4*>(S + rowoff(a) + n0);
+        const float4 u0 = ra[0], u1 = ra[1];
+        float acc[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const float4* pa = reinterpret_cast<const float4*>(pan + c * kp + A);
-          const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + B);
-          const float4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
-          const float la[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float lb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(-la[r], lb[q], acc[r][q]);
+          const float la = pan[c * kp + a];
+          const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + n0);
+          const float4 b0 = pb[0], b1 = pb[1];
+          acc[0] = fmaf(-la, b0.x, acc[0]); acc[1] = fmaf(-la, b0.y, acc[1]);
+          acc[2] = fmaf(-la, b0.z, acc[2]); acc[3] = fmaf(-la, b0.w, acc[3]);
+          acc[4] = fmaf(-la, b1.x, acc[4]); acc[5] = fmaf(-la, b1.y, acc[5]);
+          acc[6] = fmaf(-la, b1.z, acc[6]); acc[7] = fmaf(-la, b1.w, acc[7]);
         }
+        ra[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        ra[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      }
+      __syncthreads();
+      // (b) warp 0: next diagonal block; warps 1..: trailing tiles (A, B), J+2 <= B <= A < Q
+      if (warp == 0) {
+        if (!diag_block(S, linv, J + 1, lane) && lane == 0) s_bad = 1;
+      } else {
+        const int m = Q - J - 2;
+        const int T = m * (m + 1) / 2;
+        for (int t = tid - 32; t < T; t += NT - 32) {
+          int ai = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+          while ((ai + 1) * (ai + 2) / 2 <= t) ++ai;
+          while (ai * (ai + 1) / 2 > t) --ai;
+          const int bi = t - ai * (ai + 1) / 2;
+          const int A = 8 * (J + 2 + ai), B = 8 * (J + 2 + bi);
+          float acc[8][8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          float4* sr = reinterpret_cast<float4*>(S + rowoff(A + r) + B);
-          sr[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-          sr[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+          for (int r = 0; r < 8; ++r) {
+            const float4* sr = reinterpret_cast<const float4*>(S + rowoff(A + r) + B);
+            const float4 u0 = sr[0], u1 = sr[1];
+            acc[r][0] = u0.x; acc[r][1] = u0.y; acc[r][2] = u0.z; acc[r][3] = u0.w;
+            acc[r][4] = u1.x; acc[r][5] = u1.y; acc[r][6] = u1.z; acc[r][7] = u1.w;
+          }
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4* pa = reinterpret_cast<const float4*>(pan + c * kp + A);
+            const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + B);
+            const float4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
+            const float la[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float lb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+              for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(-la[r], lb[q], acc[r][q]);
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            float4* sr = reinterpret_cast<float4*>(S + rowoff(A + r) + B);
+            sr[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            sr[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+          }
         }
       }
       __syncthreads();
     }
     if (s_bad) {
-      // report the row system; the failing pivot lies in block (s_bad - 1) / 8
       if (tid == 0) set_status(status, p, FMAP_ERR_NOT_SPD | (i << 8));
       for (int a = tid; a < k; a += NT) out[a] = __int_as_float(0x7fc00000);
       return;
     }
     if (mode == kSolveForward && fac != nullptr)
-      for (int e = tid; e < ssz / 4; e += NT) reinterpret_cast<float4*>(fac)[e] = reinterpret_cast<const float4*>(S)[e];
+      for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(fac)[e] = reinterpret_cast<const float4*>(S)[e];
   }
 
   // x = S^{-1} rhs
   for (int a = tid; a < kp; a += NT) v[a] = rh[a];
   __syncthreads();
-  if (warp == 0) warp_subst(S, v, Q, lane);
+  if (warp == 0) warp_subst(S, linv, v, Q, lane);
   __syncthreads();
   for (int a = tid; a < kp; a += NT) xs[a] = v[a];
   __syncthreads();
@@ -277,10 +347,16 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
         if (Ghl) {
           const float2* grow = Ghl + (int64_t)a * k;
           float hi = 0.f, lo = 0.f;
-          for (int c = lane; c < k; c += 32) {
-            const float2 g = grow[c];
-            df_fma(hi, lo, g.x, xs[c]);
-            lo = fmaf(g.y, xs[c], lo);
+          for (int c0 = lane; c0 < k; c0 += 128) {
+            float2 g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = (c0 + 32 * u < k) ? grow[c0 + 32 * u] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float xv = (c0 + 32 * u < k) ? xs[c0 + 32 * u] : 0.f;
+              df_fma(hi, lo, g[u].x, xv);
+              lo = fmaf(g[u].y, xv, lo);
+            }
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
@@ -299,7 +375,14 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
         } else {
           const float* grow = G + (int64_t)a * k;
           float sum = 0.f;
-          for (int c = lane; c < k; c += 32) sum = fmaf(grow[c], xs[c], sum);
+          for (int c0 = lane; c0 < k; c0 += 128) {
+            float g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = (c0 + 32 * u < k) ? grow[c0 + 32 * u] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (c0 + 32 * u < k) sum = fmaf(g[u], xs[c0 + 32 * u], sum);
+          }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
           r = rh[a] - fmaf(dterm, xs[a], sum);
@@ -308,7 +391,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
       if (lane == 0) v[a] = r;
     }
     __syncthreads();
-    if (warp == 0) warp_subst(S, v, Q, lane);
+    if (warp == 0) warp_subst(S, linv, v, Q, lane);
     __syncthreads();
     for (int a = tid; a < kp; a += NT) xs[a] += v[a];
     __syncthreads();
@@ -325,7 +408,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4))) cho
 
 size_t chol_smem_bytes(int kmax) {
   const int Q = (kmax + 7) / 8, kp = 8 * Q;
-  return (size_t)(rowoff(kp) + 8 * kp + 3 * kp) * sizeof(float);
+  return (size_t)(factor_floats(Q) + 8 * kp + 3 * kp) * sizeof(float);
 }
 
 template <int NT>
@@ -336,10 +419,7 @@ cudaError_t set_limit() {
 
 }  // namespace
 
-int64_t chol_factor_floats(int k) {
-  const int Q = (k + 7) / 8;
-  return rowoff(8 * Q);
-}
+int64_t chol_factor_floats(int k) { return factor_floats((k + 7) / 8); }
 
 cudaError_t solve_set_smem_limits() {
   cudaError_t e;

@@ -142,9 +142,10 @@ def test_store_factor_threshold(lib):
     specs = [dict(n=300, k=30, d=64), dict(n=300, k=30, d=64), dict(n=300, k=200, d=512), dict(n=300, k=200, d=512)]
     rc, sz = _plan(lib, specs, [(0, 1, 1e-3), (2, 3, 1e-3)], o)
     assert rc == 0
-    # one row system keeps its factor as packed lower rows padded to multiples of 8:
-    # 32 Q (Q + 1) floats for k padded to 8 Q (k = 30: Q = 4, 640 floats); k = 200 is not saved
-    per_system = 32 * 4 * 5
+    # one row system keeps its factor as packed lower rows (8 (a/8 + 1) + 4 floats for row a)
+    # plus Q inverse 8 x 8 diagonal blocks: 32 Q (Q + 2) + 64 Q floats for k padded to 8 Q
+    # (k = 30: Q = 4, 1024 floats); k = 200 is not saved
+    per_system = 32 * 4 * 6 + 64 * 4
     assert sz.saved_bytes == 4 * ((30 * per_system + 63) // 64 * 64)
 
 
