@@ -14,9 +14,9 @@
 //            in 8 x 8 register tiles, S_AB -= L_AJ L_BJ^T.
 // Three block barriers per panel. Forward and back substitution are done by
 // warp 0 with the inverse diagonal blocks (no dependency chain inside a block);
-// then `ir_steps` steps of iterative refinement with the residual rhs - S x
-// accumulated in FP32, or in double-float (error-free products and sums,
-// ~48 bits) from the (hi, lo) Gram for hi_gram pairs.
+// then `ir_steps` steps of iterative refinement with the residual rhs - S x in
+// FP32; for hi_gram pairs the residual takes G as the two FP32 halves (hi + lo)
+// of its double-float accumulation.
 #include <math.h>
 
 #include "fmap_internal.cuh"
@@ -41,17 +41,6 @@ __device__ __forceinline__ float mask_entry(const PairDev& pd, const float* evx,
 
 __device__ __forceinline__ void set_status(int32_t* status, int p, int32_t code) {
   if (status) atomicCAS(status + p, 0, code);
-}
-
-// (hi, lo) += a * b with an exact product and an error-free sum.
-__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float pe = fmaf(a, b, -p);
-  const float s = __fadd_rn(hi, p);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
 
 // Warp 0: factor the 8 x 8 diagonal block J in place (lane 0, registers) and store
@@ -200,37 +189,26 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
     for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
     __syncthreads();
   } else {
-    // S = G + lambda diag(D_i), identity in the padding rows: every row a is written
-    // over its 8 (a/8 + 1) stored columns; 8 independent loads in flight per thread
-    {
-      const int total = 32 * Q * (Q + 1);   // stored (row, column) pairs without the skew
-      for (int e0 = tid; e0 < total; e0 += 8 * NT) {
-        float val[8];
-        int dst[8];
+    // S = G + lambda diag(D_i), identity in the padding rows; one warp per row, all of
+    // a row's loads issued before its stores
+    for (int a = warp; a < kp; a += NW) {
+      float* row = S + rowoff(a);
+      const int len = (a & ~7) + 8;
+      const float* grow = G + (int64_t)a * k;
+      float val[kMaxK / 32];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int e = e0 + u * NT;
-          val[u] = 0.f;
-          dst[u] = -1;
-          if (e < total) {
-            // row block q holds rows 8q..8q+7 of length 8 (q + 1): 32 q (q + 1) entries before it
-            int q = (int)((sqrtf(1.f + (float)e / 8.f) - 1.f) * 0.5f);
-            while (32 * (q + 1) * (q + 2) <= e) ++q;
-            while (32 * q * (q + 1) > e) --q;
-            const int w = e - 32 * q * (q + 1);
-            const int a = 8 * q + w / (8 * (q + 1)), c = w % (8 * (q + 1));
-            dst[u] = rowoff(a) + c;
-            if (a < k) {
-              if (c < a) val[u] = G[(int64_t)a * k + c];
-              else if (c == a) val[u] = G[(int64_t)a * k + a] + lam * mask_entry(pd, evx, evy, i, a);
-            } else if (c == a) {
-              val[u] = 1.f;
-            }
-          }
+      for (int u = 0; u < kMaxK / 32; ++u) {
+        const int c = lane + 32 * u;
+        val[u] = (a < k && c < a) ? grow[c] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kMaxK / 32; ++u) {
+        const int c = lane + 32 * u;
+        if (c < len) {
+          float x = val[u];
+          if (c == a) x = a < k ? grow[a] + lam * mask_entry(pd, evx, evy, i, a) : 1.f;
+          row[c] = x;
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (dst[u] >= 0) S[dst[u]] = val[u];
       }
     }
     __syncthreads();
@@ -345,8 +323,9 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
       if (a < k) {
         const float dterm = lam * mask_entry(pd, evx, evy, i, a);
         if (Ghl) {
+          // FP32 residual against the double-float Gram, G = hi + lo taken as two products
           const float2* grow = Ghl + (int64_t)a * k;
-          float hi = 0.f, lo = 0.f;
+          float sum = 0.f;
           for (int c0 = lane; c0 < k; c0 += 128) {
             float2 g[4];
 #pragma unroll
@@ -354,24 +333,12 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const float xv = (c0 + 32 * u < k) ? xs[c0 + 32 * u] : 0.f;
-              df_fma(hi, lo, g[u].x, xv);
-              lo = fmaf(g[u].y, xv, lo);
+              sum = fmaf(g[u].y, xv, fmaf(g[u].x, xv, sum));
             }
           }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            const float s = __fadd_rn(hi, h2);
-            const float bb = __fsub_rn(s, hi);
-            const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-            hi = s;
-            lo = __fadd_rn(lo, __fadd_rn(l2, e));
-          }
-          // r = rhs - (hi + lo) - dterm * x_a, the large terms first
-          const float dx = __fmul_rn(dterm, xs[a]);
-          const float dxe = fmaf(dterm, xs[a], -dx);
-          r = __fsub_rn(__fsub_rn(rh[a], hi), dx) - (lo + dxe);
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          r = rh[a] - fmaf(dterm, xs[a], sum);
         } else {
           const float* grow = G + (int64_t)a * k;
           float sum = 0.f;
