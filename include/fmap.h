@@ -204,6 +204,31 @@ enum fmap_kernel_kind {
 FMAP_API int32_t fmap_batch_set_timing(fmap_batch* batch, int32_t enable);
 FMAP_API int32_t fmap_batch_read_timing(fmap_batch* batch, float* ms, int32_t* launches, int32_t n_kinds);
 
+/* ---- Allocation-free single-pair solve (no counterpart in the paper) ---------------
+ * For callers that cannot allocate device memory when they solve (a memory pool they
+ * do not own is frozen, a real-time thread must not enter the allocator, or a host
+ * application owns all device memory): the same Gram and row-system Cholesky kernels
+ * as fmap_solve for ONE pair, with every scratch byte taken from a 2 MiB array that
+ * the library defines on each GPU that loads it (held until the process exits). It
+ * needs no batch, no workspace, and never calls cudaMalloc or cudaFree.
+ *   a_x, a_y   device, k x d FP32 row-major descriptor matrices A and B (fmap_project's
+ *              output for the source and the target shape), 4-byte aligned
+ *   evals_x/y  device k FP32 eigenvalues, or NULL when mask is given
+ *   mask       device k x k FP32 mask D, or NULL: D_ij = (evals_y[i] - evals_x[j])^2
+ *   lambda     >= 0;  ir_steps 0..3 (refinement steps, as in fmap_options)
+ *   c_out      device k x k FP32 output C;  status: device int32[1] or NULL (as fmap_solve)
+ *   stream     cudaStream_t passed as void*; the call only enqueues
+ * The Gram matrix is accumulated in double-float when k >= 200, as in fmap_solve.
+ * Returns UNSUPPORTED if k > 256 or the scratch layout of k exceeds 2 MiB.
+ * The first call on a device also sets the device up (address of the scratch array,
+ * kernel shared-memory limits) on the calling thread's current device; make that
+ * first call before any stream capture. All calls share the one scratch array:
+ * calls that overlap on the GPU race and must not be issued. */
+FMAP_API int32_t fmap_solve_pair_noalloc(const float* a_x, const float* a_y, int32_t k, int32_t d,
+                                         const float* evals_x, const float* evals_y, const float* mask,
+                                         float lambda, int32_t ir_steps, float* c_out, int32_t* status,
+                                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,8 @@ _PROTOS = {
     "fmap_loss_orth": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_batch_set_timing": (c_int32, [c_void_p, c_int32]),
     "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),
+    "fmap_solve_pair_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                          c_float, c_int32, c_void_p, c_void_p, c_void_p]),
 }
 
 KIND_NAMES = ["project", "project_reduce", "gram", "solve", "adj_solve", "adj_gemm", "gather", "project_bwd",

@@ -23,6 +23,7 @@ SOURCES = [
     "k_gram.cu",
     "k_solve.cu",
     "k_chol.cu",
+    "fmap_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
