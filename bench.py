@@ -123,22 +123,24 @@ def algorithmic_work(wl, ir_steps, saved_k_max):
     for p in wl.pairs:
         k = wl.shapes[p.x].k
         solve_flops += k ** 4 / 3.0 + (2.0 + 4.0 * ir_steps) * k ** 3
-        adj_flops += (0.0 if k <= saved_k_max else k ** 4 / 3.0) + (2.0 + 4.0 * ir_steps) * k ** 3
+        adj_flops += (0.0 if k <= saved_k_max else k ** 4 / 3.0) + 2.0 * k ** 3
         loss_flops += 4.0 * k ** 3
     return dict(project=dict(bytes=proj_bytes, flops=proj_flops), project_bwd=dict(bytes=bwd_bytes, flops=proj_flops),
                 solve=dict(flops=solve_flops), adj_solve=dict(flops=adj_flops), loss=dict(flops=loss_flops))
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_pairs_per_s(wl, budget_s: float, pair_offset: int = 0, max_pairs=None):
-    """Oracle fwd+bwd, pair by pair from `pair_offset`, until `budget_s` is spent."""
+def oracle_pairs_per_s(wl, budget_s: float, pair_offset: int = 0, max_pairs=None, keep=None):
+    """Oracle fwd+bwd, pair by pair from `pair_offset`, until `budget_s` is spent.
+    With `keep` (a dict), the oracle's C and dF of every pair done are stored in it."""
     import numpy as np
     from oracle import fmap_oracle as orc
     t0 = time.perf_counter()
     done, ks = 0, []
     npairs = len(wl.pairs)
     while True:
-        p = wl.pairs[(pair_offset + done) % npairs]
+        pi = (pair_offset + done) % npairs
+        p = wl.pairs[pi]
         sx, sy = wl.shapes[p.x], wl.shapes[p.y]
         ax = orc.project(sx.phi, sx.mass, sx.feat_f64())
         ay = orc.project(sy.phi, sy.mass, sy.feat_f64())
@@ -146,8 +148,10 @@ def oracle_pairs_per_s(wl, budget_s: float, pair_offset: int = 0, max_pairs=None
         c = orc.solve(ax, ay, dm, float(np.float32(p.lam)))
         _, dc = orc.loss_orth_gt(c, p.c_gt)
         g = orc.solve_backward(ax, ay, c, dm, float(np.float32(p.lam)), dc)
-        orc.project_backward(sx.phi, sx.mass, g["dA"])
-        orc.project_backward(sy.phi, sy.mass, g["dB"])
+        dfx = orc.project_backward(sx.phi, sx.mass, g["dA"])
+        dfy = orc.project_backward(sy.phi, sy.mass, g["dB"])
+        if keep is not None:
+            keep[pi] = (c, dfx, dfy)
         done += 1
         ks.append(sx.k)
         el = time.perf_counter() - t0
@@ -199,7 +203,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2604_10377_gb300 import api, synth
+    from paper_2604_10377_gb300 import api, shard, synth
 
     rank, world, local = dist_env()
     if world > 1:
@@ -239,13 +243,6 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def timed(fn, steps, sampler=None, timing=False):
         for _ in range(args.warmup):
             fn()
@@ -266,8 +263,9 @@ def run_ours(args):
         if timing:
             b.set_timing(False)
         barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
-        return ms, clocks, kt
+        # whole job: pairs of all ranks over the slowest rank's time
+        rate, ms, _ = shard.job_throughput(float(npairs), e0.elapsed_time(e1) / steps)
+        return ms, clocks, kt, rate
 
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", ""))
@@ -275,8 +273,8 @@ def run_ours(args):
         uuid = "GPU-" + uuid
     sampler = ClockSampler(uuid) if uuid else None
 
-    ms_step, clocks, ktime = timed(step, args.steps, sampler=sampler, timing=True)
-    ms_fwd, _, _ = timed(fwd_step, args.steps)
+    ms_step, clocks, ktime, rate_step = timed(step, args.steps, sampler=sampler, timing=True)
+    ms_fwd, _, _, rate_fwd = timed(fwd_step, args.steps)
     status = b.status[:npairs].cpu().numpy()
 
     # ---- end to end: host inputs -> device, step, loss and C back to the host
@@ -296,8 +294,8 @@ def run_ours(args):
             loss_host.copy_(loss, non_blocking=True)
             c_host.copy_(b.C, non_blocking=True)
 
-        ms_e2e, _, _ = timed(e2e_step, max(1, args.steps // 2))
-        e2e = {"value": world * npairs / (ms_e2e / 1000.0), "unit": "pairs/s", "ms_per_step": ms_e2e,
+        ms_e2e, _, _, rate_e2e = timed(e2e_step, max(1, args.steps // 2))
+        e2e = {"value": rate_e2e, "unit": "pairs/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel
@@ -309,9 +307,10 @@ def run_ours(args):
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
 
     def roof_for(kind):
-        per_launch_ms = ktime[kind][0] / ktime[kind][1]
+        # the launches of one kind in one step process the batch once: the unit is the step
+        per_step_ms = ktime[kind][0] / args.steps
         if kind in ("project", "project_bwd"):
-            ach = work[kind]["bytes"] / (per_launch_ms / 1000.0) / 1e9
+            ach = work[kind]["bytes"] / (per_step_ms / 1000.0) / 1e9
             return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": None,
                     "peak_source": f"{peaks['source']} HBM copy bandwidth"}
@@ -319,8 +318,6 @@ def run_ours(args):
         if flops is None:
             return {"kernel": kind, "bound": "alu", "achieved": None, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                     "frac": None, "traffic": None}
-        # solve kernels: the sum of all launches of the kind per step is the unit
-        per_step_ms = ktime[kind][0] / args.steps
         ach = flops / (per_step_ms / 1000.0) / 1e12
         return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak_tflops, "traffic": None,
@@ -330,25 +327,41 @@ def run_ours(args):
     others = {k: roof_for(k) for k in ("project", "project_bwd", "solve", "adj_solve") if k in kernels and k != dom}
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, n, el, ks = oracle_pairs_per_s(wl, args.cpu_budget)
+        ref = {}
+        v, n, el, ks = oracle_pairs_per_s(wl, args.cpu_budget, keep=ref)
         cpu = {"value": v, "unit": "pairs/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"fwd+bwd of the first {n} pairs of the same workload (k={ks}), {el:.1f} s, NumPy FP64"}
+        # error of the GPU results (last timed step, same inputs) against the oracle
+        ec, ef = [], []
+        for pi, (c_ref, dfx, dfy) in ref.items():
+            pr = wl.pairs[pi]
+            c_gpu = b.c_view(b.C, pi).double().cpu().numpy()
+            ec.append(float(np.linalg.norm(c_gpu - c_ref) / np.linalg.norm(c_ref)))
+            for sidx, dref in ((pr.x, dfx), (pr.y, dfy)):
+                dg = lay.feat_view(b.dfeat, sidx).double().cpu().numpy()
+                ef.append(float(np.linalg.norm(dg - dref) / np.linalg.norm(dref)))
+        accuracy = {"pairs": len(ec), "C_rel_fro_max": max(ec), "C_rel_fro_mean": float(np.mean(ec)),
+                    "dF_rel_fro_max": max(ef), "dF_rel_fro_mean": float(np.mean(ef)),
+                    "tolerance": 3e-3 if wl.feat_dtype == "bf16" else 1e-5,
+                    "reference": "FP64 oracle on the same inputs"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * npairs / (ms_step / 1000.0), "unit": "pairs/s", "n_gpus": world,
+            "metric": METRIC, "value": rate_step, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": npairs, "global_batch": world * npairs,
                        "parallelism": f"pairs sharded over {world} GPU(s), no collective",
                        "l2": "inputs larger than L2 (%.1f GB streamed per step)" % (work["project"]["bytes"] / 1e9)},
-            "fwd_only": {"value": world * npairs / (ms_fwd / 1000.0), "unit": "pairs/s", "ms_per_step": ms_fwd},
+            "fwd_only": {"value": rate_fwd, "unit": "pairs/s", "ms_per_step": ms_fwd},
             "roofline": roofline,
             "roofline_other": others,
             "kernels": kernels,
             "gpu_launches": int(launches_total),
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "e2e": e2e,
             "clocks": clocks,
             "status_ok": bool((status == 0).all()),

@@ -67,6 +67,8 @@ typedef struct fmap_options {
     int32_t store_factors_max_k;/* fmap_solve saves Cholesky factors for pairs with k <= this when a
                                    `saved` buffer is given; larger pairs are refactored in the
                                    backward pass (default 256: store everything) */
+    int32_t adjoint_ir_steps;   /* refinement steps of the adjoint row solves (0..3, default 0: the
+                                   FP32 factor solve alone is far inside the gradient tolerance) */
 } fmap_options;
 
 typedef struct fmap_shape_desc {
@@ -117,7 +119,8 @@ FMAP_API const char* fmap_error_string(int32_t code);
 /* Text of the last CUDA error seen by this thread's calls (static thread-local storage). */
 FMAP_API const char* fmap_last_cuda_error(void);
 
-/* Fill *opt with the defaults: FP32, ir_steps 1, hi_gram_min_k 200, store_factors_max_k 256. */
+/* Fill *opt with the defaults: FP32, ir_steps 1, hi_gram_min_k 200, store_factors_max_k 256,
+ * adjoint_ir_steps 0. */
 FMAP_API int32_t fmap_default_options(fmap_options* opt);
 
 /* Create a context on CUDA device `device` (host only; no device memory is touched

@@ -27,7 +27,7 @@ FMAP_PREC_BF16 = 1
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("ir_steps", c_int32), ("hi_gram_min_k", c_int32),
-                ("store_factors_max_k", c_int32)]
+                ("store_factors_max_k", c_int32), ("adjoint_ir_steps", c_int32)]
 
 
 class ShapeDesc(ctypes.Structure):

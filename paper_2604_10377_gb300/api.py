@@ -92,7 +92,7 @@ class FmapBatch:
 
     def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
                  with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
-                 store_factors_max_k: int = 256):
+                 store_factors_max_k: int = 256, adjoint_ir_steps: int = 0):
         self.layout = layout
         self.device = torch.device(device)
         self.precision = precision
@@ -121,6 +121,7 @@ class FmapBatch:
         opt.ir_steps = ir_steps
         opt.hi_gram_min_k = hi_gram_min_k
         opt.store_factors_max_k = store_factors_max_k
+        opt.adjoint_ir_steps = adjoint_ir_steps
         self.options = opt
         ctx = ctypes.c_void_p()
         check(L.fmap_create(ctypes.byref(ctx), self.device.index or 0, ctypes.byref(opt)), "fmap_create")

@@ -29,6 +29,7 @@ constexpr int kTile = 64;
 constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core backward projection
 constexpr int kTcCtas = 152;           // persistent CTAs of the projection (one per GB300 SM)
 constexpr int64_t kStageV = 64;        // vertices per projection pipeline stage
+constexpr int64_t kTcSegMaxV = 8192;   // longest projection segment (one TMEM accumulation)
 constexpr int kSmemBudget = 227 * 1024;
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -62,6 +63,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// One launch of the forward projection: the segments of one spectral-size class.
+struct TcLaunch {
+  int32_t cta_off;     // offset of its kTcCtas + 1 CTA boundaries in tc_cta_first
+  int32_t stages;
+  uint32_t f_stage, p_stage, tmem_cols;
+  int32_t smem;
+};
+
 struct Plan {
   fmap_options opt{};
   std::vector<ShapeDev> shapes;
@@ -78,14 +87,14 @@ struct Plan {
   // tensor-core projection (BF16 features)
   bool tc = false;
   std::vector<TcItem> tc_items;
-  std::vector<int32_t> tc_cta_first;
+  std::vector<int32_t> tc_cta_first;   // kTcCtas + 1 entries per launch
+  std::vector<TcLaunch> tc_launches;
   std::vector<TcRedGroup> tc_groups;
   int64_t tc_max_group_elems = 0;
-  int tc_stages = 0, tc_smem = 0;
-  uint32_t tc_f_stage = 0, tc_p_stage = 0, tc_tmem_cols = 0;
+  int tc_smem = 0;                     // the largest dynamic shared memory of the launches
   // tensor-core backward projection
   std::vector<TcBwdItem> bw_items;
-  std::vector<int32_t> bw_order;
+  std::vector<int32_t> bw_cta_first;   // kTcCtas + 1 segment boundaries
   std::vector<TcBwdGroup> bw_groups;
   int bw_max_img = 0, bw_stages = 0, bw_smem = 0;
   uint32_t bw_b_bytes = 0;
@@ -96,6 +105,7 @@ int32_t validate_options(const fmap_options& o) {
   if (o.precision != FMAP_PREC_FP32 && o.precision != FMAP_PREC_BF16) return FMAP_ERR_INVALID_ARG;
   if (o.ir_steps < 0 || o.ir_steps > 3) return FMAP_ERR_INVALID_ARG;
   if (o.hi_gram_min_k < 1 || o.store_factors_max_k < 0) return FMAP_ERR_INVALID_ARG;
+  if (o.adjoint_ir_steps < 0 || o.adjoint_ir_steps > 3) return FMAP_ERR_INVALID_ARG;
   return FMAP_OK;
 }
 
@@ -164,12 +174,12 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       cur = align_up(cur + (int64_t)sd.nchunk * sd.k * sd.d, kAlignFloats);
     }
   } else {
-    uint32_t fmax = 0, pmax = 0, tmax = 0;
-    // (shape, feature group) units, then a stream-K split of their vertex ranges
-    // into kTcCtas ranges of equal cost (64-vertex granularity)
+    // (shape, feature group) units, grouped by spectral-size class (k padded to 32, 64,
+    // 128, 256); every class is one launch with its own pipeline depth, and within a
+    // class a stream-K split of the vertex ranges into kTcCtas ranges of equal cost
+    // (64-vertex granularity)
     struct Unit { int s, f0, fg, npad, dspan; double cpv; };
-    std::vector<Unit> units;
-    double total = 0.0;
+    std::vector<Unit> classes[4];
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
       const int npad = (sd.k + 15) / 16 * 16;
@@ -177,63 +187,80 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       const int fg_cap = std::max(1, std::min(4, 512 / npad));
       const int groups = (mt + fg_cap - 1) / fg_cap;
       const int fg_s = (mt + groups - 1) / groups;
+      const int cls = npad <= 32 ? 0 : (npad <= 64 ? 1 : (npad <= 128 ? 2 : 3));
       for (int g = 0; g < groups; ++g) {
         Unit u;
         u.s = s; u.f0 = g * fg_s * 128; u.fg = std::min(fg_s, mt - g * fg_s); u.npad = npad;
         u.dspan = std::min(u.fg * 128, sd.d - u.f0);
         u.cpv = 4.0 * sd.k + 4.0 + 2.0 * u.dspan;   // HBM bytes per vertex
-        units.push_back(u);
-        total += u.cpv * (double)sd.n;
+        classes[cls].push_back(u);
+      }
+    }
+    for (int cls = 0; cls < 4; ++cls) {
+      const std::vector<Unit>& units = classes[cls];
+      if (units.empty()) continue;
+      uint32_t fmax = 0, pmax = 0, tmax = 0;
+      double total = 0.0;
+      for (const Unit& u : units) {
+        total += u.cpv * (double)P.shapes[u.s].n;
         fmax = std::max<uint32_t>(fmax, (uint32_t)u.fg * 16384u);
-        const uint32_t pb = std::max<uint32_t>((uint32_t)((npad + 31) / 32) * 8192u, (uint32_t)npad * 256u);
+        const uint32_t pb = std::max<uint32_t>((uint32_t)((u.npad + 31) / 32) * 8192u, (uint32_t)u.npad * 256u);
         pmax = std::max<uint32_t>(pmax, pb);
-        tmax = std::max<uint32_t>(tmax, (uint32_t)(u.fg * npad));
+        tmax = std::max<uint32_t>(tmax, (uint32_t)(u.fg * u.npad));
       }
-    }
-    const double per_cta = total / kTcCtas;
-    int cta = 0;
-    double budget = per_cta;
-    P.tc_cta_first.assign(kTcCtas + 1, 0);
-    for (const Unit& u : units) {
-      const ShapeDev& sd = P.shapes[u.s];
-      TcRedGroup rg{};
-      rg.shape = u.s; rg.f0 = u.f0; rg.stride = u.fg * 128; rg.dspan = u.dspan;
-      rg.it_beg = (int32_t)P.tc_items.size();
-      int64_t v = 0;
-      while (v < sd.n) {
-        int64_t take = (int64_t)std::ceil(std::max(budget, 0.0) / u.cpv);
-        take = std::max<int64_t>(kStageV, (take + kStageV - 1) / kStageV * kStageV);
-        if (cta == kTcCtas - 1) take = sd.n - v;
-        take = std::min<int64_t>(take, sd.n - v);
-        TcItem it{};
-        it.shape = u.s; it.f0 = u.f0; it.fg = u.fg; it.npad = u.npad;
-        it.v0 = v; it.v1 = v + take;
-        it.part_off = cur;
-        cur = align_up(cur + (int64_t)sd.k * rg.stride, kAlignFloats);
-        P.tc_items.push_back(it);
-        v += take;
-        budget -= u.cpv * (double)take;
-        if (budget <= 0.0 && cta < kTcCtas - 1) {
-          ++cta;
-          P.tc_cta_first[cta] = (int32_t)P.tc_items.size();
-          budget += per_cta;
+      TcLaunch L{};
+      L.cta_off = (int32_t)P.tc_cta_first.size();
+      P.tc_cta_first.resize(P.tc_cta_first.size() + kTcCtas + 1, 0);
+      int32_t* first = P.tc_cta_first.data() + L.cta_off;
+      first[0] = (int32_t)P.tc_items.size();
+      const double per_cta = total / kTcCtas;
+      int cta = 0;
+      double budget = per_cta;
+      for (const Unit& u : units) {
+        const ShapeDev& sd = P.shapes[u.s];
+        TcRedGroup rg{};
+        rg.shape = u.s; rg.f0 = u.f0; rg.stride = u.fg * 128; rg.dspan = u.dspan;
+        rg.it_beg = (int32_t)P.tc_items.size();
+        int64_t v = 0;
+        while (v < sd.n) {
+          int64_t take = (int64_t)std::ceil(std::max(budget, 0.0) / u.cpv);
+          take = std::max<int64_t>(kStageV, (take + kStageV - 1) / kStageV * kStageV);
+          if (cta == kTcCtas - 1) take = sd.n - v;
+          // a segment accumulates in TMEM; bounding its length bounds the accumulated
+          // rounding of the tensor-core FP32 sums (partials are added in IEEE FP32)
+          take = std::min<int64_t>(std::min<int64_t>(take, kTcSegMaxV), sd.n - v);
+          TcItem it{};
+          it.shape = u.s; it.f0 = u.f0; it.fg = u.fg; it.npad = u.npad;
+          it.v0 = v; it.v1 = v + take;
+          it.part_off = cur;
+          cur = align_up(cur + (int64_t)sd.k * rg.stride, kAlignFloats);
+          P.tc_items.push_back(it);
+          v += take;
+          budget -= u.cpv * (double)take;
+          if (budget <= 1e-9 * per_cta && cta < kTcCtas - 1) {
+            ++cta;
+            first[cta] = (int32_t)P.tc_items.size();
+            budget += per_cta;
+          }
         }
+        rg.it_end = (int32_t)P.tc_items.size();
+        P.tc_groups.push_back(rg);
+        P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)sd.k * rg.dspan);
       }
-      rg.it_end = (int32_t)P.tc_items.size();
-      P.tc_groups.push_back(rg);
-      P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)sd.k * rg.dspan);
+      for (int c = cta + 1; c <= kTcCtas; ++c) first[c] = (int32_t)P.tc_items.size();
+      L.f_stage = std::max<uint32_t>(fmax, 16384u);
+      L.p_stage = (std::max<uint32_t>(pmax, 8192u) + 1023u) / 1024u * 1024u;
+      uint32_t cols = 32;
+      while (cols < tmax) cols <<= 1;
+      L.tmem_cols = cols;
+      const int fixed = 1024 + 512;
+      const int per_stage = (int)(L.f_stage + L.p_stage) + kStageV * 4;
+      L.stages = std::min(6, (kSmemBudget - fixed) / per_stage);
+      if (L.stages < 2) return FMAP_ERR_UNSUPPORTED;
+      L.smem = fixed + L.stages * per_stage;
+      P.tc_smem = std::max(P.tc_smem, L.smem);
+      P.tc_launches.push_back(L);
     }
-    for (int c = cta + 1; c <= kTcCtas; ++c) P.tc_cta_first[c] = (int32_t)P.tc_items.size();
-    P.tc_f_stage = std::max<uint32_t>(fmax, 16384u);
-    P.tc_p_stage = (std::max<uint32_t>(pmax, 8192u) + 1023u) / 1024u * 1024u;
-    uint32_t cols = 32;
-    while (cols < tmax) cols <<= 1;
-    P.tc_tmem_cols = cols;
-    const int fixed = 1024 + 512;
-    const int per_stage = (int)(P.tc_f_stage + P.tc_p_stage) + kStageV * 4;
-    P.tc_stages = std::min(6, (kSmemBudget - fixed) / per_stage);
-    if (n_shapes > 0 && P.tc_stages < 2) return FMAP_ERR_UNSUPPORTED;
-    P.tc_smem = fixed + P.tc_stages * per_stage;
   }
   for (auto& pd : P.pairs) {
     const int64_t kk = (int64_t)pd.k * pd.k;
@@ -260,6 +287,16 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   P.da_int_off = cur;
   cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
   if (P.tc) {
+    // (shape, feature group) images and vertex-chunk work items (about four per SM).
+    // Items are sorted by cost with the feature groups of one chunk adjacent, and dealt
+    // to the CTAs round-robin: the groups of a chunk run at the same time on
+    // neighbouring SMs and share Phi through L2.
+    int64_t bw_work = 0;
+    for (int s = 0; s < n_shapes; ++s)
+      if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + 127) / 128);
+    const int64_t bw_chunk = std::min<int64_t>(
+        kTcChunkV, std::max<int64_t>(1024, (bw_work / (4 * kTcCtas) + 127) / 128 * 128));
+    std::vector<TcBwdItem> items;
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
       if (!sd.dfeat) continue;
@@ -275,28 +312,37 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         P.bw_groups.push_back(bg);
         P.bw_max_img = std::max(P.bw_max_img, kb * bg.nf * 32);
         P.bw_b_bytes = std::max<uint32_t>(P.bw_b_bytes, (uint32_t)(kb * bg.nf * 128));
-        for (int64_t v0 = 0; v0 < sd.n; v0 += kTcChunkV) {
+        for (int64_t v0 = 0; v0 < sd.n; v0 += bw_chunk) {
           TcBwdItem it{};
           it.shape = s; it.f0 = bg.f0; it.nf = bg.nf; it.kb = kb;
-          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + kTcChunkV);
+          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + bw_chunk);
           it.img_off = bg.img_off;
-          P.bw_items.push_back(it);
+          items.push_back(it);
         }
       }
     }
-    P.bw_order.resize(P.bw_items.size());
-    for (size_t i = 0; i < P.bw_items.size(); ++i) P.bw_order[i] = (int32_t)i;
-    auto bcost = [&](const TcBwdItem& it) {
-      return (double)(it.v1 - it.v0) * (4.0 * P.shapes[it.shape].k + 2.0 * it.nf);
-    };
-    std::stable_sort(P.bw_order.begin(), P.bw_order.end(), [&](int32_t a, int32_t b) {
-      const TcBwdItem &x = P.bw_items[a], &y = P.bw_items[b];
-      const double cx = bcost(x), cy = bcost(y);
-      if (cx != cy) return cx > cy;
-      if (x.shape != y.shape) return x.shape < y.shape;
-      if (x.v0 != y.v0) return x.v0 < y.v0;
-      return x.f0 < y.f0;
-    });
+    if (!items.empty()) {
+      std::vector<int32_t> order(items.size());
+      for (size_t i = 0; i < items.size(); ++i) order[i] = (int32_t)i;
+      auto bcost = [&](const TcBwdItem& it) {
+        return (double)(it.v1 - it.v0) * (4.0 * P.shapes[it.shape].k + 2.0 * it.nf);
+      };
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const TcBwdItem &x = items[a], &y = items[b];
+        const double cx = bcost(x), cy = bcost(y);
+        if (cx != cy) return cx > cy;
+        if (x.shape != y.shape) return x.shape < y.shape;
+        if (x.v0 != y.v0) return x.v0 < y.v0;
+        return x.f0 < y.f0;
+      });
+      // CTA c takes items c, c + kTcCtas, c + 2 kTcCtas, ... of the sorted list, stored contiguously
+      P.bw_cta_first.assign(kTcCtas + 1, 0);
+      for (int c = 0; c < kTcCtas; ++c) {
+        P.bw_cta_first[c] = (int32_t)P.bw_items.size();
+        for (size_t j = c; j < order.size(); j += kTcCtas) P.bw_items.push_back(items[order[j]]);
+      }
+      P.bw_cta_first[kTcCtas] = (int32_t)P.bw_items.size();
+    }
     const int fixed = 1024 + 512;
     P.bw_stages = std::min(6, (kSmemBudget - fixed - (int)P.bw_b_bytes) / 16384);
     if (!P.bw_items.empty() && P.bw_stages < 2) return FMAP_ERR_UNSUPPORTED;
@@ -409,7 +455,7 @@ struct fmap_batch {
   const CUtensorMap* d_phimaps_fwd = nullptr;
   const CUtensorMap* d_massmaps = nullptr;
   const TcBwdItem* d_bw_items = nullptr;
-  const int32_t* d_bw_order = nullptr;
+  const int32_t* d_bw_cta_first = nullptr;
   const TcBwdGroup* d_bw_groups = nullptr;
   int sm_count = 148;
 };
@@ -469,6 +515,7 @@ int32_t fmap_default_options(fmap_options* opt) {
   opt->ir_steps = 1;
   opt->hi_gram_min_k = 200;
   opt->store_factors_max_k = 256;
+  opt->adjoint_ir_steps = 0;
   return FMAP_OK;
 }
 
@@ -537,7 +584,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_mm = o_fp + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_bi = o_mm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
-  const int64_t o_bg = o_bo + bytes_of(P.bw_order.size(), sizeof(int32_t));
+  const int64_t o_bg = o_bo + bytes_of(P.bw_cta_first.size(), sizeof(int32_t));
   const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
   e = cudaMalloc(&b->dev_mem, (size_t)total);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch tables)"); }
@@ -611,7 +658,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
       put(o_mm + s * (int64_t)sizeof(CUtensorMap), &mm, sizeof(mm));
     }
     put(o_bi, P.bw_items.data(), P.bw_items.size() * sizeof(TcBwdItem));
-    put(o_bo, P.bw_order.data(), P.bw_order.size() * sizeof(int32_t));
+    put(o_bo, P.bw_cta_first.data(), P.bw_cta_first.size() * sizeof(int32_t));
     put(o_bg, P.bw_groups.data(), P.bw_groups.size() * sizeof(TcBwdGroup));
     if (!P.bw_items.empty()) {
       e = project_bwd_tc_set_smem(P.bw_smem);
@@ -635,6 +682,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->dev.n_pairs = n_pairs;
   b->dev.feat_bf16 = ctx->opt.precision == FMAP_PREC_BF16 ? 1 : 0;
   b->dev.ir_steps = ctx->opt.ir_steps;
+  b->dev.ir_steps_adj = ctx->opt.adjoint_ir_steps;
   b->d_ptiles = reinterpret_cast<const ProjTile*>(base + o_pt);
   b->d_btiles = reinterpret_cast<const BwdTile*>(base + o_bt);
   b->d_systems = reinterpret_cast<const int2*>(base + o_sy);
@@ -646,7 +694,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_phimaps_fwd = reinterpret_cast<const CUtensorMap*>(base + o_fp);
   b->d_massmaps = reinterpret_cast<const CUtensorMap*>(base + o_mm);
   b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
-  b->d_bw_order = reinterpret_cast<const int32_t*>(base + o_bo);
+  b->d_bw_cta_first = reinterpret_cast<const int32_t*>(base + o_bo);
   b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
   *out = b;
   return FMAP_OK;
@@ -721,25 +769,26 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control)");
   const Plan& P = b->plan;
   if (P.tc) {
-    TcProjParams tp{};
-    tp.shapes = b->dev.shapes;
-    tp.fmaps = b->d_fmaps;
-    tp.phimaps = b->d_phimaps_fwd;
-    tp.massmaps = b->d_massmaps;
-    tp.items = b->d_tc_items;
-    tp.cta_first = b->d_tc_cta_first;
-    tp.stages = P.tc_stages;
-    tp.f_stage_bytes = P.tc_f_stage;
-    tp.p_stage_bytes = P.tc_p_stage;
-    tp.tmem_cols = P.tc_tmem_cols;
-    tp.ws = w;
-    tp.err = static_cast<int*>(ws);
-    const int grid = P.tc_items.empty() ? 0 : kTcCtas;
-    {
-      TimedScope ts(b, FMAP_KIND_PROJECT, st);
-      e = launch_project_tc(tp, grid, P.tc_smem, st);
+    for (const TcLaunch& L : P.tc_launches) {
+      TcProjParams tp{};
+      tp.shapes = b->dev.shapes;
+      tp.fmaps = b->d_fmaps;
+      tp.phimaps = b->d_phimaps_fwd;
+      tp.massmaps = b->d_massmaps;
+      tp.items = b->d_tc_items;
+      tp.cta_first = b->d_tc_cta_first + L.cta_off;
+      tp.stages = L.stages;
+      tp.f_stage_bytes = L.f_stage;
+      tp.p_stage_bytes = L.p_stage;
+      tp.tmem_cols = L.tmem_cols;
+      tp.ws = w;
+      tp.err = static_cast<int*>(ws);
+      {
+        TimedScope ts(b, FMAP_KIND_PROJECT, st);
+        e = launch_project_tc(tp, kTcCtas, L.smem, st);
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
     {
       TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
       e = launch_project_tc_reduce(b->dev.shapes, b->d_tc_items, b->d_tc_groups, (int)P.tc_groups.size(),
@@ -845,16 +894,14 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     bp.shapes = b->dev.shapes;
     bp.phimaps = b->d_phimaps;
     bp.items = b->d_bw_items;
-    bp.order = b->d_bw_order;
-    bp.n_items = (int32_t)P.bw_items.size();
+    bp.cta_first = b->d_bw_cta_first;
     bp.stages = P.bw_stages;
     bp.b_bytes_max = P.bw_b_bytes;
     bp.tmem_cols = 256;
     bp.ws = w;
     bp.err = static_cast<int*>(ws);
-    const int grid = (int)std::min<int64_t>((int64_t)P.bw_items.size(), b->sm_count);
     TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
-    e = launch_project_bwd_tc(bp, grid, P.bw_smem, st);
+    e = launch_project_bwd_tc(bp, kTcCtas, P.bw_smem, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "project backward");
   return FMAP_OK;

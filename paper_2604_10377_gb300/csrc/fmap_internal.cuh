@@ -76,7 +76,8 @@ struct BatchDev {
   const int64_t* slot_list;     // workspace float offsets of dA contributions, grouped per shape
   int32_t n_shapes, n_pairs;
   int32_t feat_bf16;
-  int32_t ir_steps;
+  int32_t ir_steps;       // refinement steps of the forward row solves
+  int32_t ir_steps_adj;   // refinement steps of the adjoint row solves
 };
 
 __host__ __device__ inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
@@ -126,9 +127,8 @@ struct TcBwdGroup {
 struct TcBwdParams {
   const ShapeDev* shapes;
   const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 128, 128-byte swizzle
-  const TcBwdItem* items;
-  const int32_t* order;
-  int32_t n_items;
+  const TcBwdItem* items;       // segments, grouped by CTA
+  const int32_t* cta_first;     // CTA c owns segments [cta_first[c], cta_first[c + 1])
   int32_t stages;
   uint32_t b_bytes_max;
   uint32_t tmem_cols;

@@ -97,53 +97,88 @@ __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lan
   return !bad;
 }
 
-// Warp 0: in-place solve of L L^T v = v with the inverse diagonal blocks.
-__device__ __forceinline__ void warp_subst(const float* S, const float* linv, float* v, int Q, int lane) {
-  for (int J = 0; J < Q; ++J) {                 // L y = v
-    const int r0 = 8 * J;
+// v <- L^{-1} v with every thread of the block (NT >= kp): thread t updates row
+// r0 + 8 + t against y_J; warp 0 owns the next block's rows and applies its inverse
+// diagonal block right after updating them. One barrier per 8-row block.
+template <int NT>
+__device__ __forceinline__ void block_fwd(const float* S, const float* linv, float* v, int Q, int tid, int lane,
+                                          int warp) {
+  const int kp = 8 * Q;
+  if (warp == 0) {
     float y = 0.f;
-    if (lane < 8) {
-      const float* li = linv + J * 64 + lane * 8;
+    if (lane < 8)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) y = fmaf(li[j], v[r0 + j], y);
-    }
+      for (int j = 0; j < 8; ++j) y = fmaf(linv[lane * 8 + j], v[j], y);
     __syncwarp();
-    if (lane < 8) v[r0 + lane] = y;
-    __syncwarp();
-    float yy[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) yy[m] = v[r0 + m];
-    for (int a = r0 + 8 + lane; a < 8 * Q; a += 32) {
+    if (lane < 8) v[lane] = y;
+  }
+  __syncthreads();
+  for (int J = 0; J < Q; ++J) {
+    const int r0 = 8 * J;
+    const int a = r0 + 8 + tid;
+    if (a < kp) {
       const float4* ra = reinterpret_cast<const float4*>(S + rowoff(a) + r0);
       const float4 l0 = ra[0], l1 = ra[1];
+      const float4 y0 = *reinterpret_cast<const float4*>(v + r0);
+      const float4 y1 = *reinterpret_cast<const float4*>(v + r0 + 4);
       float t = v[a];
-      t = fmaf(-l0.x, yy[0], t); t = fmaf(-l0.y, yy[1], t); t = fmaf(-l0.z, yy[2], t); t = fmaf(-l0.w, yy[3], t);
-      t = fmaf(-l1.x, yy[4], t); t = fmaf(-l1.y, yy[5], t); t = fmaf(-l1.z, yy[6], t); t = fmaf(-l1.w, yy[7], t);
+      t = fmaf(-l0.x, y0.x, t); t = fmaf(-l0.y, y0.y, t); t = fmaf(-l0.z, y0.z, t); t = fmaf(-l0.w, y0.w, t);
+      t = fmaf(-l1.x, y1.x, t); t = fmaf(-l1.y, y1.y, t); t = fmaf(-l1.z, y1.z, t); t = fmaf(-l1.w, y1.w, t);
       v[a] = t;
     }
-    __syncwarp();
+    if (J + 1 < Q && warp == 0) {
+      __syncwarp();
+      float y = 0.f;
+      if (lane < 8) {
+        const float* li = linv + (J + 1) * 64 + lane * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y = fmaf(li[j], v[r0 + 8 + j], y);
+      }
+      __syncwarp();
+      if (lane < 8) v[r0 + 8 + lane] = y;
+    }
+    __syncthreads();
   }
-  for (int J = Q - 1; J >= 0; --J) {            // L^T x = y
+}
+
+// v <- L^{-T} v: thread t updates row t against x_J; the warp owning the previous
+// block's rows applies that block's transposed inverse. One barrier per block.
+template <int NT>
+__device__ __forceinline__ void block_bwd(const float* S, const float* linv, float* v, int Q, int tid, int lane,
+                                          int warp) {
+  {
+    const int r0 = 8 * (Q - 1);
+    if (warp == (r0 >> 5)) {
+      const int i = lane - (r0 & 31);
+      float x = 0.f;
+      if (i >= 0 && i < 8)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x = fmaf(linv[(Q - 1) * 64 + j * 8 + i], v[r0 + j], x);
+      __syncwarp();
+      if (i >= 0 && i < 8) v[r0 + i] = x;
+    }
+  }
+  __syncthreads();
+  for (int J = Q - 1; J >= 1; --J) {
     const int r0 = 8 * J;
-    float x = 0.f;
-    if (lane < 8) {
+    if (tid < r0) {
+      float t = v[tid];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x = fmaf(linv[J * 64 + j * 8 + lane], v[r0 + j], x);
+      for (int m = 0; m < 8; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], v[r0 + m], t);
+      v[tid] = t;
     }
-    __syncwarp();
-    if (lane < 8) v[r0 + lane] = x;
-    __syncwarp();
-    float xx[8];
-    const float* rr[8];
+    const int p0 = r0 - 8;                 // rows of block J - 1, owned by threads p0..p0+7
+    if (warp == (p0 >> 5)) {
+      __syncwarp();
+      const int i = lane - (p0 & 31);
+      float x = 0.f;
+      if (i >= 0 && i < 8)
 #pragma unroll
-    for (int m = 0; m < 8; ++m) { xx[m] = v[r0 + m]; rr[m] = S + rowoff(r0 + m); }
-    for (int a = lane; a < r0; a += 32) {
-      float t = v[a];
-#pragma unroll
-      for (int m = 0; m < 8; ++m) t = fmaf(-rr[m][a], xx[m], t);
-      v[a] = t;
+        for (int j = 0; j < 8; ++j) x = fmaf(linv[(J - 1) * 64 + j * 8 + i], v[p0 + j], x);
+      __syncwarp();
+      if (i >= 0 && i < 8) v[p0 + i] = x;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -189,34 +224,53 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
     for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
     __syncthreads();
   } else {
-    // S = G + lambda diag(D_i), identity in the padding rows; one warp per row, all of
-    // a row's loads issued before its stores
-    for (int a = warp; a < kp; a += NW) {
-      float* row = S + rowoff(a);
-      const int len = (a & ~7) + 8;
-      const float* grow = G + (int64_t)a * k;
-      float val[kMaxK / 32];
+    // S = G + lambda diag(D_i), identity in the padding rows; one warp per row, four
+    // rows' loads in flight before any store
+    for (int a0 = warp; a0 < kp; a0 += 4 * NW) {
+      float val[4][kMaxK / 32];
 #pragma unroll
-      for (int u = 0; u < kMaxK / 32; ++u) {
-        const int c = lane + 32 * u;
-        val[u] = (a < k && c < a) ? grow[c] : 0.f;
+      for (int u = 0; u < 4; ++u) {
+        const int a = a0 + u * NW;
+        const float* grow = G + (int64_t)a * k;
+#pragma unroll
+        for (int q = 0; q < kMaxK / 32; ++q) {
+          const int c = lane + 32 * q;
+          val[u][q] = (a < k && c < a) ? grow[c] : 0.f;
+        }
       }
 #pragma unroll
-      for (int u = 0; u < kMaxK / 32; ++u) {
-        const int c = lane + 32 * u;
-        if (c < len) {
-          float x = val[u];
-          if (c == a) x = a < k ? grow[a] + lam * mask_entry(pd, evx, evy, i, a) : 1.f;
-          row[c] = x;
+      for (int u = 0; u < 4; ++u) {
+        const int a = a0 + u * NW;
+        if (a >= kp) break;
+        float* row = S + rowoff(a);
+        const int len = (a & ~7) + 8;
+#pragma unroll
+        for (int q = 0; q < kMaxK / 32; ++q) {
+          const int c = lane + 32 * q;
+          if (c < len) {
+            float x = val[u][q];
+            if (c == a) x = a < k ? G[(int64_t)a * k + a] + lam * mask_entry(pd, evx, evy, i, a) : 1.f;
+            row[c] = x;
+          }
         }
       }
     }
+    for (int a = tid; a < kp; a += NT) v[a] = rh[a];   // right-hand side, reduced during the factorisation
     __syncthreads();
     if (warp == 0 && !diag_block(S, linv, 0, lane) && lane == 0) s_bad = 1;
     __syncthreads();
     for (int J = 0; J < Q && !s_bad; ++J) {
       const int r0 = 8 * J;
       const float* li = linv + J * 64;
+      // forward substitution, bordered into the factorisation: y_J = L_JJ^-1 v_J
+      if (warp == 0) {
+        float y = 0.f;
+        if (lane < 8)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) y = fmaf(li[lane * 8 + j], v[r0 + j], y);
+        __syncwarp();
+        if (lane < 8) v[r0 + lane] = y;
+      }
       // TRSM: rows below the diagonal block, x = s L_JJ^-T
       for (int a = r0 + 8 + tid; a < kp; a += NT) {
         float4* ra = reinterpret_cast<float4*>(S + rowoff(a) + r0);
@@ -237,15 +291,18 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
       }
       __syncthreads();
       if (J + 1 == Q) break;
-      // (a) the next column block, one row per thread
+      // (a) the next column block, one row per thread; the row's right-hand side
+      // takes the panel's contribution, v_a -= L_aJ y_J
       const int n0 = r0 + 8;
       for (int a = n0 + tid; a < kp; a += NT) {
         float4* ra = reinterpret_cast<float4*>(S + rowoff(a) + n0);
         const float4 u0 = ra[0], u1 = ra[1];
         float acc[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        float va = v[a];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const float la = pan[c * kp + a];
+          va = fmaf(-la, v[r0 + c], va);
           const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + n0);
           const float4 b0 = pb[0], b1 = pb[1];
           acc[0] = fmaf(-la, b0.x, acc[0]); acc[1] = fmaf(-la, b0.y, acc[1]);
@@ -255,6 +312,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
         }
         ra[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         ra[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        v[a] = va;
       }
       __syncthreads();
       // (b) warp 0: next diagonal block; warps 1..: trailing tiles (A, B), J+2 <= B <= A < Q
@@ -308,58 +366,71 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
       for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(fac)[e] = reinterpret_cast<const float4*>(S)[e];
   }
 
-  // x = S^{-1} rhs
-  for (int a = tid; a < kp; a += NT) v[a] = rh[a];
-  __syncthreads();
-  if (warp == 0) warp_subst(S, linv, v, Q, lane);
-  __syncthreads();
+  // x = S^{-1} rhs: the factorisation already applied L^{-1} to v; with loaded factors
+  // the forward substitution runs here
+  if (mode == kSolveAdjoint && fac != nullptr) {
+    for (int a = tid; a < kp; a += NT) v[a] = rh[a];
+    __syncthreads();
+    block_fwd<NT>(S, linv, v, Q, tid, lane, warp);
+  }
+  block_bwd<NT>(S, linv, v, Q, tid, lane, warp);
   for (int a = tid; a < kp; a += NT) xs[a] = v[a];
   __syncthreads();
 
-  // iterative refinement: x += S^{-1} (rhs - S x)
-  for (int it = 0; it < b.ir_steps; ++it) {
-    for (int a = warp; a < kp; a += NW) {
-      float r = 0.f;
-      if (a < k) {
-        const float dterm = lam * mask_entry(pd, evx, evy, i, a);
-        if (Ghl) {
-          // FP32 residual against the double-float Gram, G = hi + lo taken as two products
-          const float2* grow = Ghl + (int64_t)a * k;
-          float sum = 0.f;
-          for (int c0 = lane; c0 < k; c0 += 128) {
-            float2 g[4];
+  // iterative refinement: x += S^{-1} (rhs - S x); four rows of G in flight per warp
+  const int n_ir = mode == kSolveForward ? b.ir_steps : b.ir_steps_adj;
+  for (int it = 0; it < n_ir; ++it) {
+    for (int a0 = warp; a0 < kp; a0 += 4 * NW) {
+      float sum[4] = {0.f, 0.f, 0.f, 0.f};
+      if (Ghl) {
+        float2 g[4][kMaxK / 32];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) g[u] = (c0 + 32 * u < k) ? grow[c0 + 32 * u] : make_float2(0.f, 0.f);
+        for (int u = 0; u < 4; ++u) {
+          const int a = a0 + u * NW;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float xv = (c0 + 32 * u < k) ? xs[c0 + 32 * u] : 0.f;
-              sum = fmaf(g[u].y, xv, fmaf(g[u].x, xv, sum));
-            }
+          for (int q = 0; q < kMaxK / 32; ++q) {
+            const int c = lane + 32 * q;
+            g[u][q] = (a < k && c < k) ? Ghl[(int64_t)a * k + c] : make_float2(0.f, 0.f);
           }
+        }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-          r = rh[a] - fmaf(dterm, xs[a], sum);
-        } else {
-          const float* grow = G + (int64_t)a * k;
-          float sum = 0.f;
-          for (int c0 = lane; c0 < k; c0 += 128) {
-            float g[4];
+        for (int q = 0; q < kMaxK / 32; ++q) {
+          const int c = lane + 32 * q;
+          const float xv = c < k ? xs[c] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) g[u] = (c0 + 32 * u < k) ? grow[c0 + 32 * u] : 0.f;
+          for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q].y, xv, fmaf(g[u][q].x, xv, sum[u]));
+        }
+      } else {
+        float g[4][kMaxK / 32];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (c0 + 32 * u < k) sum = fmaf(g[u], xs[c0 + 32 * u], sum);
+        for (int u = 0; u < 4; ++u) {
+          const int a = a0 + u * NW;
+#pragma unroll
+          for (int q = 0; q < kMaxK / 32; ++q) {
+            const int c = lane + 32 * q;
+            g[u][q] = (a < k && c < k) ? G[(int64_t)a * k + c] : 0.f;
           }
+        }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-          r = rh[a] - fmaf(dterm, xs[a], sum);
+        for (int q = 0; q < kMaxK / 32; ++q) {
+          const int c = lane + 32 * q;
+          const float xv = c < k ? xs[c] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q], xv, sum[u]);
         }
       }
-      if (lane == 0) v[a] = r;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum[u] += __shfl_xor_sync(0xffffffffu, sum[u], o);
+        const int a = a0 + u * NW;
+        if (lane == 0 && a < kp)
+          v[a] = a < k ? rh[a] - fmaf(lam * mask_entry(pd, evx, evy, i, a), xs[a], sum[u]) : 0.f;
+      }
     }
     __syncthreads();
-    if (warp == 0) warp_subst(S, linv, v, Q, lane);
-    __syncthreads();
+    block_fwd<NT>(S, linv, v, Q, tid, lane, warp);
+    block_bwd<NT>(S, linv, v, Q, tid, lane, warp);
     for (int a = tid; a < kp; a += NT) xs[a] += v[a];
     __syncthreads();
   }

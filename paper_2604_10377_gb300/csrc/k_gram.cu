@@ -1,5 +1,8 @@
 // Gram matrix and right-hand sides of the row systems (Eq. 4):
 //   G = A_x A_x^T and R = A_y A_x^T, both k x k, per pair.
+// 64 x 64 output tiles, 4 x 4 outputs per thread, the feature dimension staged
+// through shared memory 16 columns at a time. G is symmetric: only its lower
+// tiles are computed and each is written twice (transposed).
 // For pairs flagged hi_gram (large k) G is accumulated in double-float
 // arithmetic: every product is split exactly (fma) and summed with an
 // error-free transformation, which keeps ~48 significant bits, as an FP64
@@ -11,7 +14,8 @@
 namespace fmap {
 namespace {
 
-constexpr int kT = 32;
+constexpr int kT = 64;
+constexpr int kS = 16;
 
 // (hi, lo) += a * b with an exact product and an error-free sum.
 __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
@@ -24,69 +28,41 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
   lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
 
-__device__ __forceinline__ void gram_tile_df(const float* X, int k, int d, int ti, int tj, float* out32,
-                                             float2* outhl) {
-  __shared__ float sX[kT][kT + 1];
-  __shared__ float sY[kT][kT + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int f0 = 0; f0 < d; f0 += kT) {
-    for (int e = threadIdx.x; e < kT * kT; e += 256) {
-      const int r = e / kT, c = e % kT;
-      const int xi = ti * kT + r, yj = tj * kT + r, f = f0 + c;
-      sX[r][c] = (xi < k && f < d) ? X[(int64_t)xi * d + f] : 0.f;
-      sY[r][c] = (yj < k && f < d) ? X[(int64_t)yj * d + f] : 0.f;
+// out[i][j] = sum_f X[i0 + i][f] Y[j0 + j][f] for one 64 x 64 tile.
+template <bool kDF>
+__device__ __forceinline__ void gram_tile(const float* X, const float* Y, int k, int d, int i0, int j0,
+                                          float (&hi)[4][4], float (&lo)[4][4]) {
+  __shared__ float sX[kS][kT + 4];
+  __shared__ float sY[kS][kT + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { hi[a][b] = 0.f; lo[a][b] = 0.f; }
+  for (int f0 = 0; f0 < d; f0 += kS) {
+    for (int e = tid; e < kT * kS; e += 256) {
+      const int r = e / kS, c = e % kS, f = f0 + c;
+      sX[c][r] = (i0 + r < k && f < d) ? X[(int64_t)(i0 + r) * d + f] : 0.f;
+      sY[c][r] = (j0 + r < k && f < d) ? Y[(int64_t)(j0 + r) * d + f] : 0.f;
     }
     __syncthreads();
-    for (int c = 0; c < kT; ++c) {
-      const float yv = sY[tx][c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) df_fma(hi[r], lo[r], sX[ty + 8 * r][c], yv);
+    for (int c = 0; c < kS; ++c) {
+      const float4 xa = *reinterpret_cast<const float4*>(&sX[c][ty * 4]);
+      const float4 yb = *reinterpret_cast<const float4*>(&sY[c][tx * 4]);
+      const float xv[4] = {xa.x, xa.y, xa.z, xa.w};
+      const float yv[4] = {yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (kDF)
+            df_fma(hi[a][b], lo[a][b], xv[a], yv[b]);
+          else
+            hi[a][b] = fmaf(xv[a], yv[b], hi[a][b]);
+        }
     }
     __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = ti * kT + ty + 8 * r, j = tj * kT + tx;
-    if (i < k && j < k) {
-      const float s = __fadd_rn(hi[r], lo[r]);
-      const float e = __fsub_rn(lo[r], __fsub_rn(s, hi[r]));
-      out32[(int64_t)i * k + j] = s;
-      outhl[(int64_t)i * k + j] = make_float2(s, e);
-    }
-  }
-}
-
-template <typename Acc>
-__device__ __forceinline__ void gram_tile(const float* X, const float* Y, int k, int d, int ti, int tj,
-                                          float* out32, double* out64) {
-  __shared__ float sX[kT][kT + 1];
-  __shared__ float sY[kT][kT + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
-  Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-  for (int f0 = 0; f0 < d; f0 += kT) {
-    for (int e = threadIdx.x; e < kT * kT; e += 256) {
-      const int r = e / kT, c = e % kT;
-      const int xi = ti * kT + r, yj = tj * kT + r, f = f0 + c;
-      sX[r][c] = (xi < k && f < d) ? X[(int64_t)xi * d + f] : 0.f;
-      sY[r][c] = (yj < k && f < d) ? Y[(int64_t)yj * d + f] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int c = 0; c < kT; ++c) {
-      const Acc yv = Acc(sY[tx][c]);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[r] += Acc(sX[ty + 8 * r][c]) * yv;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = ti * kT + ty + 8 * r, j = tj * kT + tx;
-    if (i < k && j < k) {
-      out32[(int64_t)i * k + j] = (float)acc[r];
-      if (out64) out64[(int64_t)i * k + j] = (double)acc[r];
-    }
   }
 }
 
@@ -94,17 +70,54 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
   const PairDev pd = b.pairs[blockIdx.z];
   const int k = pd.k, d = pd.d;
   const int nt = (k + kT - 1) / kT;
-  if ((int)blockIdx.x >= nt * nt) return;
-  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
   const float* ax = a + b.shapes[pd.x].a_off;
   const float* ay = a + b.shapes[pd.y].a_off;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float hi[4][4], lo[4][4];
   if (blockIdx.y == 0) {
+    // G: lower tiles only (ti >= tj), mirrored on store
+    int t = blockIdx.x, ti = 0;
+    while (t > ti) { t -= ti + 1; ++ti; }
+    const int tj = t;
+    if (ti >= nt) return;
+    const int i0 = ti * kT, j0 = tj * kT;
+    float* g = ws + pd.g_off;
+    float2* ghl = pd.hi_gram ? reinterpret_cast<float2*>(ws) + pd.g64_off : nullptr;
     if (pd.hi_gram)
-      gram_tile_df(ax, k, d, ti, tj, ws + pd.g_off, reinterpret_cast<float2*>(ws) + pd.g64_off);
+      gram_tile<true>(ax, ax, k, d, i0, j0, hi, lo);
     else
-      gram_tile<float>(ax, ax, k, d, ti, tj, ws + pd.g_off, nullptr);
+      gram_tile<false>(ax, ax, k, d, i0, j0, hi, lo);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = i0 + ty * 4 + r, j = j0 + tx * 4 + c;
+        if (i >= k || j >= k) continue;
+        float v = hi[r][c], e = 0.f;
+        if (ghl) {
+          v = __fadd_rn(hi[r][c], lo[r][c]);
+          e = __fsub_rn(lo[r][c], __fsub_rn(v, hi[r][c]));
+        }
+        g[(int64_t)i * k + j] = v;
+        g[(int64_t)j * k + i] = v;
+        if (ghl) {
+          ghl[(int64_t)i * k + j] = make_float2(v, e);
+          ghl[(int64_t)j * k + i] = make_float2(v, e);
+        }
+      }
   } else {
-    gram_tile<float>(ay, ax, k, d, ti, tj, ws + pd.r_off, nullptr);
+    // R = A_y A_x^T: every tile
+    if ((int)blockIdx.x >= nt * nt) return;
+    const int i0 = (blockIdx.x / nt) * kT, j0 = (blockIdx.x % nt) * kT;
+    gram_tile<false>(ay, ax, k, d, i0, j0, hi, lo);
+    float* r = ws + pd.r_off;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = i0 + ty * 4 + rr, j = j0 + tx * 4 + c;
+        if (i < k && j < k) r[(int64_t)i * k + j] = hi[rr][c];
+      }
   }
 }
 

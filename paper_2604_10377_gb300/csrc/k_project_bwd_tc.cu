@@ -20,7 +20,7 @@
 namespace fmap {
 namespace {
 
-constexpr int kEpiWarps = 4;
+constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each storing half of the columns
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kTileV = 128;                       // vertices per output tile (MMA M)
 constexpr uint32_t kAStageBytes = kTileV * 128;   // 128 rows x 32 fp32
@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
     // ------------------------------------------------------------ TMA producer (Phi tiles, dA^T image)
     if (lane == 0) {
       uint32_t stage = 0, phase = 0, bphase = 0;
-      for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-        const TcBwdItem item = P.items[P.order[it]];
+      for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
+        const TcBwdItem item = P.items[it];
         const CUtensorMap* map = P.phimaps + item.shape;
         tc::prefetch_tmap(map);
         if (!tc::mbar_wait(b_empty, bphase ^ 1, abort_flag)) goto producer_done;
@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
       uint32_t acc_phase[2] = {0, 0};
       int buf = 0;
       bool ok = true;
-      for (int it = blockIdx.x; it < P.n_items && ok; it += gridDim.x) {
-        const TcBwdItem item = P.items[P.order[it]];
+      for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1] && ok; ++it) {
+        const TcBwdItem item = P.items[it];
         if (!tc::mbar_wait(b_full, bphase, abort_flag)) break;
         bphase ^= 1;
         tc::tc_fence_after();
@@ -162,21 +162,22 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
     }
   } else {
     // ------------------------------------------------------------ epilogue: TMEM -> M * acc -> BF16 dF
-    const int quarter = warp & 3;
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
     uint32_t acc_phase[2] = {0, 0};
     int buf = 0;
-    for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-      const TcBwdItem item = P.items[P.order[it]];
+    for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
+      const TcBwdItem item = P.items[it];
       const ShapeDev s = P.shapes[item.shape];
       __nv_bfloat16* df = reinterpret_cast<__nv_bfloat16*>(s.dfeat);
       const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
       for (int t = 0; t < ntiles; ++t) {
-        if (!tc::mbar_wait(&acc_full[buf], acc_phase[buf], abort_flag)) goto epi_done;
-        tc::tc_fence_after();
+        // the row's mass is loaded before the accumulator wait, so its latency is hidden
         const int64_t v = item.v0 + (int64_t)t * kTileV + quarter * 32 + lane;
         const bool vok = v < item.v1;
         const float m = vok ? __ldg(s.mass + v) : 0.f;
-        for (int ch = 0; ch < item.nf / 16; ++ch) {
+        if (!tc::mbar_wait(&acc_full[buf], acc_phase[buf], abort_flag)) goto epi_done;
+        tc::tc_fence_after();
+        for (int ch = half; ch < item.nf / 16; ch += 2) {
           float x[16];
           tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + ch * 16), x);
           if (vok) {
@@ -252,7 +253,7 @@ cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* gro
 }
 
 cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st) {
-  if (p.n_items <= 0) return cudaSuccess;
+  if (grid <= 0) return cudaSuccess;
   project_bwd_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
   return cudaGetLastError();
 }

@@ -124,7 +124,7 @@ def test_plan_rejects_k_mismatch_and_missing_evals(lib):
 def test_options_validation(lib):
     from paper_2604_10377_gb300 import _lib
     o = _lib.default_options()
-    assert (o.precision, o.ir_steps, o.hi_gram_min_k, o.store_factors_max_k) == (0, 1, 200, 256)
+    assert (o.precision, o.ir_steps, o.hi_gram_min_k, o.store_factors_max_k, o.adjoint_ir_steps) == (0, 1, 200, 256, 0)
     ctx = ctypes.c_void_p()
     assert lib.fmap_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == 0
     assert lib.fmap_destroy(ctx) == 0
