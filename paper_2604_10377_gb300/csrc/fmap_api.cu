@@ -287,61 +287,69 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   P.da_int_off = cur;
   cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
   if (P.tc) {
-    // (shape, feature group) images and vertex-chunk work items (about four per SM).
-    // Items are sorted by cost with the feature groups of one chunk adjacent, and dealt
-    // to the CTAs round-robin: the groups of a chunk run at the same time on
-    // neighbouring SMs and share Phi through L2.
+    // Backward work runs on clusters of two CTAs that share each Phi tile (multicast):
+    // a shape's features split into an even number of groups of <= 128, and a work
+    // item is (shape, vertex chunk, pair of groups), one group per CTA of the
+    // cluster. Items are sorted by cost and dealt to the clusters round-robin.
+    const int n_clusters = kTcCtas / 2;
     int64_t bw_work = 0;
     for (int s = 0; s < n_shapes; ++s)
-      if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + 127) / 128);
+      if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + 255) / 256);
     const int64_t bw_chunk = std::min<int64_t>(
-        kTcChunkV, std::max<int64_t>(1024, (bw_work / (4 * kTcCtas) + 127) / 128 * 128));
-    std::vector<TcBwdItem> items;
+        kTcChunkV, std::max<int64_t>(1024, (bw_work / (4 * n_clusters) + 127) / 128 * 128));
+    std::vector<TcBwdItem> items;   // pairs: [2 j] for cluster rank 0, [2 j + 1] for rank 1
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
       if (!sd.dfeat) continue;
       const int kb = (sd.k + 31) / 32;
-      const int ngroups = (sd.d + 127) / 128;
+      const int ngroups = 2 * ((sd.d + 255) / 256);
       const int nf_s = ((sd.d + ngroups - 1) / ngroups + 15) / 16 * 16;
+      std::vector<TcBwdGroup> gl(ngroups);
       for (int g = 0; g < ngroups; ++g) {
-        TcBwdGroup bg{};
-        bg.shape = s; bg.f0 = g * nf_s; bg.nf = std::min(nf_s, sd.d - bg.f0); bg.kb = kb;
+        TcBwdGroup& bg = gl[g];
+        bg.shape = s; bg.f0 = g * nf_s; bg.nf = std::max(0, std::min(nf_s, sd.d - bg.f0)); bg.kb = kb;
+        bg.img_off = -1;
         if (bg.nf <= 0) continue;
         bg.img_off = cur;
         cur = align_up(cur + (int64_t)kb * bg.nf * 32, kAlignFloats);
         P.bw_groups.push_back(bg);
         P.bw_max_img = std::max(P.bw_max_img, kb * bg.nf * 32);
         P.bw_b_bytes = std::max<uint32_t>(P.bw_b_bytes, (uint32_t)(kb * bg.nf * 128));
-        for (int64_t v0 = 0; v0 < sd.n; v0 += bw_chunk) {
-          TcBwdItem it{};
-          it.shape = s; it.f0 = bg.f0; it.nf = bg.nf; it.kb = kb;
-          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + bw_chunk);
-          it.img_off = bg.img_off;
-          items.push_back(it);
-        }
       }
+      for (int gp = 0; gp < ngroups / 2; ++gp)
+        for (int64_t v0 = 0; v0 < sd.n; v0 += bw_chunk)
+          for (int r = 0; r < 2; ++r) {
+            const TcBwdGroup& bg = gl[2 * gp + r];
+            TcBwdItem it{};
+            it.shape = s; it.f0 = bg.f0; it.nf = bg.nf; it.kb = kb;
+            it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + bw_chunk);
+            it.img_off = bg.img_off;
+            items.push_back(it);
+          }
     }
     if (!items.empty()) {
-      std::vector<int32_t> order(items.size());
-      for (size_t i = 0; i < items.size(); ++i) order[i] = (int32_t)i;
-      auto bcost = [&](const TcBwdItem& it) {
-        return (double)(it.v1 - it.v0) * (4.0 * P.shapes[it.shape].k + 2.0 * it.nf);
+      const size_t npi = items.size() / 2;
+      std::vector<int32_t> order(npi);
+      for (size_t i = 0; i < npi; ++i) order[i] = (int32_t)i;
+      auto bcost = [&](size_t j) {
+        const TcBwdItem& it = items[2 * j];
+        return (double)(it.v1 - it.v0) * (4.0 * P.shapes[it.shape].k + 2.0 * (it.nf + items[2 * j + 1].nf));
       };
       std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        const TcBwdItem &x = items[a], &y = items[b];
-        const double cx = bcost(x), cy = bcost(y);
+        const double cx = bcost(a), cy = bcost(b);
         if (cx != cy) return cx > cy;
-        if (x.shape != y.shape) return x.shape < y.shape;
-        if (x.v0 != y.v0) return x.v0 < y.v0;
-        return x.f0 < y.f0;
+        return a < b;
       });
-      // CTA c takes items c, c + kTcCtas, c + 2 kTcCtas, ... of the sorted list, stored contiguously
-      P.bw_cta_first.assign(kTcCtas + 1, 0);
-      for (int c = 0; c < kTcCtas; ++c) {
-        P.bw_cta_first[c] = (int32_t)P.bw_items.size();
-        for (size_t j = c; j < order.size(); j += kTcCtas) P.bw_items.push_back(items[order[j]]);
+      // cluster c takes pair-items c, c + n_clusters, ... of the sorted list, stored contiguously
+      P.bw_cta_first.assign(n_clusters + 1, 0);
+      for (int c = 0; c < n_clusters; ++c) {
+        P.bw_cta_first[c] = (int32_t)(P.bw_items.size() / 2);
+        for (size_t j = c; j < order.size(); j += n_clusters) {
+          P.bw_items.push_back(items[2 * order[j]]);
+          P.bw_items.push_back(items[2 * order[j] + 1]);
+        }
       }
-      P.bw_cta_first[kTcCtas] = (int32_t)P.bw_items.size();
+      P.bw_cta_first[n_clusters] = (int32_t)(P.bw_items.size() / 2);
     }
     const int fixed = 1024 + 512;
     P.bw_stages = std::min(6, (kSmemBudget - fixed - (int)P.bw_b_bytes) / 16384);
@@ -451,7 +459,6 @@ struct fmap_batch {
   const TcItem* d_tc_items = nullptr;
   const int32_t* d_tc_cta_first = nullptr;
   const TcRedGroup* d_tc_groups = nullptr;
-  const CUtensorMap* d_phimaps = nullptr;
   const CUtensorMap* d_phimaps_fwd = nullptr;
   const CUtensorMap* d_massmaps = nullptr;
   const TcBwdItem* d_bw_items = nullptr;
@@ -579,8 +586,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_ti = o_tm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_to = o_ti + bytes_of(P.tc_items.size(), sizeof(TcItem));
   const int64_t o_tg = o_to + bytes_of(P.tc_cta_first.size(), sizeof(int32_t));
-  const int64_t o_pm = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
-  const int64_t o_fp = o_pm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_fp = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
   const int64_t o_mm = o_fp + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_bi = o_mm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
@@ -616,21 +622,11 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
         return FMAP_ERR_CUDA;
       }
       put(o_tm + s * (int64_t)sizeof(CUtensorMap), &m, sizeof(m));
-      // FP32 basis for the backward projection: box 32 basis x 128 vertices
+      // FP32 basis, box 32 basis x 64 vertices (the forward projection's tiles and the
+      // halves of the backward projection's 128-vertex tiles)
       CUtensorMap pm;
       cuuint64_t pdim[2] = {(cuuint64_t)sd.k, (cuuint64_t)sd.n};
       cuuint64_t pstride[1] = {(cuuint64_t)sd.ld_phi * 4};
-      cuuint32_t pbox[2] = {32, 128};
-      r = encode(&pm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sd.phi), pdim, pstride, pbox, estr,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) {
-        cudaFree(b->dev_mem); delete b;
-        std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled(phi) failed (%d)", (int)r);
-        return FMAP_ERR_CUDA;
-      }
-      put(o_pm + s * (int64_t)sizeof(CUtensorMap), &pm, sizeof(pm));
-      // FP32 basis for the forward projection: box 32 basis x 64 vertices
       cuuint32_t fbox[2] = {32, 64};
       r = encode(&pm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sd.phi), pdim, pstride, fbox, estr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -690,7 +686,6 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_tc_items = reinterpret_cast<const TcItem*>(base + o_ti);
   b->d_tc_cta_first = reinterpret_cast<const int32_t*>(base + o_to);
   b->d_tc_groups = reinterpret_cast<const TcRedGroup*>(base + o_tg);
-  b->d_phimaps = reinterpret_cast<const CUtensorMap*>(base + o_pm);
   b->d_phimaps_fwd = reinterpret_cast<const CUtensorMap*>(base + o_fp);
   b->d_massmaps = reinterpret_cast<const CUtensorMap*>(base + o_mm);
   b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
@@ -857,9 +852,13 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     e = launch_status_clear(status, b->plan.sizes.n_pairs, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "status_clear");
-  {
+  // the adjoint solves read G only to refactor a system whose factor was not saved,
+  // or for adjoint refinement steps
+  bool need_g = saved == nullptr || b->dev.ir_steps_adj > 0;
+  for (const PairDev& pd : b->plan.pairs) need_g = need_g || pd.fac_off < 0;
+  if (need_g) {
     TimedScope ts(b, FMAP_KIND_GRAM, st);
-    e = launch_gram(b->dev, b->plan.max_k, a, w, st);
+    e = launch_gram(b->dev, b->plan.max_k, a, w, st, /*with_r=*/false);
   }
   if (e != cudaSuccess) return cuda_fail(e, "gram");
   for (const auto& g : b->plan.groups) {
@@ -892,7 +891,7 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     if (e != cudaSuccess) return cuda_fail(e, "dA image");
     TcBwdParams bp{};
     bp.shapes = b->dev.shapes;
-    bp.phimaps = b->d_phimaps;
+    bp.phimaps = b->d_phimaps_fwd;
     bp.items = b->d_bw_items;
     bp.cta_first = b->d_bw_cta_first;
     bp.stages = P.bw_stages;

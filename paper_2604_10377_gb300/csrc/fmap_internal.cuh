@@ -126,9 +126,9 @@ struct TcBwdGroup {
 
 struct TcBwdParams {
   const ShapeDev* shapes;
-  const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 128, 128-byte swizzle
-  const TcBwdItem* items;       // segments, grouped by CTA
-  const int32_t* cta_first;     // CTA c owns segments [cta_first[c], cta_first[c + 1])
+  const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 64, 128-byte swizzle
+  const TcBwdItem* items;       // item j of a cluster: [2 j] for CTA rank 0, [2 j + 1] for rank 1
+  const int32_t* cta_first;     // cluster c (CTAs 2c, 2c + 1) owns items [cta_first[c], cta_first[c + 1])
   int32_t stages;
   uint32_t b_bytes_max;
   uint32_t tmem_cols;
@@ -153,7 +153,9 @@ cudaError_t launch_project_simt(const BatchDev& b, const ProjTile* tiles, int nt
                                 cudaStream_t st);
 cudaError_t launch_project_reduce(const BatchDev& b, int max_kd, float* a_out, const float* ws,
                                   cudaStream_t st);
-cudaError_t launch_gram(const BatchDev& b, int max_k, const float* a, float* ws, cudaStream_t st);
+// with_r = false computes G only (the adjoint solves never read R)
+cudaError_t launch_gram(const BatchDev& b, int max_k, const float* a, float* ws, cudaStream_t st,
+                        bool with_r = true);
 
 struct SolveGroup {
   int32_t first;     // index into the system list

@@ -123,10 +123,10 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
 
 }  // namespace
 
-cudaError_t launch_gram(const BatchDev& b, int max_k, const float* a, float* ws, cudaStream_t st) {
+cudaError_t launch_gram(const BatchDev& b, int max_k, const float* a, float* ws, cudaStream_t st, bool with_r) {
   if (b.n_pairs <= 0) return cudaSuccess;
   const int nt = (max_k + kT - 1) / kT;
-  dim3 grid(nt * nt, 2, b.n_pairs);
+  dim3 grid(nt * nt, with_r ? 2 : 1, b.n_pairs);
   gram_kernel<<<grid, 256, 0, st>>>(b, a, ws);
   return cudaGetLastError();
 }

@@ -3,14 +3,18 @@
 //   dF_s (n x d) = diag(M_s) Phi_s (n x k) . dA_s (k x d)
 //
 // kind::tf32 MMA, M = 128 vertices, N = one feature group (<= 128 features),
-// K = the basis index in blocks of 32. Phi is read straight from HBM by TMA as
-// FP32 tiles (K-major, 128-byte swizzle); the B operand is dA_s^T of the feature
-// group, prepared once per backward pass as a K-major swizzled FP32 image in the
-// workspace and bulk-copied into shared memory per work item. The mass is a
-// per-row (per-TMEM-lane) scale applied in the epilogue, which converts to BF16
-// and writes dF. TF32 keeps ~2^-11 relative accuracy of each operand, far inside
-// the BF16 storage of dF. Accumulators are double-buffered in TMEM so that the
-// epilogue of one vertex tile overlaps the MMAs of the next.
+// K = the basis index in blocks of 32. The kernel runs as clusters of two CTAs on
+// two SMs: both CTAs of a cluster walk the same vertex tiles, each for its own
+// feature group, and each loads half of every FP32 Phi tile by TMA and multicasts
+// it to both, so a pair of feature groups reads Phi from HBM once. The B operand
+// is dA_s^T of the CTA's feature group, prepared once per backward pass as a
+// K-major swizzled FP32 image in the workspace and bulk-copied into shared memory
+// per work item. The mass is a per-row (per-TMEM-lane) scale applied in the
+// epilogue, which converts to BF16 and writes dF. TF32 keeps ~2^-11 relative
+// accuracy of each operand, far inside the BF16 storage of dF. Accumulators are
+// double-buffered in TMEM so that the epilogue of one vertex tile overlaps the
+// MMAs of the next. A Phi stage is refilled only after the MMAs of both CTAs
+// released it (multicast commit to both CTAs' empty barriers).
 //
 // Waits are bounded like the forward kernel's; a timeout sets the workspace
 // control word to FMAP_ERR_TIMEOUT.
@@ -50,8 +54,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = P.stages;
-  uint8_t* sB = smem;                                   // resident dA^T image
-  uint8_t* sA = sB + P.b_bytes_max;                     // Phi tiles, S stages
+  uint8_t* sB = smem;                                   // resident dA^T image of this CTA's feature group
+  uint8_t* sA = sB + P.b_bytes_max;                     // Phi tiles, S stages (same offset in both CTAs)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * kAStageBytes);
   uint64_t* a_full = bars;
   uint64_t* a_empty = bars + S;
@@ -63,10 +67,13 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = tc::cluster_ctarank();     // 0 or 1: which feature group of the pair
+  const int cl = blockIdx.x >> 1;                  // cluster index
+  const int it_beg = P.cta_first[cl], it_end = P.cta_first[cl + 1];
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&a_full[s], 1);
-      tc::mbar_init(&a_empty[s], 1);
+      tc::mbar_init(&a_empty[s], 2);     // released by the MMAs of both CTAs
     }
     tc::mbar_init(b_full, 1);
     tc::mbar_init(b_empty, 1);
@@ -82,35 +89,49 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
     tc::tmem_relinquish();
     tc::tc_fence_before();
   }
-  __syncthreads();
+  // both CTAs' barriers exist before either multicasts into the other
+  tc::cluster_sync();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer (Phi tiles, dA^T image)
+    // ------------------------------------------------------------ TMA producer
+    // Each CTA loads its half (64 vertices) of every Phi tile and multicasts it to
+    // both CTAs, so the pair reads each tile from HBM once.
     if (lane == 0) {
       uint32_t stage = 0, phase = 0, bphase = 0;
-      for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
-        const TcBwdItem item = P.items[it];
+      for (int it = it_beg; it < it_end; ++it) {
+        const TcBwdItem item = P.items[2 * it + rank];
         const CUtensorMap* map = P.phimaps + item.shape;
         tc::prefetch_tmap(map);
         if (!tc::mbar_wait(b_empty, bphase ^ 1, abort_flag)) goto producer_done;
-        const uint32_t bbytes = (uint32_t)item.kb * (uint32_t)item.nf * 128u;
-        tc::mbar_arrive_expect_tx(b_full, bbytes);
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(P.ws + item.img_off);
-        for (uint32_t off = 0; off < bbytes; off += 16384u)
-          bulk_g2s(sB + off, src + off, (bbytes - off) < 16384u ? (bbytes - off) : 16384u, b_full);
+        if (item.nf > 0) {
+          const uint32_t bbytes = (uint32_t)item.kb * (uint32_t)item.nf * 128u;
+          tc::mbar_arrive_expect_tx(b_full, bbytes);
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(P.ws + item.img_off);
+          for (uint32_t off = 0; off < bbytes; off += 16384u)
+            bulk_g2s(sB + off, src + off, (bbytes - off) < 16384u ? (bbytes - off) : 16384u, b_full);
+        } else {
+          tc::mbar_arrive(b_full);
+        }
         bphase ^= 1;
         const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
         for (int t = 0; t < ntiles; ++t) {
-          const int y = (int)(item.v0 + (int64_t)t * kTileV);
+          const int y = (int)(item.v0 + (int64_t)t * kTileV) + (int)rank * (kTileV / 2);
           for (int kb = 0; kb < item.kb; ++kb) {
             if (!tc::mbar_wait(&a_empty[stage], phase ^ 1, abort_flag)) goto producer_done;
             tc::mbar_arrive_expect_tx(&a_full[stage], kAStageBytes);
-            tc::tma_load_2d(sA + (size_t)stage * kAStageBytes, map, &a_full[stage], kb * 32, y);
+            tc::tma_load_2d_multicast(sA + (size_t)stage * kAStageBytes + rank * (kAStageBytes / 2), map,
+                                      &a_full[stage], kb * 32, y, (uint16_t)0x3);
             if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
           }
         }
+      }
+      // every stage's last use has been released by both CTAs: no arrival from the
+      // peer is still on its way to this CTA's barriers
+      for (int s = 0; s < S; ++s) {
+        if (!tc::mbar_wait(&a_empty[stage], phase ^ 1, abort_flag)) break;
+        if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
       }
     producer_done:
       if (*abort_flag) {
@@ -125,12 +146,12 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
       uint32_t acc_phase[2] = {0, 0};
       int buf = 0;
       bool ok = true;
-      for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1] && ok; ++it) {
-        const TcBwdItem item = P.items[it];
+      for (int it = it_beg; it < it_end && ok; ++it) {
+        const TcBwdItem item = P.items[2 * it + rank];
         if (!tc::mbar_wait(b_full, bphase, abort_flag)) break;
         bphase ^= 1;
         tc::tc_fence_after();
-        const uint32_t idesc = idesc_tf32(128, (uint32_t)item.nf);
+        const uint32_t idesc = idesc_tf32(128, (uint32_t)(item.nf > 0 ? item.nf : 16));
         const uint32_t b_base = tc::smem_u32(sB);
         const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
         for (int t = 0; t < ntiles && ok; ++t) {
@@ -141,14 +162,16 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
             if (!tc::mbar_wait(&a_full[stage], phase, abort_flag)) { ok = false; break; }
             tc::tc_fence_after();
             const uint32_t a_base = tc::smem_u32(sA + (size_t)stage * kAStageBytes);
+            if (item.nf > 0) {
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t ad = tc::smem_desc(a_base + ks * 32, 16, 1024, tc::kLayoutSW128);
-              const uint64_t bd = tc::smem_desc(b_base + (uint32_t)(kb * item.nf * 128) + ks * 32, 16, 1024,
-                                                tc::kLayoutSW128);
-              mma_tf32(d, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ad = tc::smem_desc(a_base + ks * 32, 16, 1024, tc::kLayoutSW128);
+                const uint64_t bd = tc::smem_desc(b_base + (uint32_t)(kb * item.nf * 128) + ks * 32, 16, 1024,
+                                                  tc::kLayoutSW128);
+                mma_tf32(d, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
+              }
             }
-            tc::mma_commit(&a_empty[stage]);
+            tc::mma_commit_multicast(&a_empty[stage], (uint16_t)0x3);
             if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
@@ -165,8 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     uint32_t acc_phase[2] = {0, 0};
     int buf = 0;
-    for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
-      const TcBwdItem item = P.items[it];
+    for (int it = it_beg; it < it_end; ++it) {
+      const TcBwdItem item = P.items[2 * it + rank];
       const ShapeDev s = P.shapes[item.shape];
       __nv_bfloat16* df = reinterpret_cast<__nv_bfloat16*>(s.dfeat);
       const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
@@ -181,26 +204,14 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
           float x[16];
           tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + ch * 16), x);
           if (vok) {
-            uint4 w0, w1;
-            w0.x = __bfloat16_as_ushort(__float2bfloat16_rn(x[0] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[1] * m)) << 16);
-            w0.y = __bfloat16_as_ushort(__float2bfloat16_rn(x[2] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[3] * m)) << 16);
-            w0.z = __bfloat16_as_ushort(__float2bfloat16_rn(x[4] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[5] * m)) << 16);
-            w0.w = __bfloat16_as_ushort(__float2bfloat16_rn(x[6] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[7] * m)) << 16);
-            w1.x = __bfloat16_as_ushort(__float2bfloat16_rn(x[8] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[9] * m)) << 16);
-            w1.y = __bfloat16_as_ushort(__float2bfloat16_rn(x[10] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[11] * m)) << 16);
-            w1.z = __bfloat16_as_ushort(__float2bfloat16_rn(x[12] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[13] * m)) << 16);
-            w1.w = __bfloat16_as_ushort(__float2bfloat16_rn(x[14] * m)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[15] * m)) << 16);
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              w[j] = __bfloat16_as_ushort(__float2bfloat16_rn(x[2 * j] * m)) |
+                     ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * j + 1] * m)) << 16);
             uint4* dst = reinterpret_cast<uint4*>(df + v * s.ld_feat + item.f0 + ch * 16);
-            dst[0] = w0;
-            dst[1] = w1;
+            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
           }
         }
         tc::tc_fence_before();
@@ -214,6 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   }
 
   __syncthreads();
+  // neither CTA leaves while the other may still multicast into it
+  tc::cluster_sync();
   if (warp == 1) tc::tmem_dealloc(tmem_base, P.tmem_cols);
   if (threadIdx.x == 0 && *abort_flag) atomicExch(P.err, (int)FMAP_ERR_TIMEOUT);
 }
@@ -254,8 +267,19 @@ cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* gro
 
 cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  project_bwd_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, project_bwd_tc_kernel, p);
 }
 
 }  // namespace fmap

@@ -195,6 +195,20 @@ def test_backward_against_oracle(feat_dtype, use_saved):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= gtol
 
 
+@pytest.mark.parametrize("d", [16, 48, 384, 640])
+def test_backward_bf16_feature_groups(d):
+    """BF16 backward projection with feature counts that leave the second group of a
+    cluster empty (16), uneven (48), split into four groups (384) or into six (640),
+    and vertex counts that end inside the second 64-row half of a tile."""
+    wl = synth.make_small(11, 4, (66, 3000), [7, 30, 64, 64], d, feat_dtype="bf16")
+    out = _gpu_backward(wl)
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["bf16"]
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
+
+
 def test_gradient_against_finite_differences():
     """GPU dL/dF (FP32 mode) against central differences (h = 1e-3) of the FP64
     pipeline along 8 seeded random directions per shape."""
