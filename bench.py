@@ -159,6 +159,68 @@ def oracle_pairs_per_s(wl, budget_s: float, pair_offset: int = 0, max_pairs=None
             return done / el, done, el, ks
 
 
+# ---------------------------------------------------------------- plain PyTorch comparator
+def torch_restatement(lay, b, wl, gt_host_list, dev, steps: int, warmup: int):
+    """The method written with plain PyTorch FP32 ops on the same GPU and the same
+    resident inputs: A = Phi^T (M F), G = A A^T and R = B A^T per pair, the k row
+    systems G + lambda diag(D_i) stacked with diag_embed and handed to
+    torch.linalg.solve, the orthogonality + ground-truth loss, and autograd for the
+    backward. Pairs of equal k are batched. A comparator only: none of this runs on
+    the library's path. Returns (fwd+bwd pairs/s, fwd pairs/s, ms fwd+bwd, ms fwd)."""
+    import numpy as np
+    import torch
+
+    views = []
+    for s in range(lay.n_shapes):
+        n, k, ld = lay.ns[s], lay.ks[s], lay.ld_phi[s]
+        phi = b.phi[lay.phi_off[s]:lay.phi_off[s] + n * ld].view(n, ld)[:, :k]
+        mass = b.mass[lay.mass_off[s]:lay.mass_off[s] + n]
+        ev = b.evals[lay.evals_off[s]:lay.evals_off[s] + k]
+        views.append((phi, mass, lay.feat_view(b.feat, s), ev))
+    groups = {}
+    for pi, p in enumerate(wl.pairs):
+        groups.setdefault(lay.ks[p.x], []).append(pi)
+    gts = {k: torch.from_numpy(np.stack([gt_host_list[pi] for pi in pl])).to(dev) for k, pl in groups.items()}
+    lams = {k: torch.tensor([float(np.float32(wl.pairs[pi].lam)) for pi in pl], device=dev)
+            for k, pl in groups.items()}
+
+    def step(with_bwd: bool):
+        feats = [v[2].float().requires_grad_(with_bwd) for v in views]
+        a = [v[0].t() @ (v[1][:, None] * f) for v, f in zip(views, feats)]
+        loss = 0.0
+        for k, pl in groups.items():
+            ax = torch.stack([a[wl.pairs[pi].x] for pi in pl])
+            ay = torch.stack([a[wl.pairs[pi].y] for pi in pl])
+            ex = torch.stack([views[wl.pairs[pi].x][3] for pi in pl])
+            ey = torch.stack([views[wl.pairs[pi].y][3] for pi in pl])
+            g = ax @ ax.transpose(1, 2)
+            r = ay @ ax.transpose(1, 2)
+            dmask = (ey[:, :, None] - ex[:, None, :]) ** 2
+            sysm = g[:, None] + lams[k][:, None, None, None] * torch.diag_embed(dmask)
+            c = torch.linalg.solve(sysm, r.unsqueeze(-1)).squeeze(-1)
+            eye = torch.eye(k, device=dev)
+            loss = loss + ((c @ c.transpose(1, 2) - eye) ** 2).sum() + ((c - gts[k]) ** 2).sum()
+        if with_bwd:
+            loss.backward()
+        return loss
+
+    out = []
+    for with_bwd in (True, False):
+        with torch.set_grad_enabled(with_bwd):
+            for _ in range(warmup):
+                step(with_bwd)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                step(with_bwd)
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1) / steps)
+    npairs = len(wl.pairs)
+    return npairs / (out[0] / 1000.0), npairs / (out[1] / 1000.0), out[0], out[1]
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -243,14 +305,12 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def timed(fn, steps, sampler=None, timing=False):
+    def timed(fn, steps, timing=False):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize(); barrier(); torch.cuda.synchronize()
         if timing:
             b.set_timing(True)
-        if sampler:
-            sampler.start()
         st = torch.cuda.current_stream(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
@@ -258,14 +318,13 @@ def run_ours(args):
             fn()
         e1.record(st)
         torch.cuda.synchronize()
-        clocks = sampler.stop() if sampler else None
         kt = b.read_timing() if timing else None
         if timing:
             b.set_timing(False)
         barrier()
         # whole job: pairs of all ranks over the slowest rank's time
         rate, ms, _ = shard.job_throughput(float(npairs), e0.elapsed_time(e1) / steps)
-        return ms, clocks, kt, rate
+        return ms, None, kt, rate
 
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", ""))
@@ -273,8 +332,31 @@ def run_ours(args):
         uuid = "GPU-" + uuid
     sampler = ClockSampler(uuid) if uuid else None
 
-    ms_step, clocks, ktime, rate_step = timed(step, args.steps, sampler=sampler, timing=True)
-    ms_fwd, _, _, rate_fwd = timed(fwd_step, args.steps)
+    if sampler:
+        sampler.start()
+    # eager pass with the library's per-kind event timing (the kernel breakdown)
+    ms_eager, _, ktime, rate_eager = timed(step, args.steps, timing=True)
+    if args.no_graph:
+        ms_step, rate_step = ms_eager, rate_eager
+        ms_fwd, _, _, rate_fwd = timed(fwd_step, args.steps)
+    else:
+        # the step as one CUDA graph: every C-ABI call only enqueues, so it captures
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            step()
+            fwd_step()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize()
+        g_step, g_fwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_step):
+            step()
+        with torch.cuda.graph(g_fwd):
+            fwd_step()
+        torch.cuda.synchronize()
+        ms_step, _, _, rate_step = timed(g_step.replay, args.steps)
+        ms_fwd, _, _, rate_fwd = timed(g_fwd.replay, args.steps)
+    clocks = sampler.stop() if sampler else None
     status = b.status[:npairs].cpu().numpy()
 
     # ---- end to end: host inputs -> device, step, loss and C back to the host
@@ -347,6 +429,15 @@ def run_ours(args):
                     "tolerance": 3e-3 if wl.feat_dtype == "bf16" else 1e-5,
                     "reference": "FP64 oracle on the same inputs"}
 
+    torch_cmp = None
+    if rank == 0 and not args.no_torch_compare:
+        v_fb, v_f, ms_fb, ms_f = torch_restatement(lay, b, wl, [p.c_gt for p in wl.pairs], dev, 3, 1)
+        torch_cmp = {"value": v_fb, "unit": "pairs/s", "ms_per_step": ms_fb,
+                     "fwd_only": {"value": v_f, "unit": "pairs/s", "ms_per_step": ms_f},
+                     "what": "plain PyTorch FP32 ops on the same GPU (diag_embed + torch.linalg.solve, autograd)"}
+        del v_fb, v_f
+        torch.cuda.empty_cache()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": rate_step, "unit": "pairs/s", "n_gpus": world,
@@ -356,11 +447,14 @@ def run_ours(args):
                        "parallelism": f"pairs sharded over {world} GPU(s), no collective",
                        "l2": "inputs larger than L2 (%.1f GB streamed per step)" % (work["project"]["bytes"] / 1e9)},
             "fwd_only": {"value": rate_fwd, "unit": "pairs/s", "ms_per_step": ms_fwd},
+            "launch": "eager" if args.no_graph else "one CUDA graph per step",
+            "eager": {"value": rate_eager, "unit": "pairs/s", "ms_per_step": ms_eager},
             "roofline": roofline,
             "roofline_other": others,
             "kernels": kernels,
             "gpu_launches": int(launches_total),
             "cpu_baseline": cpu,
+            "torch_restatement": torch_cmp,
             "accuracy": accuracy,
             "e2e": e2e,
             "clocks": clocks,
@@ -375,7 +469,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=4, choices=sorted(WORKLOADS))
@@ -384,6 +478,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-torch-compare", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of one CUDA graph per step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

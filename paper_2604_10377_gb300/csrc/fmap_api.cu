@@ -264,7 +264,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   }
   for (auto& pd : P.pairs) {
     const int64_t kk = (int64_t)pd.k * pd.k;
-    pd.g_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    pd.g_off = cur; cur = align_up(cur + gram_floats(pd.k), kAlignFloats);
     pd.r_off = cur; cur = align_up(cur + kk, kAlignFloats);
     pd.e_off = cur; cur = align_up(cur + kk, kAlignFloats);
     if (pd.hi_gram) {
@@ -352,9 +352,10 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       P.bw_cta_first[n_clusters] = (int32_t)(P.bw_items.size() / 2);
     }
     const int fixed = 1024 + 512;
-    P.bw_stages = std::min(6, (kSmemBudget - fixed - (int)P.bw_b_bytes) / 16384);
+    const int out_staging = 8 * 4096;   // BF16 dF staging of the eight epilogue warps
+    P.bw_stages = std::min(6, (kSmemBudget - fixed - out_staging - (int)P.bw_b_bytes) / 16384);
     if (!P.bw_items.empty() && P.bw_stages < 2) return FMAP_ERR_UNSUPPORTED;
-    P.bw_smem = fixed + (int)P.bw_b_bytes + P.bw_stages * 16384;
+    P.bw_smem = fixed + out_staging + (int)P.bw_b_bytes + P.bw_stages * 16384;
   }
   const int64_t ws_bwd = std::max(cur, ws_fwd);
 
@@ -461,6 +462,7 @@ struct fmap_batch {
   const TcRedGroup* d_tc_groups = nullptr;
   const CUtensorMap* d_phimaps_fwd = nullptr;
   const CUtensorMap* d_massmaps = nullptr;
+  const CUtensorMap* d_dfmaps = nullptr;
   const TcBwdItem* d_bw_items = nullptr;
   const int32_t* d_bw_cta_first = nullptr;
   const TcBwdGroup* d_bw_groups = nullptr;
@@ -588,7 +590,8 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_tg = o_to + bytes_of(P.tc_cta_first.size(), sizeof(int32_t));
   const int64_t o_fp = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
   const int64_t o_mm = o_fp + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
-  const int64_t o_bi = o_mm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_dm = o_mm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_bi = o_dm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
   const int64_t o_bg = o_bo + bytes_of(P.bw_cta_first.size(), sizeof(int32_t));
   const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
@@ -652,6 +655,21 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
         return FMAP_ERR_CUDA;
       }
       put(o_mm + s * (int64_t)sizeof(CUtensorMap), &mm, sizeof(mm));
+      // BF16 dF: box 16 features x 32 vertices, stored by the backward projection
+      CUtensorMap dm;
+      std::memset(&dm, 0, sizeof(dm));
+      if (sd.dfeat) {
+        cuuint32_t dbox[2] = {16, 32};
+        r = encode(&dm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sd.dfeat, gdim, gstride, dbox, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+          cudaFree(b->dev_mem); delete b;
+          std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled(dF) failed (%d)", (int)r);
+          return FMAP_ERR_CUDA;
+        }
+      }
+      put(o_dm + s * (int64_t)sizeof(CUtensorMap), &dm, sizeof(dm));
     }
     put(o_bi, P.bw_items.data(), P.bw_items.size() * sizeof(TcBwdItem));
     put(o_bo, P.bw_cta_first.data(), P.bw_cta_first.size() * sizeof(int32_t));
@@ -688,6 +706,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_tc_groups = reinterpret_cast<const TcRedGroup*>(base + o_tg);
   b->d_phimaps_fwd = reinterpret_cast<const CUtensorMap*>(base + o_fp);
   b->d_massmaps = reinterpret_cast<const CUtensorMap*>(base + o_mm);
+  b->d_dfmaps = reinterpret_cast<const CUtensorMap*>(base + o_dm);
   b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
   b->d_bw_cta_first = reinterpret_cast<const int32_t*>(base + o_bo);
   b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
@@ -892,6 +911,7 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     TcBwdParams bp{};
     bp.shapes = b->dev.shapes;
     bp.phimaps = b->d_phimaps_fwd;
+    bp.dfmaps = b->d_dfmaps;
     bp.items = b->d_bw_items;
     bp.cta_first = b->d_bw_cta_first;
     bp.stages = P.bw_stages;

@@ -35,6 +35,12 @@ struct ShapeDev {
 };
 
 // Device copy of a pair descriptor plus workspace offsets.
+// Row stride (floats) of the FP32 Gram matrix G in the workspace: k rounded up to 4,
+// so that every row starts on a 16-byte boundary (bulk copies into shared memory).
+// The region holds k rows plus 8 floats of slack past the last row.
+__host__ __device__ __forceinline__ int gram_ld(int k) { return (k + 3) & ~3; }
+__host__ __device__ __forceinline__ int64_t gram_floats(int k) { return (int64_t)k * gram_ld(k) + 8; }
+
 struct PairDev {
   int32_t x, y;
   int32_t k, d;
@@ -42,7 +48,7 @@ struct PairDev {
   int32_t hi_gram;     // 1: Gram matrix accumulated in FP64
   const float* mask;   // k x k or nullptr (use eigenvalues)
   int64_t c_off;       // float offset of C_p / dC_p in the flat k x k buffers
-  int64_t g_off;       // float offset (workspace) of G = A_x A_x^T  (k x k)
+  int64_t g_off;       // float offset (workspace) of G = A_x A_x^T  (k x k, row stride gram_ld(k))
   int64_t r_off;       // float offset (workspace) of R = A_y A_x^T  (k x k)
   int64_t g64_off;     // float2 offset (workspace) of the double-float (hi, lo) Gram, or -1
   int64_t gam_off;     // float offset (workspace) of Gamma (k x k)
@@ -127,6 +133,7 @@ struct TcBwdGroup {
 struct TcBwdParams {
   const ShapeDev* shapes;
   const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 64, 128-byte swizzle
+  const CUtensorMap* dfmaps;   // per shape: BF16 dF, box 16 x 32, no swizzle (TMA stores)
   const TcBwdItem* items;       // item j of a cluster: [2 j] for CTA rank 0, [2 j + 1] for rank 1
   const int32_t* cta_first;     // cluster c (CTAs 2c, 2c + 1) owns items [cta_first[c], cta_first[c + 1])
   int32_t stages;

@@ -44,7 +44,7 @@ Layout layout_for(int k, bool hi) {
   L.shapes = cur; cur = align_up(cur + (int64_t)(2 * sizeof(ShapeDev) + 3) / 4, kAlign);
   L.pair = cur; cur = align_up(cur + (int64_t)(sizeof(PairDev) + 3) / 4, kAlign);
   L.systems = cur; cur = align_up(cur + 2 * (int64_t)k, kAlign);
-  L.g = cur; cur = align_up(cur + (int64_t)k * k, kAlign);
+  L.g = cur; cur = align_up(cur + gram_floats(k), kAlign);
   L.r = cur; cur = align_up(cur + (int64_t)k * k, kAlign);
   if (hi) { L.ghl = cur; cur = align_up(cur + 2 * (int64_t)k * k, kAlign); } else { L.ghl = -1; }
   L.end = cur;

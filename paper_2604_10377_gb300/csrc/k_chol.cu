@@ -4,22 +4,28 @@
 // S_i is padded to kp = k rounded up to 8 (identity in the padding) and kept in
 // shared memory as packed lower rows: row a holds 8 (a/8 + 1) + 4 floats, so a
 // row's 8-column tile segment is two aligned float4 and consecutive rows fall on
-// different banks. The factorisation is a blocked right-looking Cholesky in FP32
-// with 8-column panels and one panel of lookahead:
+// different banks. Each row's segment is bulk-copied (cp.async.bulk) straight from
+// G, then lambda D_i is added to the diagonal. The factorisation is a blocked
+// right-looking Cholesky in FP32 with 8-column panels and one panel of lookahead:
 //   TRSM     every thread solves one row of panel J below its diagonal block,
-//            x = s L_JJ^-T, as a product with the stored inverse block;
-//   (a)      every thread updates one row of the next column block J+1;
+//            x = s L_JJ^-T, as a product with the stored inverse block; one warp
+//            applies L_JJ^-1 to the right-hand side (forward substitution bordered
+//            into the factorisation);
+//   (a)      every thread updates one row of the next column block J+1 and its
+//            right-hand side entry;
 //   (b)      warp 0 factors the diagonal block J+1 in registers and stores its
 //            inverse, while the other warps update the rest of the trailing matrix
-//            in 8 x 8 register tiles, S_AB -= L_AJ L_BJ^T.
-// Three block barriers per panel. Forward and back substitution are done by
-// warp 0 with the inverse diagonal blocks (no dependency chain inside a block);
-// then `ir_steps` steps of iterative refinement with the residual rhs - S x in
-// FP32; for hi_gram pairs the residual takes G as the two FP32 halves (hi + lo)
-// of its double-float accumulation.
+//            in 8x8, 8x4 or 4x4 register tiles (whichever balances best),
+//            S_AB -= L_AJ L_BJ^T.
+// (a) and (b) touch disjoint blocks, so a panel costs two block barriers. The back
+// substitution and the refinement's triangular solves use every warp with the inverse
+// diagonal blocks (one barrier per block); `ir_steps` steps of iterative refinement
+// take the residual rhs - S x in FP32, for hi_gram pairs with G as the two FP32
+// halves (hi + lo) of its double-float accumulation.
 #include <math.h>
 
 #include "fmap_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fmap {
 namespace {
@@ -95,6 +101,58 @@ __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lan
   }
   __syncwarp();
   return !bad;
+}
+
+// Row index of entry t of a lower triangle enumerated row by row (t = a(a+1)/2 + b).
+__device__ __forceinline__ void tri_decode(int t, int& a, int& b) {
+  int ai = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((ai + 1) * (ai + 2) / 2 <= t) ++ai;
+  while (ai * (ai + 1) / 2 > t) --ai;
+  a = ai;
+  b = t - ai * (ai + 1) / 2;
+}
+
+// S[A.., B..] -= L[A.., J] L[B.., J]^T for one R x C tile (R, C in {4, 8}), with the
+// panel's 8 columns read from `pan` (column-major, leading dimension kp).
+template <int R, int C>
+__device__ __forceinline__ void trail_tile(float* S, const float* pan, int kp, int A, int B) {
+  float acc[R][C];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float4* sr = reinterpret_cast<const float4*>(S + rowoff(A + r) + B);
+#pragma unroll
+    for (int h = 0; h < C / 4; ++h) {
+      const float4 u = sr[h];
+      acc[r][4 * h] = u.x; acc[r][4 * h + 1] = u.y; acc[r][4 * h + 2] = u.z; acc[r][4 * h + 3] = u.w;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float la[R], lb[C];
+    const float4* pa = reinterpret_cast<const float4*>(pan + c * kp + A);
+    const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + B);
+#pragma unroll
+    for (int h = 0; h < R / 4; ++h) {
+      const float4 u = pa[h];
+      la[4 * h] = u.x; la[4 * h + 1] = u.y; la[4 * h + 2] = u.z; la[4 * h + 3] = u.w;
+    }
+#pragma unroll
+    for (int h = 0; h < C / 4; ++h) {
+      const float4 u = pb[h];
+      lb[4 * h] = u.x; lb[4 * h + 1] = u.y; lb[4 * h + 2] = u.z; lb[4 * h + 3] = u.w;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int q = 0; q < C; ++q) acc[r][q] = fmaf(-la[r], lb[q], acc[r][q]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float4* sr = reinterpret_cast<float4*>(S + rowoff(A + r) + B);
+#pragma unroll
+    for (int h = 0; h < C / 4; ++h)
+      sr[h] = make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+  }
 }
 
 // v <- L^{-1} v with every thread of the block (NT >= kp): thread t updates row
@@ -185,10 +243,12 @@ __device__ __forceinline__ void block_bwd(const float* S, const float* linv, flo
 template <int NT>
 __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
     chol_solve_kernel(BatchDev b, const int2* systems, int first, int count, int mode, const float* rhs_flat,
-                      float* out_flat, float* saved, int32_t* status, float* ws) {
+                      float* out_flat, float* saved, int32_t* status, float* ws, int gs_ok) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_bad;
+  __shared__ __align__(8) uint64_t s_bar;   // bulk copies of the Gram rows
+  __shared__ int s_abort;
   if ((int)blockIdx.x >= count) return;
   const int2 sys = systems[first + blockIdx.x];
   const int p = sys.x, i = sys.y;
@@ -205,56 +265,73 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
   float* v = pan + 8 * kp;         // working vector
   float* xs = v + kp;              // solution
   float* rh = xs + kp;             // right-hand side
+  float* Gs = rh + kp;             // copy of G for the refinement residual (launches with gs_ok)
   const float* G = ws + pd.g_off;
+  const int ldg = gram_ld(k);
   const float2* Ghl = pd.g64_off >= 0 ? reinterpret_cast<const float2*>(ws) + pd.g64_off : nullptr;
   const float* rhs = (mode == kSolveForward) ? ws + pd.r_off + (int64_t)i * k : rhs_flat + pd.c_off + (int64_t)i * k;
   float* out = (mode == kSolveForward) ? out_flat + pd.c_off + (int64_t)i * k : ws + pd.gam_off + (int64_t)i * k;
   const int fsz = factor_floats(Q);
   float* fac = (saved != nullptr && pd.fac_off >= 0) ? saved + pd.fac_off + (int64_t)i * fsz : nullptr;
   const float lam = pd.lam;
+  const int n_ir = mode == kSolveForward ? b.ir_steps : b.ir_steps_adj;
+  // small FP32-Gram systems keep G in shared memory for the refinement residual
+  const bool use_gs = gs_ok != 0 && Ghl == nullptr && n_ir > 0;
+  const uint32_t gs_bytes = use_gs ? (uint32_t)k * (uint32_t)ldg * 4u : 0u;
 
   if (tid == 0) {
     s_bad = 0;
+    s_abort = 0;
+    tc::mbar_init(&s_bar, 1);
+    tc::fence_mbar_init();
     // a projection wait that timed out leaves its error in the workspace's first word
     if (i == 0 && reinterpret_cast<const int*>(ws)[0] != 0) set_status(status, p, FMAP_ERR_TIMEOUT);
   }
   for (int a = tid; a < kp; a += NT) rh[a] = a < k ? rhs[a] : 0.f;
 
   if (mode == kSolveAdjoint && fac != nullptr) {
-    for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
-    __syncthreads();
-  } else {
-    // S = G + lambda diag(D_i), identity in the padding rows; one warp per row, four
-    // rows' loads in flight before any store
-    for (int a0 = warp; a0 < kp; a0 += 4 * NW) {
-      float val[4][kMaxK / 32];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int a = a0 + u * NW;
-        const float* grow = G + (int64_t)a * k;
-#pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-          const int c = lane + 32 * q;
-          val[u][q] = (a < k && c < a) ? grow[c] : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int a = a0 + u * NW;
-        if (a >= kp) break;
-        float* row = S + rowoff(a);
-        const int len = (a & ~7) + 8;
-#pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-          const int c = lane + 32 * q;
-          if (c < len) {
-            float x = val[u][q];
-            if (c == a) x = a < k ? G[(int64_t)a * k + a] + lam * mask_entry(pd, evx, evy, i, a) : 1.f;
-            row[c] = x;
-          }
-        }
+    if (use_gs) {
+      __syncthreads();   // barrier initialised
+      if (tid == 0) {
+        tc::mbar_arrive_expect_tx(&s_bar, gs_bytes);
+        tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
       }
     }
+    for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
+    if (use_gs && !tc::mbar_wait(&s_bar, 0, &s_abort)) {
+      if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
+      const uint64_t t0 = tc::globaltimer();
+      while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}
+      return;
+    }
+    __syncthreads();
+  } else {
+    // S = G + lambda diag(D_i). Row a's packed segment (columns 0 .. end of its
+    // diagonal block) is bulk-copied from G; the entries above the diagonal inside a
+    // diagonal block are never read. Padding rows are identity rows.
+    __syncthreads();   // barrier initialised
+    if (warp == 0) {
+      if (lane == 0) {
+        const int qf = k >> 3, rem = k & 7;
+        tc::mbar_arrive_expect_tx(&s_bar, (uint32_t)(32 * qf * (qf + 1) + 8 * rem * (qf + 1)) * 4u + gs_bytes);
+        if (use_gs) tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
+      }
+      __syncwarp();
+      for (int a = lane; a < k; a += 32)
+        tc::bulk_g2s(S + rowoff(a), G + (int64_t)a * ldg, (uint32_t)((a & ~7) + 8) * 4u, &s_bar);
+    }
+    for (int a = k + tid; a < kp; a += NT) {
+      float* row = S + rowoff(a);
+      for (int c = 0; c < (a & ~7) + 8; ++c) row[c] = (c == a) ? 1.f : 0.f;
+    }
+    if (!tc::mbar_wait(&s_bar, 0, &s_abort)) {
+      // copies that never completed: report, give them a bounded time to land, leave
+      if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
+      const uint64_t t0 = tc::globaltimer();
+      while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}
+      return;
+    }
+    for (int a = tid; a < k; a += NT) S[rowoff(a) + a] += lam * mask_entry(pd, evx, evy, i, a);
     for (int a = tid; a < kp; a += NT) v[a] = rh[a];   // right-hand side, reduced during the factorisation
     __syncthreads();
     if (warp == 0 && !diag_block(S, linv, 0, lane) && lane == 0) s_bad = 1;
@@ -262,8 +339,10 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
     for (int J = 0; J < Q && !s_bad; ++J) {
       const int r0 = 8 * J;
       const float* li = linv + J * 64;
-      // forward substitution, bordered into the factorisation: y_J = L_JJ^-1 v_J
-      if (warp == 0) {
+      // forward substitution, bordered into the factorisation: y_J = L_JJ^-1 v_J, on the
+      // last warp when it has no panel rows (off the TRSM's critical path), else warp 0
+      const int yw = (r0 + 8 + (NW - 1) * 32 >= kp) ? NW - 1 : 0;
+      if (warp == yw) {
         float y = 0.f;
         if (lane < 8)
 #pragma unroll
@@ -314,44 +393,37 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
         ra[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
         v[a] = va;
       }
-      __syncthreads();
+      // (a) writes column block J+1 and (b)'s tiles touch only blocks J+2.. (both read the
+      // panel), so no block barrier separates them: warp 0 updated the diagonal block's
+      // rows itself (threads 0-7) and factors it right away
+      __syncwarp();
       // (b) warp 0: next diagonal block; warps 1..: trailing tiles (A, B), J+2 <= B <= A < Q
       if (warp == 0) {
         if (!diag_block(S, linv, J + 1, lane) && lane == 0) s_bad = 1;
       } else {
+        // trailing blocks (A, B), J+2 <= B <= A < Q, as 8x8, 8x4 or 4x4 register tiles:
+        // the size whose rounds over the NT - 32 threads cost the fewest instructions
         const int m = Q - J - 2;
-        const int T = m * (m + 1) / 2;
-        for (int t = tid - 32; t < T; t += NT - 32) {
-          int ai = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-          while ((ai + 1) * (ai + 2) / 2 <= t) ++ai;
-          while (ai * (ai + 1) / 2 > t) --ai;
-          const int bi = t - ai * (ai + 1) / 2;
-          const int A = 8 * (J + 2 + ai), B = 8 * (J + 2 + bi);
-          float acc[8][8];
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const float4* sr = reinterpret_cast<const float4*>(S + rowoff(A + r) + B);
-            const float4 u0 = sr[0], u1 = sr[1];
-            acc[r][0] = u0.x; acc[r][1] = u0.y; acc[r][2] = u0.z; acc[r][3] = u0.w;
-            acc[r][4] = u1.x; acc[r][5] = u1.y; acc[r][6] = u1.z; acc[r][7] = u1.w;
+        const int nb = NT - 32, t0 = tid - 32, base = 8 * (J + 2);
+        const int T88 = m * (m + 1) / 2, T84 = 2 * T88, T44 = m * (2 * m + 1);
+        const int c88 = (T88 + nb - 1) / nb * 576, c84 = (T84 + nb - 1) / nb * 296, c44 = (T44 + nb - 1) / nb * 152;
+        if (c88 <= c84 && c88 <= c44) {
+          for (int t = t0; t < T88; t += nb) {
+            int ai, bi;
+            tri_decode(t, ai, bi);
+            trail_tile<8, 8>(S, pan, kp, base + 8 * ai, base + 8 * bi);
           }
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float4* pa = reinterpret_cast<const float4*>(pan + c * kp + A);
-            const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + B);
-            const float4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
-            const float la[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float lb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-              for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(-la[r], lb[q], acc[r][q]);
+        } else if (c84 <= c44) {
+          for (int t = t0; t < T84; t += nb) {
+            int ai, bi;
+            tri_decode(t >> 1, ai, bi);
+            trail_tile<8, 4>(S, pan, kp, base + 8 * ai, base + 8 * bi + 4 * (t & 1));
           }
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            float4* sr = reinterpret_cast<float4*>(S + rowoff(A + r) + B);
-            sr[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-            sr[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+        } else {
+          for (int t = t0; t < T44; t += nb) {
+            int ai, bi;
+            tri_decode(t, ai, bi);
+            trail_tile<4, 4>(S, pan, kp, base + 4 * ai, base + 4 * bi);
           }
         }
       }
@@ -378,7 +450,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
   __syncthreads();
 
   // iterative refinement: x += S^{-1} (rhs - S x); four rows of G in flight per warp
-  const int n_ir = mode == kSolveForward ? b.ir_steps : b.ir_steps_adj;
+  const float* Gres = use_gs ? Gs : G;
   for (int it = 0; it < n_ir; ++it) {
     for (int a0 = warp; a0 < kp; a0 += 4 * NW) {
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
@@ -408,7 +480,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
 #pragma unroll
           for (int q = 0; q < kMaxK / 32; ++q) {
             const int c = lane + 32 * q;
-            g[u][q] = (a < k && c < k) ? G[(int64_t)a * k + c] : 0.f;
+            g[u][q] = (a < k && c < k) ? Gres[(int64_t)a * ldg + c] : 0.f;
           }
         }
 #pragma unroll
@@ -444,9 +516,13 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
   if (!finite) set_status(status, p, FMAP_ERR_NONFINITE | (i << 8));
 }
 
+// Launches for k <= kGsMaxK reserve a copy of G (k x gram_ld(k) floats) after the vectors.
+constexpr int kGsMaxK = 128;
+
 size_t chol_smem_bytes(int kmax) {
   const int Q = (kmax + 7) / 8, kp = 8 * Q;
-  return (size_t)(factor_floats(Q) + 8 * kp + 3 * kp) * sizeof(float);
+  const int64_t gs = kmax <= kGsMaxK ? (int64_t)kmax * gram_ld(kmax) : 0;
+  return (size_t)(factor_floats(Q) + 8 * kp + 3 * kp + gs) * sizeof(float);
 }
 
 template <int NT>
@@ -470,18 +546,19 @@ cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* sys
                          float* out_flat, float* saved, int32_t* status, float* ws, cudaStream_t st) {
   if (g.count <= 0) return cudaSuccess;
   const size_t smem = chol_smem_bytes(g.kmax);
+  const int gs = g.kmax <= kGsMaxK ? 1 : 0;
   switch (g.threads) {
     case 64:
       chol_solve_kernel<64><<<g.count, 64, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat, saved,
-                                                       status, ws);
+                                                       status, ws, gs);
       break;
     case 128:
       chol_solve_kernel<128><<<g.count, 128, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat,
-                                                         saved, status, ws);
+                                                         saved, status, ws, gs);
       break;
     default:
       chol_solve_kernel<256><<<g.count, 256, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat,
-                                                         saved, status, ws);
+                                                         saved, status, ws, gs);
       break;
   }
   return cudaGetLastError();

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
     if (ti >= nt) return;
     const int i0 = ti * kT, j0 = tj * kT;
     float* g = ws + pd.g_off;
+    const int ldg = gram_ld(k);
     float2* ghl = pd.hi_gram ? reinterpret_cast<float2*>(ws) + pd.g64_off : nullptr;
     if (pd.hi_gram)
       gram_tile<true>(ax, ax, k, d, i0, j0, hi, lo);
@@ -98,8 +99,8 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
           v = __fadd_rn(hi[r][c], lo[r][c]);
           e = __fsub_rn(lo[r][c], __fsub_rn(v, hi[r][c]));
         }
-        g[(int64_t)i * k + j] = v;
-        g[(int64_t)j * k + i] = v;
+        g[(int64_t)i * ldg + j] = v;
+        g[(int64_t)j * ldg + i] = v;
         if (ghl) {
           ghl[(int64_t)i * k + j] = make_float2(v, e);
           ghl[(int64_t)j * k + i] = make_float2(v, e);

@@ -28,12 +28,8 @@ constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each storing half o
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kTileV = 128;                       // vertices per output tile (MMA M)
 constexpr uint32_t kAStageBytes = kTileV * 128;   // 128 rows x 32 fp32
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(tc::smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
-               : "memory");
-}
+constexpr uint32_t kOutChunkBytes = 32 * 32;      // 32 rows x 16 BF16: one TMA store box
+constexpr uint32_t kOutWarpBytes = 4 * kOutChunkBytes;   // <= 4 chunks of 16 features per warp and tile
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -56,7 +52,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   const int S = P.stages;
   uint8_t* sB = smem;                                   // resident dA^T image of this CTA's feature group
   uint8_t* sA = sB + P.b_bytes_max;                     // Phi tiles, S stages (same offset in both CTAs)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)S * kAStageBytes);
+  uint8_t* sOut = sA + (size_t)S * kAStageBytes;        // BF16 dF staging, kOutWarpBytes per epilogue warp
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sOut + (size_t)kEpiWarps * kOutWarpBytes);
   uint64_t* a_full = bars;
   uint64_t* a_empty = bars + S;
   uint64_t* b_full = bars + 2 * S;
@@ -110,7 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
           tc::mbar_arrive_expect_tx(b_full, bbytes);
           const uint8_t* src = reinterpret_cast<const uint8_t*>(P.ws + item.img_off);
           for (uint32_t off = 0; off < bbytes; off += 16384u)
-            bulk_g2s(sB + off, src + off, (bbytes - off) < 16384u ? (bbytes - off) : 16384u, b_full);
+            tc::bulk_g2s(sB + off, src + off, (bbytes - off) < 16384u ? (bbytes - off) : 16384u, b_full);
         } else {
           tc::mbar_arrive(b_full);
         }
@@ -185,43 +182,57 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
     }
   } else {
     // ------------------------------------------------------------ epilogue: TMEM -> M * acc -> BF16 dF
+    // Each warp converts its 32 rows x (its chunks of 16 features) into shared memory
+    // and one lane writes them with TMA stores (full-line writes, rows past n clipped).
     const int quarter = warp & 3, half = (warp - 2) >> 2;
+    uint8_t* stage_out = sOut + (size_t)(warp - 2) * kOutWarpBytes;
     uint32_t acc_phase[2] = {0, 0};
     int buf = 0;
     for (int it = it_beg; it < it_end; ++it) {
       const TcBwdItem item = P.items[2 * it + rank];
       const ShapeDev s = P.shapes[item.shape];
-      __nv_bfloat16* df = reinterpret_cast<__nv_bfloat16*>(s.dfeat);
+      const CUtensorMap* dmap = P.dfmaps + item.shape;
       const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
       for (int t = 0; t < ntiles; ++t) {
         // the row's mass is loaded before the accumulator wait, so its latency is hidden
-        const int64_t v = item.v0 + (int64_t)t * kTileV + quarter * 32 + lane;
-        const bool vok = v < item.v1;
-        const float m = vok ? __ldg(s.mass + v) : 0.f;
+        const int64_t vrow0 = item.v0 + (int64_t)t * kTileV + quarter * 32;
+        const int64_t v = vrow0 + lane;
+        const float m = v < item.v1 ? __ldg(s.mass + v) : 0.f;
         if (!tc::mbar_wait(&acc_full[buf], acc_phase[buf], abort_flag)) goto epi_done;
         tc::tc_fence_after();
-        for (int ch = half; ch < item.nf / 16; ch += 2) {
+        // the previous tile's stores have read the staging buffer
+        if (lane == 0) tc::bulk_wait_group_read0();
+        __syncwarp();
+        int j = 0;
+        for (int ch = half; ch < item.nf / 16; ch += 2, ++j) {
           float x[16];
           tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + ch * 16), x);
-          if (vok) {
-            uint32_t w[8];
+          uint32_t w[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              w[j] = __bfloat16_as_ushort(__float2bfloat16_rn(x[2 * j] * m)) |
-                     ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * j + 1] * m)) << 16);
-            uint4* dst = reinterpret_cast<uint4*>(df + v * s.ld_feat + item.f0 + ch * 16);
-            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-          }
+          for (int q = 0; q < 8; ++q)
+            w[q] = __bfloat16_as_ushort(__float2bfloat16_rn(x[2 * q] * m)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * q + 1] * m)) << 16);
+          uint4* dst = reinterpret_cast<uint4*>(stage_out + j * kOutChunkBytes + lane * 32);
+          dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
         }
         tc::tc_fence_before();
+        tc::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+        if (lane == 0 && vrow0 < s.n) {
+          j = 0;
+          for (int ch = half; ch < item.nf / 16; ch += 2, ++j)
+            tc::tma_store_2d(dmap, stage_out + j * kOutChunkBytes, item.f0 + ch * 16, (int)vrow0);
+          tc::bulk_commit_group();
+        }
         acc_phase[buf] ^= 1;
         buf ^= 1;
       }
     }
-  epi_done:;
+  epi_done:
+    // every TMA store of this warp has completed before the CTA exits
+    if (lane == 0) tc::bulk_wait_group0();
   }
 
   __syncthreads();
