@@ -52,6 +52,39 @@ def load_peaks():
                     source="fallback")
 
 
+# DRAM traffic per step of each kernel kind, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), committed with the SHA-256 of the kernel source it was taken
+# on (the kernel's file followed by the two shared headers); a kind whose source changed
+# since reports null.
+TRAFFIC_FILES = {4: "profiles/traffic_ragged256_k30-200_d256.txt"}
+KIND_SOURCES = {"project": "k_project_tc.cu", "project_bwd": "k_project_bwd_tc.cu", "solve": "k_chol.cu",
+                "adj_solve": "k_chol.cu"}
+
+
+def load_traffic(workload: int) -> dict:
+    import hashlib
+    out = {}
+    rel = TRAFFIC_FILES.get(workload)
+    if not rel or not os.path.exists(os.path.join(ROOT, rel)):
+        return out
+    csrc = os.path.join(ROOT, "paper_2604_10377_gb300", "csrc")
+    for line in open(os.path.join(ROOT, rel)):
+        parts = line.split()
+        if len(parts) != 4 or line.startswith("#"):
+            continue
+        kind, src, sha, nbytes = parts
+        try:
+            h = hashlib.sha256()
+            for f in (src, "fmap_internal.cuh", "tc_ptx.cuh"):
+                h.update(open(os.path.join(csrc, f), "rb").read())
+            cur = h.hexdigest()
+        except OSError:
+            continue
+        if cur == sha:
+            out[kind] = int(nbytes)
+    return out
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -120,13 +153,21 @@ def algorithmic_work(wl, ir_steps, saved_k_max):
     proj_flops = sum(2.0 * s.n * s.k * s.d for s in wl.shapes)
     bwd_bytes = sum(s.n * (4 * s.k + 4 + fsz * s.d) + 4 * s.k * s.d for s in wl.shapes)
     solve_flops, adj_flops, loss_flops = 0.0, 0.0, 0.0
+    solve_bytes, adj_bytes = 0, 0
     for p in wl.pairs:
-        k = wl.shapes[p.x].k
+        k, d = wl.shapes[p.x].k, wl.shapes[p.x].d
+        kp = (k + 7) // 8 * 8
+        q = kp // 8
+        fac = 4 * k * (32 * q * (q + 2) + 64 * q) if k <= saved_k_max else 0
         solve_flops += k ** 4 / 3.0 + (2.0 + 4.0 * ir_steps) * k ** 3
         adj_flops += (0.0 if k <= saved_k_max else k ** 4 / 3.0) + 2.0 * k ** 3
         loss_flops += 4.0 * k ** 3
+        # G and R read once, C written once, saved factors written (forward) / read (adjoint)
+        solve_bytes += 4 * 3 * k * k + fac
+        adj_bytes += 4 * 2 * k * k + fac
     return dict(project=dict(bytes=proj_bytes, flops=proj_flops), project_bwd=dict(bytes=bwd_bytes, flops=proj_flops),
-                solve=dict(flops=solve_flops), adj_solve=dict(flops=adj_flops), loss=dict(flops=loss_flops))
+                solve=dict(flops=solve_flops, bytes=solve_bytes), adj_solve=dict(flops=adj_flops, bytes=adj_bytes),
+                loss=dict(flops=loss_flops))
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -388,13 +429,15 @@ def run_ours(args):
     launches_total = sum(v[1] for v in ktime.values())
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
 
+    traffic = load_traffic(args.workload)
+
     def roof_for(kind):
         # the launches of one kind in one step process the batch once: the unit is the step
         per_step_ms = ktime[kind][0] / args.steps
         if kind in ("project", "project_bwd"):
             ach = work[kind]["bytes"] / (per_step_ms / 1000.0) / 1e9
             return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic.get(kind),
                     "peak_source": f"{peaks['source']} HBM copy bandwidth"}
         flops = work.get(kind, {}).get("flops")
         if flops is None:
@@ -402,7 +445,8 @@ def run_ours(args):
                     "frac": None, "traffic": None}
         ach = flops / (per_step_ms / 1000.0) / 1e12
         return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak_tflops, "traffic": None,
+                "frac": ach / fp32_peak_tflops, "traffic": traffic.get(kind),
+                "algorithmic_bytes": work.get(kind, {}).get("bytes"),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
 
     roofline = roof_for(dom)

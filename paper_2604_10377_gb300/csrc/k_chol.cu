@@ -49,17 +49,22 @@ __device__ __forceinline__ void set_status(int32_t* status, int p, int32_t code)
   if (status) atomicCAS(status + p, 0, code);
 }
 
-// Warp 0: factor the 8 x 8 diagonal block J in place (lane 0, registers) and store
-// its inverse (lanes 0-7, one column each). Returns false on a bad pivot.
+// Warp 0: factor the 8 x 8 diagonal block J in place and store its inverse. Lanes
+// 0-7 each factor the block in registers (the same arithmetic on every lane, loads
+// broadcast), then lane c forms column c of L_JJ^-1 from its own registers. Returns
+// false on a bad pivot.
 __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lane) {
   const int r0 = 8 * J;
   bool bad = false;
-  if (lane == 0) {
+  if (lane < 8) {
     float a[8][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) a[i][j] = S[rowoff(r0 + i) + r0 + j];
+    for (int i = 0; i < 8; ++i) {
+      const float4* rp = reinterpret_cast<const float4*>(S + rowoff(r0 + i) + r0);
+      const float4 u0 = rp[0], u1 = rp[1];
+      a[i][0] = u0.x; a[i][1] = u0.y; a[i][2] = u0.z; a[i][3] = u0.w;
+      a[i][4] = u1.x; a[i][5] = u1.y; a[i][6] = u1.z; a[i][7] = u1.w;
+    }
     float rinv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -75,30 +80,27 @@ __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lan
 #pragma unroll
         for (int m = j + 1; m <= i; ++m) a[i][m] = fmaf(-a[i][j], a[m][j], a[i][m]);
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) S[rowoff(r0 + i) + r0 + j] = a[i][j];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) linv[J * 64 + j * 9] = rinv[j];   // diagonal of L_JJ^-1
-  }
-  bad = __shfl_sync(0xffffffffu, bad ? 1 : 0, 0) != 0;
-  __syncwarp();
-  if (lane < 8) {
     // column `lane` of L_JJ^-1: forward substitution on the unit vector
     float x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float* row = S + rowoff(r0 + i) + r0;
       float t = (i == lane) ? 1.f : 0.f;
 #pragma unroll
-      for (int m = 0; m < i; ++m) t = fmaf(-row[m], x[m], t);
-      x[i] = (i >= lane) ? t * linv[J * 64 + i * 9] : 0.f;
+      for (int m = 0; m < i; ++m) t = fmaf(-a[i][m], x[m], t);
+      x[i] = (i >= lane) ? t * rinv[i] : 0.f;
     }
-    __syncwarp(0xffu);   // lanes 0-7: every diagonal entry is read before any column is stored
 #pragma unroll
     for (int i = 0; i < 8; ++i) linv[J * 64 + i * 8 + lane] = x[i];
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float4* rp = reinterpret_cast<float4*>(S + rowoff(r0 + i) + r0);
+        rp[0] = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
+        rp[1] = make_float4(a[i][4], a[i][5], a[i][6], a[i][7]);
+      }
+    }
   }
+  bad = __shfl_sync(0xffffffffu, bad ? 1 : 0, 0) != 0;
   __syncwarp();
   return !bad;
 }
@@ -265,7 +267,8 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
   float* v = pan + 8 * kp;         // working vector
   float* xs = v + kp;              // solution
   float* rh = xs + kp;             // right-hand side
-  float* Gs = rh + kp;             // copy of G for the refinement residual (launches with gs_ok)
+  float* dg = rh + kp;             // lambda D_i (the diagonal shift of this row system)
+  float* Gs = dg + kp;             // copy of G for the refinement residual (launches with gs_ok)
   const float* G = ws + pd.g_off;
   const int ldg = gram_ld(k);
   const float2* Ghl = pd.g64_off >= 0 ? reinterpret_cast<const float2*>(ws) + pd.g64_off : nullptr;
@@ -287,7 +290,10 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
     // a projection wait that timed out leaves its error in the workspace's first word
     if (i == 0 && reinterpret_cast<const int*>(ws)[0] != 0) set_status(status, p, FMAP_ERR_TIMEOUT);
   }
-  for (int a = tid; a < kp; a += NT) rh[a] = a < k ? rhs[a] : 0.f;
+  for (int a = tid; a < kp; a += NT) {
+    rh[a] = a < k ? rhs[a] : 0.f;
+    dg[a] = a < k ? lam * mask_entry(pd, evx, evy, i, a) : 0.f;
+  }
 
   if (mode == kSolveAdjoint && fac != nullptr) {
     if (use_gs) {
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
       while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}
       return;
     }
-    for (int a = tid; a < k; a += NT) S[rowoff(a) + a] += lam * mask_entry(pd, evx, evy, i, a);
+    for (int a = tid; a < k; a += NT) S[rowoff(a) + a] += dg[a];
     for (int a = tid; a < kp; a += NT) v[a] = rh[a];   // right-hand side, reduced during the factorisation
     __syncthreads();
     if (warp == 0 && !diag_block(S, linv, 0, lane) && lane == 0) s_bad = 1;
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
         for (int o = 16; o > 0; o >>= 1) sum[u] += __shfl_xor_sync(0xffffffffu, sum[u], o);
         const int a = a0 + u * NW;
         if (lane == 0 && a < kp)
-          v[a] = a < k ? rh[a] - fmaf(lam * mask_entry(pd, evx, evy, i, a), xs[a], sum[u]) : 0.f;
+          v[a] = a < k ? rh[a] - fmaf(dg[a], xs[a], sum[u]) : 0.f;
       }
     }
     __syncthreads();
@@ -522,7 +528,7 @@ constexpr int kGsMaxK = 128;
 size_t chol_smem_bytes(int kmax) {
   const int Q = (kmax + 7) / 8, kp = 8 * Q;
   const int64_t gs = kmax <= kGsMaxK ? (int64_t)kmax * gram_ld(kmax) : 0;
-  return (size_t)(factor_floats(Q) + 8 * kp + 3 * kp + gs) * sizeof(float);
+  return (size_t)(factor_floats(Q) + 8 * kp + 4 * kp + gs) * sizeof(float);
 }
 
 template <int NT>
