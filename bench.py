@@ -510,6 +510,86 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- spectral-resolution sweep
+# Fig. 1 of the paper: runtime of the functional-map solve against the number of
+# eigenfunctions k for one shape pair. The paper's numbers for its batched PyTorch solver
+# (another GPU; context, not a target), in ms.
+PAPER_FIG1_MS = {20: 1.98, 30: 1.11, 40: 1.98, 50: 1.82, 60: 1.90, 70: 2.79, 80: 2.65, 90: 2.37, 100: 2.59,
+                 110: 2.80, 120: 2.96, 130: 3.89, 140: 3.85, 150: 4.33, 160: 4.45, 170: 5.23, 180: 5.57,
+                 190: 6.03, 200: 7.05, 210: 7.86, 220: 8.39, 230: 9.28, 240: 9.54, 250: 10.94, 260: 12.29,
+                 270: 13.47, 280: 14.66, 290: 16.53, 300: 17.46}
+
+
+def run_ksweep(args):
+    """One pair per k (n = 5000 vertices per shape, d = 256 BF16 features, mask from the
+    eigenvalues): the solve alone (Gram + row solves from resident A, B), the whole
+    forward (projection + solve) and forward + loss + backward, each timed with CUDA
+    events over `steps` launches after `warmup`; beside them the same solve written with
+    plain PyTorch FP32 ops (G + lambda diag_embed(D), torch.linalg.solve) on this GPU."""
+    import numpy as np
+    import torch
+
+    from paper_2604_10377_gb300 import api, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+
+    def time_ms(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    rows = []
+    for k in sorted(PAPER_FIG1_MS):
+        wl = synth.make_small(1000 + k, 1, (5000, 5000), [k], 256, feat_dtype="bf16", lam_range=(1e-3, 1e-3))
+        b = api.batch_from_workload(wl, device=dev, with_grad=True)
+        gt = api.flat_c(b, [p.c_gt for p in wl.pairs])
+        loss = torch.empty(1, device=dev)
+        dc = torch.empty_like(b.C)
+        a = b.project()
+
+        def fwd_bwd():
+            aa = b.project()
+            cc = b.solve(aa)
+            b.loss_orth(cc, gt, loss=loss, d_c=dc)
+            b.solve_backward(dc, aa, cc)
+
+        t_solve = time_ms(lambda: b.solve(a))
+        t_fwd = time_ms(lambda: b.solve(b.project()))
+        t_fb = time_ms(fwd_bwd)
+        ax, ay = b.a_view(a, 0).clone(), b.a_view(a, 1).clone()
+        lay = b.layout
+        ex = b.evals[lay.evals_off[0]:lay.evals_off[0] + k]
+        ey = b.evals[lay.evals_off[1]:lay.evals_off[1] + k]
+        lam = float(np.float32(wl.pairs[0].lam))
+
+        def torch_solve():
+            g = ax @ ax.t()
+            r = ay @ ax.t()
+            sysm = g[None] + lam * torch.diag_embed((ey[:, None] - ex[None, :]) ** 2)
+            return torch.linalg.solve(sysm, r.unsqueeze(-1)).squeeze(-1)
+
+        t_torch = time_ms(torch_solve)
+        c_ref = torch_solve()
+        err = float((b.c_view(b.solve(a), 0) - c_ref).norm() / c_ref.norm())
+        rows.append({"k": k, "solve_ms": t_solve, "fwd_ms": t_fwd, "fwd_bwd_ms": t_fb, "torch_solve_ms": t_torch,
+                     "rel_diff_vs_torch_fp32": err, "paper_fig1_ms": PAPER_FIG1_MS[k]})
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "spectral resolution k (Fig. 1), one pair, n = 5000, d = 256 BF16",
+                      "steps": args.steps, "warmup": args.warmup, "rows": rows,
+                      "paper_fig1_ms": "the paper's batched PyTorch solver on its own GPU (context only)"}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,16 +598,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=4, choices=sorted(WORKLOADS))
     ap.add_argument("--ir-steps", type=int, default=1)
-    ap.add_argument("--store-factors-max-k", type=int, default=256)
+    ap.add_argument("--store-factors-max-k", type=int, default=304)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-torch-compare", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of one CUDA graph per step")
+    ap.add_argument("--k-sweep", action="store_true", help="spectral-resolution sweep (Fig. 1) instead of the step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.k_sweep:
+        run_ksweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

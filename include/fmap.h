@@ -46,7 +46,7 @@ extern "C" {
 enum fmap_status {
     FMAP_OK = 0,
     FMAP_ERR_INVALID_ARG = 1,   /* null pointer, bad index, size mismatch */
-    FMAP_ERR_UNSUPPORTED = 2,   /* k > 256, d % 16 != 0, misaligned ld, ... */
+    FMAP_ERR_UNSUPPORTED = 2,   /* k > 304, d % 16 != 0, misaligned ld, ... */
     FMAP_ERR_CUDA = 3,          /* a CUDA runtime call failed (see fmap_last_cuda_error) */
     FMAP_ERR_NOT_SPD = 4,       /* per pair: a row system had a non-positive pivot */
     FMAP_ERR_NONFINITE = 5,     /* per pair: NaN/Inf in the result */
@@ -66,14 +66,14 @@ typedef struct fmap_options {
     int32_t hi_gram_min_k;      /* pairs with k >= this accumulate A A^T in FP64 (default 200) */
     int32_t store_factors_max_k;/* fmap_solve saves Cholesky factors for pairs with k <= this when a
                                    `saved` buffer is given; larger pairs are refactored in the
-                                   backward pass (default 256: store everything) */
+                                   backward pass (default 304: store everything) */
     int32_t adjoint_ir_steps;   /* refinement steps of the adjoint row solves (0..3, default 0: the
                                    FP32 factor solve alone is far inside the gradient tolerance) */
 } fmap_options;
 
 typedef struct fmap_shape_desc {
     int64_t n;             /* vertices, >= 1 */
-    int32_t k;             /* basis size, 1..256 */
+    int32_t k;             /* basis size, 1..304 */
     int32_t d;             /* feature dimension, multiple of 16, <= 4096 */
     const float* phi;      /* device, n x ld_phi FP32, columns 0..k-1 used (M-orthonormal basis) */
     int64_t ld_phi;        /* >= k, multiple of 4 (16-byte rows) */
@@ -119,7 +119,7 @@ FMAP_API const char* fmap_error_string(int32_t code);
 /* Text of the last CUDA error seen by this thread's calls (static thread-local storage). */
 FMAP_API const char* fmap_last_cuda_error(void);
 
-/* Fill *opt with the defaults: FP32, ir_steps 1, hi_gram_min_k 200, store_factors_max_k 256,
+/* Fill *opt with the defaults: FP32, ir_steps 1, hi_gram_min_k 200, store_factors_max_k 304,
  * adjoint_ir_steps 0. */
 FMAP_API int32_t fmap_default_options(fmap_options* opt);
 

@@ -92,7 +92,7 @@ class FmapBatch:
 
     def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
                  with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
-                 store_factors_max_k: int = 256, adjoint_ir_steps: int = 0):
+                 store_factors_max_k: int = 304, adjoint_ir_steps: int = 0):
         self.layout = layout
         self.device = torch.device(device)
         self.precision = precision

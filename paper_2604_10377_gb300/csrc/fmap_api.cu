@@ -178,22 +178,30 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     // 128, 256); every class is one launch with its own pipeline depth, and within a
     // class a stream-K split of the vertex ranges into kTcCtas ranges of equal cost
     // (64-vertex granularity)
-    struct Unit { int s, f0, fg, npad, dspan; double cpv; };
+    // A spectral size above 256 (the MMA's largest N) is split into two basis ranges
+    // (units n0 = 0 and n0 = 160), each reading its own Phi columns and all of F.
+    struct Unit { int s, f0, fg, npad, n0, nk, dspan; double cpv; };
     std::vector<Unit> classes[4];
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
-      const int npad = (sd.k + 15) / 16 * 16;
-      const int mt = (sd.d + 127) / 128;
-      const int fg_cap = std::max(1, std::min(4, 512 / npad));
-      const int groups = (mt + fg_cap - 1) / fg_cap;
-      const int fg_s = (mt + groups - 1) / groups;
-      const int cls = npad <= 32 ? 0 : (npad <= 64 ? 1 : (npad <= 128 ? 2 : 3));
-      for (int g = 0; g < groups; ++g) {
-        Unit u;
-        u.s = s; u.f0 = g * fg_s * 128; u.fg = std::min(fg_s, mt - g * fg_s); u.npad = npad;
-        u.dspan = std::min(u.fg * 128, sd.d - u.f0);
-        u.cpv = 4.0 * sd.k + 4.0 + 2.0 * u.dspan;   // HBM bytes per vertex
-        classes[cls].push_back(u);
+      const int nsplit = sd.k > 256 ? 2 : 1;
+      for (int h = 0; h < nsplit; ++h) {
+        const int n0 = h * 160;
+        const int nk = nsplit == 1 ? sd.k : (h == 0 ? 160 : sd.k - 160);
+        const int npad = (nk + 15) / 16 * 16;
+        const int mt = (sd.d + 127) / 128;
+        const int fg_cap = std::max(1, std::min(4, 512 / npad));
+        const int groups = (mt + fg_cap - 1) / fg_cap;
+        const int fg_s = (mt + groups - 1) / groups;
+        const int cls = npad <= 32 ? 0 : (npad <= 64 ? 1 : (npad <= 128 ? 2 : 3));
+        for (int g = 0; g < groups; ++g) {
+          Unit u;
+          u.s = s; u.f0 = g * fg_s * 128; u.fg = std::min(fg_s, mt - g * fg_s); u.npad = npad;
+          u.n0 = n0; u.nk = nk;
+          u.dspan = std::min(u.fg * 128, sd.d - u.f0);
+          u.cpv = 4.0 * nk + 4.0 + 2.0 * u.dspan;   // HBM bytes per vertex
+          classes[cls].push_back(u);
+        }
       }
     }
     for (int cls = 0; cls < 4; ++cls) {
@@ -220,6 +228,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         const ShapeDev& sd = P.shapes[u.s];
         TcRedGroup rg{};
         rg.shape = u.s; rg.f0 = u.f0; rg.stride = u.fg * 128; rg.dspan = u.dspan;
+        rg.n0 = u.n0; rg.nk = u.nk;
         rg.it_beg = (int32_t)P.tc_items.size();
         int64_t v = 0;
         while (v < sd.n) {
@@ -231,9 +240,10 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
           take = std::min<int64_t>(std::min<int64_t>(take, kTcSegMaxV), sd.n - v);
           TcItem it{};
           it.shape = u.s; it.f0 = u.f0; it.fg = u.fg; it.npad = u.npad;
+          it.n0 = u.n0; it.nk = u.nk;
           it.v0 = v; it.v1 = v + take;
           it.part_off = cur;
-          cur = align_up(cur + (int64_t)sd.k * rg.stride, kAlignFloats);
+          cur = align_up(cur + (int64_t)u.nk * rg.stride, kAlignFloats);
           P.tc_items.push_back(it);
           v += take;
           budget -= u.cpv * (double)take;
@@ -245,7 +255,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         }
         rg.it_end = (int32_t)P.tc_items.size();
         P.tc_groups.push_back(rg);
-        P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)sd.k * rg.dspan);
+        P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)u.nk * rg.dspan);
       }
       for (int c = cta + 1; c <= kTcCtas; ++c) first[c] = (int32_t)P.tc_items.size();
       L.f_stage = std::max<uint32_t>(fmax, 16384u);
@@ -275,7 +285,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     }
   }
   P.loss_part_off = cur;   // per-pair, per-tile partial sums of the training loss
-  cur = align_up(cur + (int64_t)n_pairs * 16, kAlignFloats);
+  cur = align_up(cur + (int64_t)n_pairs * kMaxLossTiles, kAlignFloats);
   const int64_t ws_fwd = cur;
   for (auto& pd : P.pairs) {
     const int64_t kk = (int64_t)pd.k * pd.k, kd = (int64_t)pd.k * pd.d;
@@ -402,11 +412,14 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   }
 
   // ---- row systems, grouped by block size, largest k first
-  const int bounds[3] = {64, 128, 256};
-  for (int gi = 0; gi < 3; ++gi) {
+  // (k <= 64: 64 threads, <= 128: 128, <= 256: 256, <= kMaxK: 320 -- every block has at
+  // least one thread per padded row)
+  const int bounds[4] = {64, 128, 256, kMaxK};
+  const int threads[4] = {64, 128, 256, 320};
+  for (int gi = 0; gi < 4; ++gi) {
     SolveGroup g{};
     g.first = (int32_t)P.systems.size();
-    g.threads = bounds[gi];
+    g.threads = threads[gi];
     std::vector<int> members;
     for (int p = 0; p < n_pairs; ++p) {
       const int k = P.pairs[p].k;
@@ -523,7 +536,7 @@ int32_t fmap_default_options(fmap_options* opt) {
   opt->precision = FMAP_PREC_FP32;
   opt->ir_steps = 1;
   opt->hi_gram_min_k = 200;
-  opt->store_factors_max_k = 256;
+  opt->store_factors_max_k = kMaxK;
   opt->adjoint_ir_steps = 0;
   return FMAP_OK;
 }

@@ -12,7 +12,9 @@
 
 namespace fmap {
 
-constexpr int kMaxK = 256;
+constexpr int kMaxK = 304;
+// per-pair partial sums of the training loss: one per 64 x 64 tile of C
+constexpr int kMaxLossTiles = ((kMaxK + 63) / 64) * ((kMaxK + 63) / 64);
 constexpr int kMaxD = 4096;
 
 // Device copy of a shape descriptor plus the offsets the library assigns to it.
@@ -35,10 +37,15 @@ struct ShapeDev {
 };
 
 // Device copy of a pair descriptor plus workspace offsets.
-// Row stride (floats) of the FP32 Gram matrix G in the workspace: k rounded up to 4,
-// so that every row starts on a 16-byte boundary (bulk copies into shared memory).
-// The region holds k rows plus 8 floats of slack past the last row.
-__host__ __device__ __forceinline__ int gram_ld(int k) { return (k + 3) & ~3; }
+// Row stride (floats) of the FP32 Gram matrix G in the workspace: k rounded up to a
+// multiple of 4 (every row starts on a 16-byte boundary, for bulk copies into shared
+// memory) with an odd number of 16-byte quads (rows read by consecutive threads as
+// float4 then fall on distinct bank groups). The region holds k rows plus 8 floats of
+// slack past the last row.
+__host__ __device__ __forceinline__ int gram_ld(int k) {
+  const int q = (k + 3) >> 2;
+  return 4 * (q | 1);
+}
 __host__ __device__ __forceinline__ int64_t gram_floats(int k) { return (int64_t)k * gram_ld(k) + 8; }
 
 struct PairDev {
@@ -92,13 +99,16 @@ __host__ __device__ inline int64_t tri(int64_t k) { return k * (k + 1) / 2; }
 // (fg M-tiles of 128 features starting at feature f0) of one shape.
 struct TcItem {
   int32_t shape, f0, fg, npad;
+  int32_t n0, nk;      // basis rows n0 .. n0+nk of A (npad = nk rounded up to 16)
   int64_t v0, v1;
-  int64_t part_off;    // float offset (workspace) of the segment's partial, k x (fg*128)
+  int64_t part_off;    // float offset (workspace) of the segment's partial, nk x (fg*128)
 };
 
-// Items [it_beg, it_end) hold the partials of features f0 .. f0+dspan of one shape.
+// Items [it_beg, it_end) hold the partials of basis rows n0 .. n0+nk and features
+// f0 .. f0+dspan of one shape.
 struct TcRedGroup {
   int32_t shape, f0, dspan, stride;
+  int32_t n0, nk;
   int32_t it_beg, it_end;
 };
 

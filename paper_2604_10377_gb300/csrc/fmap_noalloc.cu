@@ -22,6 +22,7 @@ namespace fmap {
 namespace {
 
 constexpr size_t kScratchBytes = size_t(2) << 20;   // 2 MiB per device
+constexpr int kNoallocMaxK = 256;                     // the layout of one pair fits the scratch
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -129,7 +130,7 @@ extern "C" FMAP_API int32_t fmap_solve_pair_noalloc(const float* a_x, const floa
   if (!a_x || !a_y || !c_out) return FMAP_ERR_INVALID_ARG;
   if (k < 1 || d < 1 || !(lambda >= 0.f) || ir_steps < 0 || ir_steps > 3) return FMAP_ERR_INVALID_ARG;
   if (!mask && (!evals_x || !evals_y)) return FMAP_ERR_INVALID_ARG;
-  if (k > kMaxK) return FMAP_ERR_UNSUPPORTED;
+  if (k > kNoallocMaxK) return FMAP_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(a_x) | reinterpret_cast<uintptr_t>(a_y)) % 4 != 0) return FMAP_ERR_UNSUPPORTED;
   const bool hi = k >= 200;
   const Layout lay = layout_for(k, hi);

@@ -15,7 +15,7 @@
 //            right-hand side entry;
 //   (b)      warp 0 factors the diagonal block J+1 in registers and stores its
 //            inverse, while the other warps update the rest of the trailing matrix
-//            in 8x8, 8x4 or 4x4 register tiles (whichever balances best),
+//            in 8x4 or 4x4 register tiles (whichever balances best),
 //            S_AB -= L_AJ L_BJ^T.
 // (a) and (b) touch disjoint blocks, so a panel costs two block barriers. The back
 // substitution and the refinement's triangular solves use every warp with the inverse
@@ -243,7 +243,7 @@ __device__ __forceinline__ void block_bwd(const float* S, const float* linv, flo
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
+__global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 128 ? 4 : 8))))
     chol_solve_kernel(BatchDev b, const int2* systems, int first, int count, int mode, const float* rhs_flat,
                       float* out_flat, float* saved, int32_t* status, float* ws, int gs_ok) {
   constexpr int NW = NT / 32;
@@ -407,19 +407,14 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
       if (warp == 0) {
         if (!diag_block(S, linv, J + 1, lane) && lane == 0) s_bad = 1;
       } else {
-        // trailing blocks (A, B), J+2 <= B <= A < Q, as 8x8, 8x4 or 4x4 register tiles:
-        // the size whose rounds over the NT - 32 threads cost the fewest instructions
+        // trailing blocks (A, B), J+2 <= B <= A < Q, as 8x4 or 4x4 register tiles: the
+        // size whose rounds over the NT - 32 threads cost the fewest instructions (an 8x8
+        // tile would save ~1% of the instructions and spill registers at two blocks/SM)
         const int m = Q - J - 2;
         const int nb = NT - 32, t0 = tid - 32, base = 8 * (J + 2);
-        const int T88 = m * (m + 1) / 2, T84 = 2 * T88, T44 = m * (2 * m + 1);
-        const int c88 = (T88 + nb - 1) / nb * 576, c84 = (T84 + nb - 1) / nb * 296, c44 = (T44 + nb - 1) / nb * 152;
-        if (c88 <= c84 && c88 <= c44) {
-          for (int t = t0; t < T88; t += nb) {
-            int ai, bi;
-            tri_decode(t, ai, bi);
-            trail_tile<8, 8>(S, pan, kp, base + 8 * ai, base + 8 * bi);
-          }
-        } else if (c84 <= c44) {
+        const int T84 = m * (m + 1), T44 = m * (2 * m + 1);
+        const int c84 = (T84 + nb - 1) / nb * 296, c44 = (T44 + nb - 1) / nb * 152;
+        if (c84 <= c44) {
           for (int t = t0; t < T84; t += nb) {
             int ai, bi;
             tri_decode(t >> 1, ai, bi);
@@ -455,46 +450,75 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : (NT >= 128 ? 3 : 4)))
   for (int a = tid; a < kp; a += NT) xs[a] = v[a];
   __syncthreads();
 
-  // iterative refinement: x += S^{-1} (rhs - S x); four rows of G in flight per warp
+  // iterative refinement: x += S^{-1} (rhs - S x). With G in shared memory every thread
+  // forms one row's residual (float4 reads, four partial sums); otherwise each warp
+  // reduces rows of G read from global memory, four rows in flight.
   const float* Gres = use_gs ? Gs : G;
   for (int it = 0; it < n_ir; ++it) {
+    if (use_gs) {
+      for (int a = tid; a < kp; a += NT) {
+        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+        if (a < k) {
+          const float4* gr = reinterpret_cast<const float4*>(Gs + (int64_t)a * ldg);
+          const float4* xq = reinterpret_cast<const float4*>(xs);
+          const int nq = k >> 2;   // full quads; the columns past k hold no G entries
+          for (int q = 0; q < nq; ++q) {
+            const float4 g4 = gr[q], x4 = xq[q];
+            s4[0] = fmaf(g4.x, x4.x, s4[0]);
+            s4[1] = fmaf(g4.y, x4.y, s4[1]);
+            s4[2] = fmaf(g4.z, x4.z, s4[2]);
+            s4[3] = fmaf(g4.w, x4.w, s4[3]);
+          }
+          for (int c = 4 * nq; c < k; ++c) s4[c & 3] = fmaf(Gs[(int64_t)a * ldg + c], xs[c], s4[c & 3]);
+        }
+        v[a] = a < k ? rh[a] - fmaf(dg[a], xs[a], (s4[0] + s4[1]) + (s4[2] + s4[3])) : 0.f;
+      }
+      __syncthreads();
+      block_fwd<NT>(S, linv, v, Q, tid, lane, warp);
+      block_bwd<NT>(S, linv, v, Q, tid, lane, warp);
+      for (int a = tid; a < kp; a += NT) xs[a] += v[a];
+      __syncthreads();
+      continue;
+    }
     for (int a0 = warp; a0 < kp; a0 += 4 * NW) {
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
-      if (Ghl) {
-        float2 g[4][kMaxK / 32];
+      for (int c0 = 0; c0 < k; c0 += 128) {   // 128 columns (four per lane) per round
+        if (Ghl) {
+          float2 g[4][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int a = a0 + u * NW;
+          for (int u = 0; u < 4; ++u) {
+            const int a = a0 + u * NW;
 #pragma unroll
-          for (int q = 0; q < kMaxK / 32; ++q) {
-            const int c = lane + 32 * q;
-            g[u][q] = (a < k && c < k) ? Ghl[(int64_t)a * k + c] : make_float2(0.f, 0.f);
+            for (int q = 0; q < 4; ++q) {
+              const int c = c0 + lane + 32 * q;
+              g[u][q] = (a < k && c < k) ? Ghl[(int64_t)a * k + c] : make_float2(0.f, 0.f);
+            }
           }
-        }
 #pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-          const int c = lane + 32 * q;
-          const float xv = c < k ? xs[c] : 0.f;
+          for (int q = 0; q < 4; ++q) {
+            const int c = c0 + lane + 32 * q;
+            const float xv = c < k ? xs[c] : 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q].y, xv, fmaf(g[u][q].x, xv, sum[u]));
-        }
-      } else {
-        float g[4][kMaxK / 32];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int a = a0 + u * NW;
-#pragma unroll
-          for (int q = 0; q < kMaxK / 32; ++q) {
-            const int c = lane + 32 * q;
-            g[u][q] = (a < k && c < k) ? Gres[(int64_t)a * ldg + c] : 0.f;
+            for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q].y, xv, fmaf(g[u][q].x, xv, sum[u]));
           }
-        }
+        } else {
+          float g[4][4];
 #pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-          const int c = lane + 32 * q;
-          const float xv = c < k ? xs[c] : 0.f;
+          for (int u = 0; u < 4; ++u) {
+            const int a = a0 + u * NW;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q], xv, sum[u]);
+            for (int q = 0; q < 4; ++q) {
+              const int c = c0 + lane + 32 * q;
+              g[u][q] = (a < k && c < k) ? Gres[(int64_t)a * ldg + c] : 0.f;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = c0 + lane + 32 * q;
+            const float xv = c < k ? xs[c] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q], xv, sum[u]);
+          }
         }
       }
 #pragma unroll
@@ -545,7 +569,8 @@ cudaError_t solve_set_smem_limits() {
   cudaError_t e;
   if ((e = set_limit<64>()) != cudaSuccess) return e;
   if ((e = set_limit<128>()) != cudaSuccess) return e;
-  return set_limit<256>();
+  if ((e = set_limit<256>()) != cudaSuccess) return e;
+  return set_limit<320>();
 }
 
 cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode, const float* rhs_flat,
@@ -562,8 +587,12 @@ cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* sys
       chol_solve_kernel<128><<<g.count, 128, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat,
                                                          saved, status, ws, gs);
       break;
-    default:
+    case 256:
       chol_solve_kernel<256><<<g.count, 256, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat,
+                                                         saved, status, ws, gs);
+      break;
+    default:
+      chol_solve_kernel<320><<<g.count, 320, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat,
                                                          saved, status, ws, gs);
       break;
   }

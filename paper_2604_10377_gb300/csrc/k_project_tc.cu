@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
           for (int m = 0; m < item.fg; ++m)
             for (int h = 0; h < 2; ++h)
               tc::tma_load_2d(dst + (m * 2 + h) * kBoxBytes, fmap, &full_f[stage], item.f0 + m * 128 + h * 64, y);
-          for (int b = 0; b < kb; ++b) tc::tma_load_2d(pdst + b * kPhiBoxBytes, pmap, &full_f[stage], b * 32, y);
+          for (int b = 0; b < kb; ++b)
+            tc::tma_load_2d(pdst + b * kPhiBoxBytes, pmap, &full_f[stage], item.n0 + b * 32, y);
           tc::tma_load_1d(sM + (size_t)stage * kStageV, mmap, &full_f[stage], y);
           if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
         }
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
 #pragma unroll
               for (int t = 0; t < 16; ++t) {
                 const int n = ch * 16 + t;
-                if (n < k) part[(int64_t)n * stride + fl] = v[t];
+                if (n < item.nk) part[(int64_t)n * stride + fl] = v[t];
               }
             }
           }
@@ -267,17 +268,17 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
   if (threadIdx.x == 0 && *abort_flag) atomicExch(P.err, (int)FMAP_ERR_TIMEOUT);
 }
 
-// A_s[n][f0 + f] = sum over the group's items (in order) of partial[n][f].
+// A_s[n0 + n][f0 + f] = sum over the group's items (in order) of partial[n][f].
 __global__ void project_tc_reduce_kernel(const ShapeDev* shapes, const TcItem* items, const TcRedGroup* groups,
                                          float* a_out, const float* ws) {
   const TcRedGroup g = groups[blockIdx.y];
   const ShapeDev s = shapes[g.shape];
-  const int64_t total = (int64_t)s.k * g.dspan;
+  const int64_t total = (int64_t)g.nk * g.dspan;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = e / g.dspan, f = e % g.dspan;
     float acc = 0.f;
     for (int i = g.it_beg; i < g.it_end; ++i) acc += ws[items[i].part_off + n * g.stride + f];
-    a_out[s.a_off + n * s.d + g.f0 + f] = acc;
+    a_out[s.a_off + (g.n0 + n) * s.d + g.f0 + f] = acc;
   }
 }
 

@@ -191,7 +191,6 @@ __global__ void gather_da_kernel(BatchDev b, float* d_a, const float* ws) {
 // as two tiled passes over (64 x 64 output tile, pair):
 //   pass 1: E = C C^T - I (into the workspace) and per-tile partial sums of the loss;
 //   pass 2: dC = 4 E C + 2 (C - C_gt); tile 0 of each pair adds the partials in order.
-constexpr int kMaxLossTiles = 16;   // (256 / 64)^2
 
 __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_flat, const float* gt_flat,
                                                       float* ws, float* partial) {

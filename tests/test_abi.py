@@ -89,13 +89,31 @@ def test_plan_sizes(lib):
     assert sz.saved_bytes >= 4 * (2 * 30 * 30 * 31 // 2 + 200 * 200 * 201 // 2)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_plan_accepts_k_up_to_304(lib, precision):
+    """Spectral sizes above 256 (split into two basis ranges by the tensor-core
+    projection, 320-thread solve blocks) up to the 304 limit."""
+    from paper_2604_10377_gb300 import _lib
+    opt = _lib.default_options()
+    opt.precision = precision
+    specs = [dict(n=4000, k=k, d=256) for k in (257, 257, 300, 300, 304, 304)]
+    rc, sz = _plan(lib, specs, [(0, 1, 1e-3), (2, 3, 1e-3), (4, 5, 1e-3)], opt)
+    assert rc == 0
+    assert sz.a_floats == 2 * 256 * (257 + 300 + 304)
+    assert sz.c_floats == 257 ** 2 + 300 ** 2 + 304 ** 2
+    # every system's factor is stored by default: 32Q(Q+2) + 64Q floats per system
+    # (each pair's block 256-byte aligned)
+    fac = sum(k * 4 * (32 * q * (q + 2) + 64 * q) for k, q in ((257, 33), (300, 38), (304, 38)))
+    assert fac <= sz.saved_bytes < fac + 3 * 256
+
+
 def test_plan_sizes_empty(lib):
     rc, sz = _plan(lib, [dict(n=10, k=4, d=16)], [])
     assert rc == 0 and sz.c_floats == 0 and sz.n_pairs == 0
 
 
 @pytest.mark.parametrize("bad,code", [
-    (dict(k=0), 1), (dict(k=257), 2), (dict(d=24), 2), (dict(n=0), 1),
+    (dict(k=0), 1), (dict(k=305), 2), (dict(d=24), 2), (dict(n=0), 1),
     (dict(ld_phi=30), 1), (dict(ld_phi=34), 2), (dict(ld_feat=132), 2),
     (dict(phi=0x10004), 2), (dict(feat=0x40008), 2),
 ])
@@ -124,7 +142,7 @@ def test_plan_rejects_k_mismatch_and_missing_evals(lib):
 def test_options_validation(lib):
     from paper_2604_10377_gb300 import _lib
     o = _lib.default_options()
-    assert (o.precision, o.ir_steps, o.hi_gram_min_k, o.store_factors_max_k, o.adjoint_ir_steps) == (0, 1, 200, 256, 0)
+    assert (o.precision, o.ir_steps, o.hi_gram_min_k, o.store_factors_max_k, o.adjoint_ir_steps) == (0, 1, 200, 304, 0)
     ctx = ctypes.c_void_p()
     assert lib.fmap_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == 0
     assert lib.fmap_destroy(ctx) == 0

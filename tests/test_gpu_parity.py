@@ -209,6 +209,24 @@ def test_backward_bf16_feature_groups(d):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
 
 
+@pytest.mark.parametrize("feat_dtype,use_saved", [("fp32", True), ("bf16", True), ("bf16", False)])
+def test_large_spectral_sizes(feat_dtype, use_saved):
+    """k above 256 up to the 304 limit: the tensor-core projection splits the basis into
+    two ranges, the solve runs 320-thread blocks with one system per SM; forward and
+    backward (saved or recomputed factors) against the oracle."""
+    wl = synth.make_small(12, 3, (400, 1500), [257, 300, 304], 320, feat_dtype=feat_dtype)
+    out = _gpu_backward(wl, use_saved=use_saved)
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    tol, gtol = TOL[feat_dtype], GTOL[feat_dtype]
+    assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert rel_fro(out["C"][p], fwd["C"][p]) <= tol
+        assert abs(out["loss"][p] - losses[p]) <= tol * max(1.0, abs(losses[p]))
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= gtol
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= gtol
+
+
 def test_gradient_against_finite_differences():
     """GPU dL/dF (FP32 mode) against central differences (h = 1e-3) of the FP64
     pipeline along 8 seeded random directions per shape."""
