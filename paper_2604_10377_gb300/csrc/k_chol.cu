@@ -4,8 +4,8 @@
 // S_i is padded to kp = k rounded up to 8 (identity in the padding) and kept in
 // shared memory as packed lower rows: row a holds 8 (a/8 + 1) + 4 floats, so a
 // row's 8-column tile segment is two aligned float4 and consecutive rows fall on
-// different banks. Each row's segment is bulk-copied (cp.async.bulk) straight from
-// G, then lambda D_i is added to the diagonal. The factorisation is a blocked
+// different banks. Each row's segment is copied from G by 16-byte asynchronous copies
+// (cp.async) spread over the block, then lambda D_i is added to the diagonal. The factorisation is a blocked
 // right-looking Cholesky in FP32 with 8-column panels and one panel of lookahead:
 //   TRSM     every thread solves one row of panel J below its diagonal block,
 //            x = s L_JJ^-T, as a product with the stored inverse block; one warp
@@ -18,8 +18,8 @@
 //            in 8x4 or 4x4 register tiles (whichever balances best),
 //            S_AB -= L_AJ L_BJ^T.
 // (a) and (b) touch disjoint blocks, so a panel costs two block barriers. The back
-// substitution and the refinement's triangular solves use every warp with the inverse
-// diagonal blocks (one barrier per block); `ir_steps` steps of iterative refinement
+// substitution and the refinement's triangular solves use every warp with the inverses
+// of 16-row diagonal blocks (one barrier per 16 rows); `ir_steps` steps of iterative refinement
 // take the residual rhs - S x in FP32, for hi_gram pairs with G as the two FP32
 // halves (hi + lo) of its double-float accumulation.
 #include <math.h>
@@ -105,6 +105,15 @@ __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lan
   return !bad;
 }
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned), and the
+// wait for every such copy issued by this thread.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Row index of entry t of a lower triangle enumerated row by row (t = a(a+1)/2 + b).
 __device__ __forceinline__ void tri_decode(int t, int& a, int& b) {
   int ai = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -157,86 +166,137 @@ __device__ __forceinline__ void trail_tile(float* S, const float* pan, int kp, i
   }
 }
 
-// v <- L^{-1} v with every thread of the block (NT >= kp): thread t updates row
-// r0 + 8 + t against y_J; warp 0 owns the next block's rows and applies its inverse
-// diagonal block right after updating them. One barrier per 8-row block.
-template <int NT>
-__device__ __forceinline__ void block_fwd(const float* S, const float* linv, float* v, int Q, int tid, int lane,
-                                          int warp) {
-  const int kp = 8 * Q;
-  if (warp == 0) {
-    float y = 0.f;
-    if (lane < 8)
+// The triangular solves work on 16-row blocks p (rows 16p .. 16p+15; the last block has
+// 8 rows when Q is odd). The inverse of a 16-row diagonal block is formed from the two
+// 8x8 inverses A^-1, B^-1 and the block below the diagonal L21:
+//   [A 0; L21 B]^-1 = [A^-1 0; M B^-1] with M = -B^-1 L21 A^-1,
+// and M (64 floats per 16-row block) is computed once per factor, by every thread.
+__device__ __forceinline__ void pair_blocks_prepare(const float* S, const float* linv, float* mo, int Q, int tid,
+                                                    int nt) {
+  const int np = Q >> 1;   // 16-row blocks with two 8-row halves
+  for (int e = tid; e < np * 64; e += nt) {
+    const int p = e >> 6, i = (e >> 3) & 7, j = e & 7;
+    const float* Ai = linv + (2 * p) * 64;        // A^-1, row-major
+    const float* Bi = linv + (2 * p + 1) * 64;    // B^-1
+    float acc = 0.f;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) y = fmaf(linv[lane * 8 + j], v[j], y);
-    __syncwarp();
-    if (lane < 8) v[lane] = y;
+    for (int m = 0; m < 8; ++m) {
+      // (L21 A^-1)[m][j]
+      const float* l21 = S + rowoff(16 * p + 8 + m) + 16 * p;
+      float t = 0.f;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) t = fmaf(l21[l], Ai[l * 8 + j], t);
+      acc = fmaf(Bi[i * 8 + m], t, acc);
+    }
+    mo[e] = -acc;
   }
+}
+
+// Lanes 0-15 of one warp: v[16p ..] <- (16-row diagonal block p)^-1 v[16p ..].
+__device__ __forceinline__ void apply_inv_fwd(const float* linv, const float* mo, float* v, int p, int Q, int lane) {
+  const int r0 = 16 * p;
+  const bool two = 2 * p + 1 < Q;
+  float y = 0.f;
+  if (lane < 8) {
+    const float* Ai = linv + (2 * p) * 64 + lane * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) y = fmaf(Ai[j], v[r0 + j], y);
+  } else if (lane < 16 && two) {
+    const int i = lane - 8;
+    const float* Mi = mo + p * 64 + i * 8;
+    const float* Bi = linv + (2 * p + 1) * 64 + i * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) y = fmaf(Mi[j], v[r0 + j], fmaf(Bi[j], v[r0 + 8 + j], y));
+  }
+  __syncwarp();
+  if (lane < (two ? 16 : 8)) v[r0 + lane] = y;
+  __syncwarp();
+}
+
+// Lanes l0 .. l0+15 of one warp: v[16p ..] <- (16-row diagonal block p)^-T v[16p ..].
+__device__ __forceinline__ void apply_inv_bwd(const float* linv, const float* mo, float* v, int p, int Q, int i) {
+  const int r0 = 16 * p;
+  const bool two = 2 * p + 1 < Q;
+  float x = 0.f;
+  if (i >= 0 && i < 8) {
+    const float* Ai = linv + (2 * p) * 64;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x = fmaf(Ai[j * 8 + i], v[r0 + j], x);
+    if (two) {
+      const float* Mp = mo + p * 64;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x = fmaf(Mp[j * 8 + i], v[r0 + 8 + j], x);
+    }
+  } else if (i >= 8 && i < 16 && two) {
+    const float* Bi = linv + (2 * p + 1) * 64;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x = fmaf(Bi[j * 8 + (i - 8)], v[r0 + 8 + j], x);
+  }
+  __syncwarp();
+  if (i >= 0 && i < (two ? 16 : 8)) v[r0 + i] = x;
+  __syncwarp();
+}
+
+// v <- L^{-1} v with every thread of the block (NT >= kp): thread t updates row
+// r0 + 16 + t against the finished block; warp 0 owns the next block's rows and applies
+// its inverse right after updating them. One block barrier per 16-row block.
+template <int NT>
+__device__ __forceinline__ void block_fwd(const float* S, const float* linv, const float* mo, float* v, int Q,
+                                          int tid, int lane, int warp) {
+  const int kp = 8 * Q, nb = (Q + 1) >> 1;
+  if (warp == 0) apply_inv_fwd(linv, mo, v, 0, Q, lane);
   __syncthreads();
-  for (int J = 0; J < Q; ++J) {
-    const int r0 = 8 * J;
-    const int a = r0 + 8 + tid;
+  for (int p = 0; p + 1 < nb; ++p) {
+    const int r0 = 16 * p;
+    const int a = r0 + 16 + tid;
     if (a < kp) {
       const float4* ra = reinterpret_cast<const float4*>(S + rowoff(a) + r0);
-      const float4 l0 = ra[0], l1 = ra[1];
-      const float4 y0 = *reinterpret_cast<const float4*>(v + r0);
-      const float4 y1 = *reinterpret_cast<const float4*>(v + r0 + 4);
+      const float4* ya = reinterpret_cast<const float4*>(v + r0);
       float t = v[a];
-      t = fmaf(-l0.x, y0.x, t); t = fmaf(-l0.y, y0.y, t); t = fmaf(-l0.z, y0.z, t); t = fmaf(-l0.w, y0.w, t);
-      t = fmaf(-l1.x, y1.x, t); t = fmaf(-l1.y, y1.y, t); t = fmaf(-l1.z, y1.z, t); t = fmaf(-l1.w, y1.w, t);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float4 l = ra[h], y = ya[h];
+        t = fmaf(-l.x, y.x, t); t = fmaf(-l.y, y.y, t); t = fmaf(-l.z, y.z, t); t = fmaf(-l.w, y.w, t);
+      }
       v[a] = t;
     }
-    if (J + 1 < Q && warp == 0) {
+    if (warp == 0) {
       __syncwarp();
-      float y = 0.f;
-      if (lane < 8) {
-        const float* li = linv + (J + 1) * 64 + lane * 8;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) y = fmaf(li[j], v[r0 + 8 + j], y);
-      }
-      __syncwarp();
-      if (lane < 8) v[r0 + 8 + lane] = y;
+      apply_inv_fwd(linv, mo, v, p + 1, Q, lane);
     }
     __syncthreads();
   }
 }
 
-// v <- L^{-T} v: thread t updates row t against x_J; the warp owning the previous
-// block's rows applies that block's transposed inverse. One barrier per block.
+// v <- L^{-T} v: thread t updates row t against the finished block; the warp owning the
+// previous block's rows applies that block's transposed inverse. One barrier per block.
 template <int NT>
-__device__ __forceinline__ void block_bwd(const float* S, const float* linv, float* v, int Q, int tid, int lane,
-                                          int warp) {
+__device__ __forceinline__ void block_bwd(const float* S, const float* linv, const float* mo, float* v, int Q,
+                                          int tid, int lane, int warp) {
+  const int kp = 8 * Q, nb = (Q + 1) >> 1;
   {
-    const int r0 = 8 * (Q - 1);
-    if (warp == (r0 >> 5)) {
-      const int i = lane - (r0 & 31);
-      float x = 0.f;
-      if (i >= 0 && i < 8)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) x = fmaf(linv[(Q - 1) * 64 + j * 8 + i], v[r0 + j], x);
-      __syncwarp();
-      if (i >= 0 && i < 8) v[r0 + i] = x;
-    }
+    const int r0 = 16 * (nb - 1);
+    if (warp == (r0 >> 5)) apply_inv_bwd(linv, mo, v, nb - 1, Q, lane - (r0 & 31));
   }
   __syncthreads();
-  for (int J = Q - 1; J >= 1; --J) {
-    const int r0 = 8 * J;
+  for (int p = nb - 1; p >= 1; --p) {
+    const int r0 = 16 * p;
+    const int w = (r0 + 16 <= kp) ? 16 : 8;
     if (tid < r0) {
       float t = v[tid];
+      if (w == 16) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], v[r0 + m], t);
+        for (int m = 0; m < 16; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], v[r0 + m], t);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], v[r0 + m], t);
+      }
       v[tid] = t;
     }
-    const int p0 = r0 - 8;                 // rows of block J - 1, owned by threads p0..p0+7
+    const int p0 = r0 - 16;                 // rows of block p - 1, owned by threads p0..p0+15
     if (warp == (p0 >> 5)) {
       __syncwarp();
-      const int i = lane - (p0 & 31);
-      float x = 0.f;
-      if (i >= 0 && i < 8)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) x = fmaf(linv[(J - 1) * 64 + j * 8 + i], v[p0 + j], x);
-      __syncwarp();
-      if (i >= 0 && i < 8) v[p0 + i] = x;
+      apply_inv_bwd(linv, mo, v, p - 1, Q, lane - (p0 & 31));
     }
     __syncthreads();
   }
@@ -313,30 +373,38 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
     __syncthreads();
   } else {
     // S = G + lambda diag(D_i). Row a's packed segment (columns 0 .. end of its
-    // diagonal block) is bulk-copied from G; the entries above the diagonal inside a
-    // diagonal block are never read. Padding rows are identity rows.
+    // diagonal block) is copied from G in 16-byte asynchronous copies spread over all
+    // threads (8-row block q holds rows of 2q + 2 chunks); the entries above the diagonal
+    // inside a diagonal block are never read. Padding rows are identity rows.
     __syncthreads();   // barrier initialised
-    if (warp == 0) {
-      if (lane == 0) {
-        const int qf = k >> 3, rem = k & 7;
-        tc::mbar_arrive_expect_tx(&s_bar, (uint32_t)(32 * qf * (qf + 1) + 8 * rem * (qf + 1)) * 4u + gs_bytes);
-        if (use_gs) tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
+    if (use_gs && tid == 0) {
+      tc::mbar_arrive_expect_tx(&s_bar, gs_bytes);
+      tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
+    }
+    {
+      const int nch = 8 * Q * (Q + 1);
+      for (int t = tid; t < nch; t += NT) {
+        int q = (int)((sqrtf(1.f + 0.5f * (float)t) - 1.f) * 0.5f);
+        while (8 * (q + 1) * (q + 2) <= t) ++q;
+        while (8 * q * (q + 1) > t) --q;
+        const int rem = t - 8 * q * (q + 1), len = 2 * q + 2;
+        const int a = 8 * q + rem / len, ch = rem - (rem / len) * len;
+        if (a < k) cp_async16(S + rowoff(a) + 4 * ch, G + (int64_t)a * ldg + 4 * ch);
       }
-      __syncwarp();
-      for (int a = lane; a < k; a += 32)
-        tc::bulk_g2s(S + rowoff(a), G + (int64_t)a * ldg, (uint32_t)((a & ~7) + 8) * 4u, &s_bar);
+      cp_async_commit_wait_all();
     }
     for (int a = k + tid; a < kp; a += NT) {
       float* row = S + rowoff(a);
       for (int c = 0; c < (a & ~7) + 8; ++c) row[c] = (c == a) ? 1.f : 0.f;
     }
-    if (!tc::mbar_wait(&s_bar, 0, &s_abort)) {
-      // copies that never completed: report, give them a bounded time to land, leave
+    if (use_gs && !tc::mbar_wait(&s_bar, 0, &s_abort)) {
+      // a copy that never completed: report, give it a bounded time to land, leave
       if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
       const uint64_t t0 = tc::globaltimer();
       while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}
       return;
     }
+    __syncthreads();   // every thread's copies are visible
     for (int a = tid; a < k; a += NT) S[rowoff(a) + a] += dg[a];
     for (int a = tid; a < kp; a += NT) v[a] = rh[a];   // right-hand side, reduced during the factorisation
     __syncthreads();
@@ -439,14 +507,19 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
       for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(fac)[e] = reinterpret_cast<const float4*>(S)[e];
   }
 
+  // inverses of the 16-row diagonal blocks (their off-diagonal parts, in the panel's space)
+  float* mo = pan;
+  pair_blocks_prepare(S, linv, mo, Q, tid, NT);
+  __syncthreads();
+
   // x = S^{-1} rhs: the factorisation already applied L^{-1} to v; with loaded factors
   // the forward substitution runs here
   if (mode == kSolveAdjoint && fac != nullptr) {
     for (int a = tid; a < kp; a += NT) v[a] = rh[a];
     __syncthreads();
-    block_fwd<NT>(S, linv, v, Q, tid, lane, warp);
+    block_fwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
   }
-  block_bwd<NT>(S, linv, v, Q, tid, lane, warp);
+  block_bwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
   for (int a = tid; a < kp; a += NT) xs[a] = v[a];
   __syncthreads();
 
@@ -474,8 +547,8 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
         v[a] = a < k ? rh[a] - fmaf(dg[a], xs[a], (s4[0] + s4[1]) + (s4[2] + s4[3])) : 0.f;
       }
       __syncthreads();
-      block_fwd<NT>(S, linv, v, Q, tid, lane, warp);
-      block_bwd<NT>(S, linv, v, Q, tid, lane, warp);
+      block_fwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
+      block_bwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
       for (int a = tid; a < kp; a += NT) xs[a] += v[a];
       __syncthreads();
       continue;
@@ -531,8 +604,8 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
       }
     }
     __syncthreads();
-    block_fwd<NT>(S, linv, v, Q, tid, lane, warp);
-    block_bwd<NT>(S, linv, v, Q, tid, lane, warp);
+    block_fwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
+    block_bwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
     for (int a = tid; a < kp; a += NT) xs[a] += v[a];
     __syncthreads();
   }
