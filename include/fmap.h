@@ -69,6 +69,19 @@ typedef struct fmap_options {
                                    backward pass (default 304: store everything) */
     int32_t adjoint_ir_steps;   /* refinement steps of the adjoint row solves (0..3, default 0: the
                                    FP32 factor solve alone is far inside the gradient tolerance) */
+    /* Tuning knobs (0 = the built-in choice). They change how work is cut into tiles and
+     * launches, never the arithmetic of an output element beyond the order of its
+     * partial sums; the autotuner (paper_2604_10377_gb300.autotune) searches them. */
+    int32_t proj_max_stages;    /* tensor-core projection: pipeline depth cap, 2..6 (default 6) */
+    int32_t proj_seg_max_v;     /* tensor-core projection: longest vertex segment accumulated in
+                                   TMEM before a partial is written, multiple of 64 in
+                                   1024..65536 (default 8192) */
+    int32_t bwd_group_features; /* tensor-core backward projection: features per CTA group,
+                                   64 or 128 (default 128) */
+    int32_t bwd_chunk_v;        /* tensor-core backward projection: largest vertex chunk of a work
+                                   item, multiple of 128 in 1024..65536 (default 8192) */
+    int32_t solve_threads_k64;  /* row-solve block for k <= 64: 64 or 128 threads (default 64) */
+    int32_t solve_threads_k128; /* row-solve block for 64 < k <= 128: 128 or 256 (default 128) */
 } fmap_options;
 
 typedef struct fmap_shape_desc {
@@ -120,7 +133,7 @@ FMAP_API const char* fmap_error_string(int32_t code);
 FMAP_API const char* fmap_last_cuda_error(void);
 
 /* Fill *opt with the defaults: FP32, ir_steps 1, hi_gram_min_k 200, store_factors_max_k 304,
- * adjoint_ir_steps 0. */
+ * adjoint_ir_steps 0, every tuning knob 0 (built-in choice). */
 FMAP_API int32_t fmap_default_options(fmap_options* opt);
 
 /* Create a context on CUDA device `device` (host only; no device memory is touched

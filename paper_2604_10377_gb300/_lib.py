@@ -27,7 +27,13 @@ FMAP_PREC_BF16 = 1
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("ir_steps", c_int32), ("hi_gram_min_k", c_int32),
-                ("store_factors_max_k", c_int32), ("adjoint_ir_steps", c_int32)]
+                ("store_factors_max_k", c_int32), ("adjoint_ir_steps", c_int32),
+                ("proj_max_stages", c_int32), ("proj_seg_max_v", c_int32), ("bwd_group_features", c_int32),
+                ("bwd_chunk_v", c_int32), ("solve_threads_k64", c_int32), ("solve_threads_k128", c_int32)]
+
+
+TUNING_FIELDS = ("proj_max_stages", "proj_seg_max_v", "bwd_group_features", "bwd_chunk_v",
+                 "solve_threads_k64", "solve_threads_k128")
 
 
 class ShapeDesc(ctypes.Structure):

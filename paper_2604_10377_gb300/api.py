@@ -92,7 +92,7 @@ class FmapBatch:
 
     def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
                  with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
-                 store_factors_max_k: int = 304, adjoint_ir_steps: int = 0):
+                 store_factors_max_k: int = 304, adjoint_ir_steps: int = 0, tuning: Optional[dict] = None):
         self.layout = layout
         self.device = torch.device(device)
         self.precision = precision
@@ -123,11 +123,13 @@ class FmapBatch:
         opt.store_factors_max_k = store_factors_max_k
         opt.adjoint_ir_steps = adjoint_ir_steps
         self.options = opt
-        ctx = ctypes.c_void_p()
-        check(L.fmap_create(ctypes.byref(ctx), self.device.index or 0, ctypes.byref(opt)), "fmap_create")
-        self._ctx = ctx
+        self._ctx = None
         self._batch = None
-        self._build()
+        self.ws = None
+        self.saved = None
+        self._apply_tuning(tuning or {})
+        self._create()
+        self._alloc_outputs()
 
     # ------------------------------------------------------------------ setup
     def _descs(self):
@@ -150,8 +152,22 @@ class FmapBatch:
             pd[p].mask = (self.mask.data_ptr() + 4 * int(self.c_off_host[p])) if self._masks_present[p] else None
         return sd, pd
 
-    def _build(self):
+    def _apply_tuning(self, tuning: dict):
+        for name in _lib.TUNING_FIELDS:
+            setattr(self.options, name, int(tuning.get(name, 0)))
+
+    @property
+    def tuning(self) -> dict:
+        """The tuning knobs of this batch (0 = the library's built-in choice)."""
+        return {name: int(getattr(self.options, name)) for name in _lib.TUNING_FIELDS}
+
+    def _create(self):
+        """Context + batch handle for the current options over the same device buffers; the
+        workspace and factor buffers are (re)allocated when their sizes change."""
         L = _lib.lib()
+        ctx = ctypes.c_void_p()
+        check(L.fmap_create(ctypes.byref(ctx), self.device.index or 0, ctypes.byref(self.options)), "fmap_create")
+        self._ctx = ctx
         sd, pd = self._descs()
         b = ctypes.c_void_p()
         check(L.fmap_batch_create(self._ctx, sd, self.layout.n_shapes, pd, len(self.pairs), ctypes.byref(b)),
@@ -166,8 +182,22 @@ class FmapBatch:
         self.a_off = np.array(a_off[:], dtype=np.int64)
         self.c_off = np.array(c_off[:], dtype=np.int64)
         dev = self.device
-        self.ws = torch.empty(max(256, sz.ws_bwd_bytes), dtype=torch.uint8, device=dev)
-        self.saved = torch.empty(max(256, sz.saved_bytes), dtype=torch.uint8, device=dev) if sz.saved_bytes else None
+        if self.ws is None or self.ws.numel() < sz.ws_bwd_bytes:
+            self.ws = torch.empty(max(256, sz.ws_bwd_bytes), dtype=torch.uint8, device=dev)
+        if sz.saved_bytes and (self.saved is None or self.saved.numel() < sz.saved_bytes):
+            self.saved = torch.empty(max(256, sz.saved_bytes), dtype=torch.uint8, device=dev)
+
+    def retune(self, tuning: dict):
+        """Re-plan the batch with other tuning knobs (see fmap_options). Inputs, outputs and
+        results stay where they are; only the library's work lists change."""
+        torch.cuda.synchronize(self.device)
+        self.close()
+        self._apply_tuning(tuning)
+        self._create()
+
+    def _alloc_outputs(self):
+        sz = self.sizes
+        dev = self.device
         self.A = torch.empty(max(1, sz.a_floats), dtype=torch.float32, device=dev)
         self.C = torch.empty(max(1, sz.c_floats), dtype=torch.float32, device=dev)
         self.dA = torch.empty_like(self.A)
@@ -201,13 +231,37 @@ class FmapBatch:
         return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(_lib.KIND_NAMES)}
 
     # ------------------------------------------------------------------ data
-    def upload(self, host: dict, non_blocking: bool = False):
-        """Copy flat host arrays (from BatchLayout.pack_host, or pinned torch tensors) to the device."""
+    def upload(self, host: dict, non_blocking: bool = False, copy_streams: int = 1):
+        """Copy flat host arrays (from BatchLayout.pack_host, or pinned torch tensors) to the device.
+
+        With non_blocking and copy_streams > 1 the copies are cut into 64 MiB pieces spread
+        over that many side streams (several copy engines at once); the side streams start
+        after the current stream's earlier work and the current stream waits for them, so
+        the call stays ordered like a single copy."""
+        srcs = []
         for name in ("phi", "mass", "evals", "feat"):
             src = host[name]
             if isinstance(src, np.ndarray):
                 src = host_to_torch(src)
-            getattr(self, name).copy_(src, non_blocking=non_blocking)
+            srcs.append((getattr(self, name), src))
+        if copy_streams <= 1 or not non_blocking:
+            for dst, src in srcs:
+                dst.copy_(src, non_blocking=non_blocking)
+            return
+        if len(getattr(self, "_copy_streams", [])) != copy_streams:
+            self._copy_streams = [torch.cuda.Stream(self.device) for _ in range(copy_streams)]
+        cur = torch.cuda.current_stream(self.device)
+        for st in self._copy_streams:
+            st.wait_stream(cur)
+        i = 0
+        for dst, src in srcs:
+            step = max(1, (64 << 20) // dst.element_size())
+            for o in range(0, dst.numel(), step):
+                with torch.cuda.stream(self._copy_streams[i % copy_streams]):
+                    dst[o:o + step].copy_(src[o:o + step], non_blocking=True)
+                i += 1
+        for st in self._copy_streams:
+            cur.wait_stream(st)
 
     def a_view(self, flat: torch.Tensor, s: int) -> torch.Tensor:
         k, d = self.layout.ks[s], self.layout.ds[s]

@@ -106,6 +106,16 @@ int32_t validate_options(const fmap_options& o) {
   if (o.ir_steps < 0 || o.ir_steps > 3) return FMAP_ERR_INVALID_ARG;
   if (o.hi_gram_min_k < 1 || o.store_factors_max_k < 0) return FMAP_ERR_INVALID_ARG;
   if (o.adjoint_ir_steps < 0 || o.adjoint_ir_steps > 3) return FMAP_ERR_INVALID_ARG;
+  if (o.proj_max_stages != 0 && (o.proj_max_stages < 2 || o.proj_max_stages > 6)) return FMAP_ERR_INVALID_ARG;
+  if (o.proj_seg_max_v != 0 && (o.proj_seg_max_v < 2048 || o.proj_seg_max_v > 16384 || o.proj_seg_max_v % 64))
+    return FMAP_ERR_INVALID_ARG;
+  if (o.bwd_group_features != 0 && o.bwd_group_features != 64 && o.bwd_group_features != 128)
+    return FMAP_ERR_INVALID_ARG;
+  if (o.bwd_chunk_v != 0 && (o.bwd_chunk_v < 1024 || o.bwd_chunk_v > 65536 || o.bwd_chunk_v % 128))
+    return FMAP_ERR_INVALID_ARG;
+  if (o.solve_threads_k64 != 0 && o.solve_threads_k64 != 64 && o.solve_threads_k64 != 128) return FMAP_ERR_INVALID_ARG;
+  if (o.solve_threads_k128 != 0 && o.solve_threads_k128 != 128 && o.solve_threads_k128 != 256)
+    return FMAP_ERR_INVALID_ARG;
   return FMAP_OK;
 }
 
@@ -204,6 +214,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         }
       }
     }
+    const int64_t seg_max = opt.proj_seg_max_v ? (int64_t)opt.proj_seg_max_v : kTcSegMaxV;
     for (int cls = 0; cls < 4; ++cls) {
       const std::vector<Unit>& units = classes[cls];
       if (units.empty()) continue;
@@ -237,7 +248,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
           if (cta == kTcCtas - 1) take = sd.n - v;
           // a segment accumulates in TMEM; bounding its length bounds the accumulated
           // rounding of the tensor-core FP32 sums (partials are added in IEEE FP32)
-          take = std::min<int64_t>(std::min<int64_t>(take, kTcSegMaxV), sd.n - v);
+          take = std::min<int64_t>(std::min<int64_t>(take, seg_max), sd.n - v);
           TcItem it{};
           it.shape = u.s; it.f0 = u.f0; it.fg = u.fg; it.npad = u.npad;
           it.n0 = u.n0; it.nk = u.nk;
@@ -265,7 +276,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       L.tmem_cols = cols;
       const int fixed = 1024 + 512;
       const int per_stage = (int)(L.f_stage + L.p_stage) + kStageV * 4;
-      L.stages = std::min(6, (kSmemBudget - fixed) / per_stage);
+      L.stages = std::min(opt.proj_max_stages ? opt.proj_max_stages : 6, (kSmemBudget - fixed) / per_stage);
       if (L.stages < 2) return FMAP_ERR_UNSUPPORTED;
       L.smem = fixed + L.stages * per_stage;
       P.tc_smem = std::max(P.tc_smem, L.smem);
@@ -305,14 +316,16 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     int64_t bw_work = 0;
     for (int s = 0; s < n_shapes; ++s)
       if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + 255) / 256);
-    const int64_t bw_chunk = std::min<int64_t>(
-        kTcChunkV, std::max<int64_t>(1024, (bw_work / (4 * n_clusters) + 127) / 128 * 128));
+    const int64_t bw_chunk = opt.bwd_chunk_v ? (int64_t)opt.bwd_chunk_v
+                                             : std::min<int64_t>(kTcChunkV, std::max<int64_t>(
+                                                   1024, (bw_work / (4 * n_clusters) + 127) / 128 * 128));
+    const int bw_gf = opt.bwd_group_features ? opt.bwd_group_features : 128;
     std::vector<TcBwdItem> items;   // pairs: [2 j] for cluster rank 0, [2 j + 1] for rank 1
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
       if (!sd.dfeat) continue;
       const int kb = (sd.k + 31) / 32;
-      const int ngroups = 2 * ((sd.d + 255) / 256);
+      const int ngroups = 2 * ((sd.d + 2 * bw_gf - 1) / (2 * bw_gf));
       const int nf_s = ((sd.d + ngroups - 1) / ngroups + 15) / 16 * 16;
       std::vector<TcBwdGroup> gl(ngroups);
       for (int g = 0; g < ngroups; ++g) {
@@ -415,7 +428,8 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   // (k <= 64: 64 threads, <= 128: 128, <= 256: 256, <= kMaxK: 320 -- every block has at
   // least one thread per padded row)
   const int bounds[4] = {64, 128, 256, kMaxK};
-  const int threads[4] = {64, 128, 256, 320};
+  const int threads[4] = {opt.solve_threads_k64 ? opt.solve_threads_k64 : 64,
+                          opt.solve_threads_k128 ? opt.solve_threads_k128 : 128, 256, 320};
   for (int gi = 0; gi < 4; ++gi) {
     SolveGroup g{};
     g.first = (int32_t)P.systems.size();
@@ -533,6 +547,7 @@ const char* fmap_last_cuda_error(void) { return g_last_cuda_error; }
 
 int32_t fmap_default_options(fmap_options* opt) {
   if (!opt) return FMAP_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));   // tuning knobs: 0 = built-in choice
   opt->precision = FMAP_PREC_FP32;
   opt->ir_steps = 1;
   opt->hi_gram_min_k = 200;

@@ -119,15 +119,19 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
   float acc[4][4] = {};
   for (int m0 = 0; m0 < k; m0 += kStage) {
     for (int e = tid; e < kTile * kStage; e += 256) {
+      // Gamma^T[a][m] = Gamma[m][a]: consecutive threads take consecutive a (coalesced)
+      const int aa = e % kTile, mm = e / kTile;
+      const int a = a0 + aa, m = m0 + mm;
+      if (which == 0) sX[aa][mm] = (a < k && m < k) ? gam[(int64_t)m * k + a] : 0.f;
+    }
+    for (int e = tid; e < kTile * kStage; e += 256) {
       const int aa = e / kStage, mm = e % kStage;
       const int a = a0 + aa, m = m0 + mm;
       const bool ok = a < k && m < k;
-      if (which == 0) {
-        sX[aa][mm] = ok ? gam[(int64_t)m * k + a] : 0.f;     // Gamma^T[a][m]
+      if (which == 0)
         sX2[aa][mm] = ok ? -w[(int64_t)a * k + m] : 0.f;     // -W[a][m]
-      } else {
+      else
         sX[aa][mm] = ok ? gam[(int64_t)a * k + m] : 0.f;     // Gamma[a][m]
-      }
     }
     for (int e = tid; e < kStage * kTile; e += 256) {
       const int mm = e / kTile, ff = e % kTile;
@@ -214,7 +218,8 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
       sX[r][mm] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
     }
     for (int q = tid; q < kStage * kTile; q += 256) {
-      const int mm = q / kTile, r = q % kTile;
+      // C^T[m][b] = C[b][m]: consecutive threads take consecutive m (one row segment)
+      const int mm = q % kStage, r = q / kStage;
       sY[mm][r] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
     }
     __syncthreads();

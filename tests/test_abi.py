@@ -153,6 +153,37 @@ def test_options_validation(lib):
     assert lib.fmap_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == 1
 
 
+@pytest.mark.parametrize("knob,good,bad", [
+    ("proj_max_stages", (0, 2, 6), (1, 7)),
+    ("proj_seg_max_v", (0, 2048, 16384), (1024, 4000, 32768)),
+    ("bwd_group_features", (0, 64, 128), (32, 96, 256)),
+    ("bwd_chunk_v", (0, 1024, 65536), (512, 1000, 131072)),
+    ("solve_threads_k64", (0, 64, 128), (32, 256)),
+    ("solve_threads_k128", (0, 128, 256), (64, 320)),
+])
+def test_tuning_knob_validation(lib, knob, good, bad):
+    """Every tuning knob defaults to 0 (built-in choice); values outside its documented set
+    are rejected synchronously; accepted values plan the same outputs."""
+    from paper_2604_10377_gb300 import _lib
+    o = _lib.default_options()
+    assert all(getattr(o, f) == 0 for f in _lib.TUNING_FIELDS)
+    specs = [dict(n=5000, k=30, d=256), dict(n=7000, k=30, d=256), dict(n=900, k=120, d=256),
+             dict(n=800, k=120, d=256)]
+    pairs = [(0, 1, 1e-3), (2, 3, 1e-3)]
+    o.precision = 1
+    rc, ref = _plan(lib, specs, pairs, o)
+    assert rc == 0
+    for v in good:
+        setattr(o, knob, v)
+        rc, sz = _plan(lib, specs, pairs, o)
+        assert rc == 0, (knob, v)
+        assert (sz.a_floats, sz.c_floats, sz.saved_bytes) == (ref.a_floats, ref.c_floats, ref.saved_bytes)
+    for v in bad:
+        setattr(o, knob, v)
+        rc, _ = _plan(lib, specs, pairs, o)
+        assert rc == 1, (knob, v)
+
+
 def test_store_factor_threshold(lib):
     from paper_2604_10377_gb300 import _lib
     o = _lib.default_options()

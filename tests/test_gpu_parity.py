@@ -227,6 +227,51 @@ def test_large_spectral_sizes(feat_dtype, use_saved):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= gtol
 
 
+def _tuning_cases():
+    from paper_2604_10377_gb300.autotune import CANDIDATES
+    return [(knob, v) for knob, vals in CANDIDATES.items() for v in vals if v != 0]
+
+
+@pytest.mark.parametrize("knob,value", _tuning_cases())
+def test_every_tuning_candidate_matches_the_oracle(knob, value):
+    """Each value the autotuner may pick re-plans the launches without changing the
+    results beyond the order of partial sums: forward and backward stay within tolerance."""
+    wl = synth.make_small(13, 4, (300, 9000), [30, 64, 100, 128], 256, feat_dtype="bf16")
+    out = _gpu_backward(wl, tuning={knob: value})
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert rel_fro(out["C"][p], fwd["C"][p]) <= TOL["bf16"]
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
+
+
+def test_autotune_picks_a_candidate_and_keeps_results():
+    from paper_2604_10377_gb300 import api, autotune
+    wl = synth.make_small(14, 6, (2000, 30000), [30, 50, 100], 256, feat_dtype="bf16")
+    b = api.batch_from_workload(wl, with_grad=True)
+    gt = api.flat_c(b, [p.c_gt for p in wl.pairs])
+    loss = torch.empty(len(wl.pairs), device=b.device)
+    dc = torch.empty_like(b.C)
+
+    def step():
+        a = b.project()
+        c = b.solve(a)
+        b.loss_orth(c, gt, loss=loss, d_c=dc)
+        b.solve_backward(dc, a, c)
+
+    res = autotune.autotune(b, step, iters=1, reps=1)
+    for knob, v in res["tuning"].items():
+        assert v in autotune.CANDIDATES[knob]
+    assert res["ms"] <= res["baseline_ms"]
+    step()
+    torch.cuda.synchronize()
+    shapes, pairs = oracle_inputs(wl)
+    fwd = orc.forward_batch(shapes, pairs)
+    for p in range(len(wl.pairs)):
+        assert rel_fro(b.c_view(b.C, p).cpu().numpy(), fwd["C"][p]) <= TOL["bf16"]
+
+
 def test_gradient_against_finite_differences():
     """GPU dL/dF (FP32 mode) against central differences (h = 1e-3) of the FP64
     pipeline along 8 seeded random directions per shape."""
