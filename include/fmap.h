@@ -73,9 +73,10 @@ typedef struct fmap_options {
      * launches, never the arithmetic of an output element beyond the order of its
      * partial sums; the autotuner (paper_2604_10377_gb300.autotune) searches them. */
     int32_t proj_max_stages;    /* tensor-core projection: pipeline depth cap, 2..6 (default 6) */
-    int32_t proj_seg_max_v;     /* tensor-core projection: longest vertex segment accumulated in
-                                   TMEM before a partial is written, multiple of 64 in
-                                   1024..65536 (default 8192) */
+    int32_t proj_seg_max_v;     /* tensor-core projection of BF16 features: longest vertex segment
+                                   accumulated in TMEM before a partial is written, multiple of
+                                   64 in 2048..16384 (default 8192); FP32 features always use
+                                   512 (accuracy of the three TF32 passes) */
     int32_t bwd_group_features; /* tensor-core backward projection: features per CTA group,
                                    64 or 128 (default 128) */
     int32_t bwd_chunk_v;        /* tensor-core backward projection: largest vertex chunk of a work

@@ -19,6 +19,7 @@ SOURCES = [
     "fmap_api.cu",
     "k_project_simt.cu",
     "k_project_tc.cu",
+    "k_project_tc32.cu",
     "k_project_bwd_tc.cu",
     "k_gram.cu",
     "k_solve.cu",

@@ -29,7 +29,8 @@ constexpr int kTile = 64;
 constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core backward projection
 constexpr int kTcCtas = 152;           // persistent CTAs of the projection (one per GB300 SM)
 constexpr int64_t kStageV = 64;        // vertices per projection pipeline stage
-constexpr int64_t kTcSegMaxV = 8192;   // longest projection segment (one TMEM accumulation)
+constexpr int64_t kTcSegMaxV = 8192;   // longest projection segment (one TMEM accumulation), BF16 F
+constexpr int64_t kTc32SegMaxV = 512;   // the same for FP32 F (accuracy of the TF32 passes)
 constexpr int kSmemBudget = 227 * 1024;
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -84,8 +85,10 @@ struct Plan {
   int64_t max_kd = 0;
   int64_t da_int_off = 0;
   int64_t loss_part_off = 0;
-  // tensor-core projection (BF16 features)
-  bool tc = false;
+  // tensor-core projection
+  bool tc = false;        // projection on the tensor cores (every precision)
+  bool tc32 = false;      // FP32 features: three-pass TF32 kernel
+  bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features)
   std::vector<TcItem> tc_items;
   std::vector<int32_t> tc_cta_first;   // kTcCtas + 1 entries per launch
   std::vector<TcLaunch> tc_launches;
@@ -177,7 +180,9 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   // ---- workspace layout (floats, 256-byte aligned regions); the first 256 bytes
   // hold control words (word 0: error raised by a device-side wait that timed out)
   int64_t cur = kAlignFloats;
-  P.tc = opt.precision == FMAP_PREC_BF16;
+  P.tc = true;
+  P.tc32 = opt.precision == FMAP_PREC_FP32;
+  P.tc_bwd = opt.precision == FMAP_PREC_BF16;
   if (!P.tc) {
     for (auto& sd : P.shapes) {
       sd.part_off = cur;
@@ -188,19 +193,29 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     // 128, 256); every class is one launch with its own pipeline depth, and within a
     // class a stream-K split of the vertex ranges into kTcCtas ranges of equal cost
     // (64-vertex granularity)
-    // A spectral size above 256 (the MMA's largest N) is split into two basis ranges
-    // (units n0 = 0 and n0 = 160), each reading its own Phi columns and all of F.
+    // A spectral size above the widest basis range of one unit (256, the MMA's largest
+    // N, for BF16 features; 128 for FP32 features, whose stages are larger) is split
+    // into basis ranges of equal width (a multiple of 32), each reading its own Phi
+    // columns and all of F.
     struct Unit { int s, f0, fg, npad, n0, nk, dspan; double cpv; };
     std::vector<Unit> classes[4];
+    const int nmax = P.tc32 ? 128 : 256;
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
-      const int nsplit = sd.k > 256 ? 2 : 1;
+      const int nsplit = (sd.k + nmax - 1) / nmax;
+      const int width = ((sd.k + nsplit - 1) / nsplit + 31) / 32 * 32;
       for (int h = 0; h < nsplit; ++h) {
-        const int n0 = h * 160;
-        const int nk = nsplit == 1 ? sd.k : (h == 0 ? 160 : sd.k - 160);
+        const int n0 = h * width;
+        const int nk = std::min(width, sd.k - n0);
+        if (nk <= 0) continue;
         const int npad = (nk + 15) / 16 * 16;
         const int mt = (sd.d + 127) / 128;
-        const int fg_cap = std::max(1, std::min(4, 512 / npad));
+        int fg_cap = std::max(1, std::min(4, 512 / npad));
+        if (P.tc32) {
+          // two stages of (F + its remainder: 32 KB per group) + Phi, Ph, Pl must fit
+          const int pb = (npad + 31) / 32 * 4096 + npad * 256;
+          fg_cap = std::max(1, std::min(std::min(fg_cap, 2), ((kSmemBudget - 1536) / 2 - pb - 128) / 32768));
+        }
         const int groups = (mt + fg_cap - 1) / fg_cap;
         const int fg_s = (mt + groups - 1) / groups;
         const int cls = npad <= 32 ? 0 : (npad <= 64 ? 1 : (npad <= 128 ? 2 : 3));
@@ -214,7 +229,13 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         }
       }
     }
-    const int64_t seg_max = opt.proj_seg_max_v ? (int64_t)opt.proj_seg_max_v : kTcSegMaxV;
+    // The tensor cores accumulate a segment in TMEM; the FP32-feature kernel bounds that
+    // chain to 512 vertices (64 K-steps) so that the accumulator's rounding stays in the
+    // FP32 class (a longer chain drifts, ~6e-8 relative per K-step); partials are then
+    // added in IEEE FP32 by the reduction. The tuning knob applies to BF16 features.
+    const int64_t seg_max = P.tc32 ? kTc32SegMaxV : (opt.proj_seg_max_v ? (int64_t)opt.proj_seg_max_v : kTcSegMaxV);
+    // vertices per pipeline stage: 64 (BF16 F, one 128-byte row of BF16) or 32 (FP32 F)
+    const int64_t stage_v = P.tc32 ? 32 : kStageV;
     for (int cls = 0; cls < 4; ++cls) {
       const std::vector<Unit>& units = classes[cls];
       if (units.empty()) continue;
@@ -222,8 +243,12 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       double total = 0.0;
       for (const Unit& u : units) {
         total += u.cpv * (double)P.shapes[u.s].n;
-        fmax = std::max<uint32_t>(fmax, (uint32_t)u.fg * 16384u);
-        const uint32_t pb = std::max<uint32_t>((uint32_t)((u.npad + 31) / 32) * 8192u, (uint32_t)u.npad * 256u);
+        // BF16: F tile; Phi tile converted in place into P hi / lo.
+        // FP32: F tile and its TF32 remainder; Phi tile, then P hi and P lo beside it.
+        const uint32_t kbu = (uint32_t)((u.npad + 31) / 32);
+        fmax = std::max<uint32_t>(fmax, (uint32_t)u.fg * (P.tc32 ? 32768u : 16384u));
+        const uint32_t pb = P.tc32 ? kbu * 4096u + (uint32_t)u.npad * 256u
+                                   : std::max<uint32_t>(kbu * 8192u, (uint32_t)u.npad * 256u);
         pmax = std::max<uint32_t>(pmax, pb);
         tmax = std::max<uint32_t>(tmax, (uint32_t)(u.fg * u.npad));
       }
@@ -244,7 +269,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         int64_t v = 0;
         while (v < sd.n) {
           int64_t take = (int64_t)std::ceil(std::max(budget, 0.0) / u.cpv);
-          take = std::max<int64_t>(kStageV, (take + kStageV - 1) / kStageV * kStageV);
+          take = std::max<int64_t>(stage_v, (take + stage_v - 1) / stage_v * stage_v);
           if (cta == kTcCtas - 1) take = sd.n - v;
           // a segment accumulates in TMEM; bounding its length bounds the accumulated
           // rounding of the tensor-core FP32 sums (partials are added in IEEE FP32)
@@ -275,7 +300,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       while (cols < tmax) cols <<= 1;
       L.tmem_cols = cols;
       const int fixed = 1024 + 512;
-      const int per_stage = (int)(L.f_stage + L.p_stage) + kStageV * 4;
+      const int per_stage = (int)(L.f_stage + L.p_stage) + (int)stage_v * 4;
       L.stages = std::min(opt.proj_max_stages ? opt.proj_max_stages : 6, (kSmemBudget - fixed) / per_stage);
       if (L.stages < 2) return FMAP_ERR_UNSUPPORTED;
       L.smem = fixed + L.stages * per_stage;
@@ -307,7 +332,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   }
   P.da_int_off = cur;
   cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
-  if (P.tc) {
+  if (P.tc_bwd) {
     // Backward work runs on clusters of two CTAs that share each Phi tile (multicast):
     // a shape's features split into an even number of groups of <= 128, and a work
     // item is (shape, vertex chunk, pair of groups), one group per CTA of the
@@ -415,7 +440,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
           t.v1 = std::min<int64_t>(sd.n, t.v0 + kChunkV);
           P.ptiles.push_back(t);
         }
-    if (sd.dfeat && !P.tc)
+    if (sd.dfeat && !P.tc_bwd)
       for (int64_t v0 = 0; v0 < sd.n; v0 += kTile)
         for (int f0 = 0; f0 < sd.d; f0 += kTile) {
           BwdTile t;
@@ -639,26 +664,30 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
     if (!encode) { cudaFree(b->dev_mem); delete b; return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
+      // features: BF16 box 64 features x 64 vertices, or FP32 box 32 features x 32 vertices
+      // (a 128-byte row either way); the basis and mass boxes follow the stage length
+      const cuuint32_t sv = P.tc32 ? 32 : 64;
       CUtensorMap m;
       cuuint64_t gdim[2] = {(cuuint64_t)sd.d, (cuuint64_t)sd.n};
-      cuuint64_t gstride[1] = {(cuuint64_t)sd.ld_feat * 2};
-      cuuint32_t box[2] = {64, 64};
+      cuuint64_t gstride[1] = {(cuuint64_t)sd.ld_feat * (P.tc32 ? 4 : 2)};
+      cuuint32_t box[2] = {P.tc32 ? 32u : 64u, sv};
       cuuint32_t estr[2] = {1, 1};
-      CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(sd.feat), gdim, gstride, box,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      CUresult r = encode(&m, P.tc32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void*>(sd.feat), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) {
         cudaFree(b->dev_mem); delete b;
         std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled failed (%d)", (int)r);
         return FMAP_ERR_CUDA;
       }
       put(o_tm + s * (int64_t)sizeof(CUtensorMap), &m, sizeof(m));
-      // FP32 basis, box 32 basis x 64 vertices (the forward projection's tiles and the
-      // halves of the backward projection's 128-vertex tiles)
+      // FP32 basis, box 32 basis x sv vertices (the forward projection's tiles and, at 64
+      // vertices, the halves of the backward projection's 128-vertex tiles)
       CUtensorMap pm;
       cuuint64_t pdim[2] = {(cuuint64_t)sd.k, (cuuint64_t)sd.n};
       cuuint64_t pstride[1] = {(cuuint64_t)sd.ld_phi * 4};
-      cuuint32_t fbox[2] = {32, 64};
+      cuuint32_t fbox[2] = {32, sv};
       r = encode(&pm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sd.phi), pdim, pstride, fbox, estr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -668,11 +697,11 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
         return FMAP_ERR_CUDA;
       }
       put(o_fp + s * (int64_t)sizeof(CUtensorMap), &pm, sizeof(pm));
-      // mass: 1-D, box of 64
+      // mass: 1-D, box of sv
       CUtensorMap mm;
       cuuint64_t mdim[1] = {(cuuint64_t)sd.n};
       cuuint64_t mstride[1] = {4};
-      cuuint32_t mbox[1] = {64};
+      cuuint32_t mbox[1] = {sv};
       cuuint32_t mestr[1] = {1};
       r = encode(&mm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(sd.mass), mdim, mstride, mbox, mestr,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -686,7 +715,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
       // BF16 dF: box 16 features x 32 vertices, stored by the backward projection
       CUtensorMap dm;
       std::memset(&dm, 0, sizeof(dm));
-      if (sd.dfeat) {
+      if (sd.dfeat && P.tc_bwd) {
         cuuint32_t dbox[2] = {16, 32};
         r = encode(&dm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sd.dfeat, gdim, gstride, dbox, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -709,7 +738,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
     put(o_ti, P.tc_items.data(), P.tc_items.size() * sizeof(TcItem));
     put(o_to, P.tc_cta_first.data(), P.tc_cta_first.size() * sizeof(int32_t));
     put(o_tg, P.tc_groups.data(), P.tc_groups.size() * sizeof(TcRedGroup));
-    e = project_tc_set_smem(P.tc_smem);
+    e = P.tc32 ? project_tc32_set_smem(P.tc_smem) : project_tc_set_smem(P.tc_smem);
     if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project)"); }
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -827,7 +856,7 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
       tp.err = static_cast<int*>(ws);
       {
         TimedScope ts(b, FMAP_KIND_PROJECT, st);
-        e = launch_project_tc(tp, kTcCtas, L.smem, st);
+        e = P.tc32 ? launch_project_tc32(tp, kTcCtas, L.smem, st) : launch_project_tc(tp, kTcCtas, L.smem, st);
       }
       if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
     }

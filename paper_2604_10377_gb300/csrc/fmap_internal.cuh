@@ -114,9 +114,10 @@ struct TcRedGroup {
 
 struct TcProjParams {
   const ShapeDev* shapes;
-  const CUtensorMap* fmaps;     // per shape: BF16 features, box 64 features x 64 vertices, 128-byte swizzle
-  const CUtensorMap* phimaps;   // per shape: FP32 basis, box 32 basis x 64 vertices, 128-byte swizzle
-  const CUtensorMap* massmaps;  // per shape: FP32 mass, 1-D box of 64
+  const CUtensorMap* fmaps;     // per shape: features, BF16 box 64 x 64 or FP32 box 32 x 32 (features x
+                                //   vertices), 128-byte swizzle
+  const CUtensorMap* phimaps;   // per shape: FP32 basis, box 32 basis x (64 or 32) vertices, 128-byte swizzle
+  const CUtensorMap* massmaps;  // per shape: FP32 mass, 1-D box of 64 or 32
   const TcItem* items;          // segments, grouped by CTA
   const int32_t* cta_first;     // CTA c owns segments [cta_first[c], cta_first[c + 1])
   int32_t stages;
@@ -159,6 +160,8 @@ cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* gro
 cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st);
 
 cudaError_t project_tc_set_smem(int bytes);
+cudaError_t project_tc32_set_smem(int bytes);
+cudaError_t launch_project_tc32(const TcProjParams& p, int grid, int smem_bytes, cudaStream_t st);
 int project_tc_threads();
 cudaError_t launch_project_tc(const TcProjParams& p, int grid, int smem_bytes, cudaStream_t st);
 cudaError_t launch_project_tc_reduce(const ShapeDev* shapes, const TcItem* items, const TcRedGroup* groups,
