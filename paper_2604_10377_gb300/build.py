@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libfmap.so")
 
 SOURCES = [
     "fmap_api.cu",
-    "k_project_simt.cu",
+    "k_project_bwd_simt.cu",
     "k_project_tc.cu",
     "k_project_tc32.cu",
     "k_project_bwd_tc.cu",

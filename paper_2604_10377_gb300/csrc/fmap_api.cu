@@ -24,7 +24,6 @@ int32_t cuda_fail(cudaError_t e, const char* where) {
 }
 
 constexpr int64_t kAlignFloats = 64;   // 256-byte alignment of workspace regions
-constexpr int64_t kChunkV = 4096;      // vertices per split-K chunk of the projection
 constexpr int kTile = 64;
 constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core backward projection
 constexpr int kTcCtas = 152;           // persistent CTAs of the projection (one per GB300 SM)
@@ -77,7 +76,6 @@ struct Plan {
   std::vector<ShapeDev> shapes;
   std::vector<PairDev> pairs;
   std::vector<int64_t> a_off, c_off, slot_list;
-  std::vector<ProjTile> ptiles;
   std::vector<BwdTile> btiles;
   std::vector<int2> systems;
   std::vector<SolveGroup> groups;
@@ -86,7 +84,6 @@ struct Plan {
   int64_t da_int_off = 0;
   int64_t loss_part_off = 0;
   // tensor-core projection
-  bool tc = false;        // projection on the tensor cores (every precision)
   bool tc32 = false;      // FP32 features: three-pass TF32 kernel
   bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features)
   std::vector<TcItem> tc_items;
@@ -149,7 +146,6 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     sd.phi = d.phi; sd.ld_phi = d.ld_phi; sd.mass = d.mass; sd.evals = d.evals;
     sd.feat = d.feat; sd.ld_feat = d.ld_feat; sd.dfeat = d.dfeat;
     sd.a_off = P.a_off[s];
-    sd.nchunk = (int32_t)((d.n + kChunkV - 1) / kChunkV);
     P.a_off[s + 1] = P.a_off[s] + (int64_t)d.k * d.d;
     P.max_k = std::max(P.max_k, d.k);
     P.max_d = std::max(P.max_d, d.d);
@@ -180,15 +176,9 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   // ---- workspace layout (floats, 256-byte aligned regions); the first 256 bytes
   // hold control words (word 0: error raised by a device-side wait that timed out)
   int64_t cur = kAlignFloats;
-  P.tc = true;
   P.tc32 = opt.precision == FMAP_PREC_FP32;
   P.tc_bwd = opt.precision == FMAP_PREC_BF16;
-  if (!P.tc) {
-    for (auto& sd : P.shapes) {
-      sd.part_off = cur;
-      cur = align_up(cur + (int64_t)sd.nchunk * sd.k * sd.d, kAlignFloats);
-    }
-  } else {
+  {
     // (shape, feature group) units, grouped by spectral-size class (k padded to 32, 64,
     // 128, 256); every class is one launch with its own pipeline depth, and within a
     // class a stream-K split of the vertex ranges into kTcCtas ranges of equal cost
@@ -215,6 +205,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
           // two stages of (F + its remainder: 32 KB per group) + Phi, Ph, Pl must fit
           const int pb = (npad + 31) / 32 * 4096 + npad * 256;
           fg_cap = std::max(1, std::min(std::min(fg_cap, 2), ((kSmemBudget - 1536) / 2 - pb - 128) / 32768));
+          fg_cap = std::max(1, std::min(fg_cap, 256 / npad));   // two accumulators in 512 TMEM columns
         }
         const int groups = (mt + fg_cap - 1) / fg_cap;
         const int fg_s = (mt + groups - 1) / groups;
@@ -297,7 +288,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       L.f_stage = std::max<uint32_t>(fmax, 16384u);
       L.p_stage = (std::max<uint32_t>(pmax, 8192u) + 1023u) / 1024u * 1024u;
       uint32_t cols = 32;
-      while (cols < tmax) cols <<= 1;
+      while (cols < (P.tc32 ? 2 * tmax : tmax)) cols <<= 1;   // FP32: two accumulators
       L.tmem_cols = cols;
       const int fixed = 1024 + 512;
       const int per_stage = (int)(L.f_stage + L.p_stage) + (int)stage_v * 4;
@@ -431,15 +422,6 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   // ---- projection work lists
   for (int s = 0; s < n_shapes; ++s) {
     const ShapeDev& sd = P.shapes[s];
-    for (int c = 0; c < (P.tc ? 0 : sd.nchunk); ++c)
-      for (int kk0 = 0; kk0 < sd.k; kk0 += kTile)
-        for (int f0 = 0; f0 < sd.d; f0 += kTile) {
-          ProjTile t;
-          t.shape = s; t.chunk = c; t.kk0 = kk0; t.f0 = f0;
-          t.v0 = (int64_t)c * kChunkV;
-          t.v1 = std::min<int64_t>(sd.n, t.v0 + kChunkV);
-          P.ptiles.push_back(t);
-        }
     if (sd.dfeat && !P.tc_bwd)
       for (int64_t v0 = 0; v0 < sd.n; v0 += kTile)
         for (int f0 = 0; f0 < sd.d; f0 += kTile) {
@@ -505,7 +487,6 @@ struct fmap_batch {
   Timing timing;
   void* dev_mem = nullptr;
   BatchDev dev{};
-  const ProjTile* d_ptiles = nullptr;
   const BwdTile* d_btiles = nullptr;
   const int2* d_systems = nullptr;
   const CUtensorMap* d_fmaps = nullptr;
@@ -634,17 +615,16 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_sh = 0;
   const int64_t o_pr = o_sh + bytes_of(P.shapes.size(), sizeof(ShapeDev));
   const int64_t o_sl = o_pr + bytes_of(P.pairs.size(), sizeof(PairDev));
-  const int64_t o_pt = o_sl + bytes_of(P.slot_list.size(), sizeof(int64_t));
-  const int64_t o_bt = o_pt + bytes_of(P.ptiles.size(), sizeof(ProjTile));
+  const int64_t o_bt = o_sl + bytes_of(P.slot_list.size(), sizeof(int64_t));
   const int64_t o_sy = o_bt + bytes_of(P.btiles.size(), sizeof(BwdTile));
   const int64_t o_tm = o_sy + bytes_of(P.systems.size(), sizeof(int2));
-  const int64_t o_ti = o_tm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_ti = o_tm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
   const int64_t o_to = o_ti + bytes_of(P.tc_items.size(), sizeof(TcItem));
   const int64_t o_tg = o_to + bytes_of(P.tc_cta_first.size(), sizeof(int32_t));
   const int64_t o_fp = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
-  const int64_t o_mm = o_fp + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
-  const int64_t o_dm = o_mm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
-  const int64_t o_bi = o_dm + bytes_of(P.tc ? P.shapes.size() : 0, sizeof(CUtensorMap));
+  const int64_t o_mm = o_fp + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
+  const int64_t o_dm = o_mm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
+  const int64_t o_bi = o_dm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
   const int64_t o_bg = o_bo + bytes_of(P.bw_cta_first.size(), sizeof(int32_t));
   const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
@@ -656,10 +636,9 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   put(o_sh, P.shapes.data(), P.shapes.size() * sizeof(ShapeDev));
   put(o_pr, P.pairs.data(), P.pairs.size() * sizeof(PairDev));
   put(o_sl, P.slot_list.data(), P.slot_list.size() * sizeof(int64_t));
-  put(o_pt, P.ptiles.data(), P.ptiles.size() * sizeof(ProjTile));
   put(o_bt, P.btiles.data(), P.btiles.size() * sizeof(BwdTile));
   put(o_sy, P.systems.data(), P.systems.size() * sizeof(int2));
-  if (P.tc && n_shapes > 0) {
+  if (n_shapes > 0) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) { cudaFree(b->dev_mem); delete b; return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
     for (int s = 0; s < n_shapes; ++s) {
@@ -754,7 +733,6 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->dev.feat_bf16 = ctx->opt.precision == FMAP_PREC_BF16 ? 1 : 0;
   b->dev.ir_steps = ctx->opt.ir_steps;
   b->dev.ir_steps_adj = ctx->opt.adjoint_ir_steps;
-  b->d_ptiles = reinterpret_cast<const ProjTile*>(base + o_pt);
   b->d_btiles = reinterpret_cast<const BwdTile*>(base + o_bt);
   b->d_systems = reinterpret_cast<const int2*>(base + o_sy);
   b->d_fmaps = reinterpret_cast<const CUtensorMap*>(base + o_tm);
@@ -839,42 +817,30 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
   cudaError_t e = cudaMemsetAsync(ws, 0, 256, st);   // control words
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(control)");
   const Plan& P = b->plan;
-  if (P.tc) {
-    for (const TcLaunch& L : P.tc_launches) {
-      TcProjParams tp{};
-      tp.shapes = b->dev.shapes;
-      tp.fmaps = b->d_fmaps;
-      tp.phimaps = b->d_phimaps_fwd;
-      tp.massmaps = b->d_massmaps;
-      tp.items = b->d_tc_items;
-      tp.cta_first = b->d_tc_cta_first + L.cta_off;
-      tp.stages = L.stages;
-      tp.f_stage_bytes = L.f_stage;
-      tp.p_stage_bytes = L.p_stage;
-      tp.tmem_cols = L.tmem_cols;
-      tp.ws = w;
-      tp.err = static_cast<int*>(ws);
-      {
-        TimedScope ts(b, FMAP_KIND_PROJECT, st);
-        e = P.tc32 ? launch_project_tc32(tp, kTcCtas, L.smem, st) : launch_project_tc(tp, kTcCtas, L.smem, st);
-      }
-      if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
-    }
-    {
-      TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
-      e = launch_project_tc_reduce(b->dev.shapes, b->d_tc_items, b->d_tc_groups, (int)P.tc_groups.size(),
-                                   P.tc_max_group_elems, a_out, w, st);
-    }
-  } else {
+  for (const TcLaunch& L : P.tc_launches) {
+    TcProjParams tp{};
+    tp.shapes = b->dev.shapes;
+    tp.fmaps = b->d_fmaps;
+    tp.phimaps = b->d_phimaps_fwd;
+    tp.massmaps = b->d_massmaps;
+    tp.items = b->d_tc_items;
+    tp.cta_first = b->d_tc_cta_first + L.cta_off;
+    tp.stages = L.stages;
+    tp.f_stage_bytes = L.f_stage;
+    tp.p_stage_bytes = L.p_stage;
+    tp.tmem_cols = L.tmem_cols;
+    tp.ws = w;
+    tp.err = static_cast<int*>(ws);
     {
       TimedScope ts(b, FMAP_KIND_PROJECT, st);
-      e = launch_project_simt(b->dev, b->d_ptiles, (int)P.ptiles.size(), w, st);
+      e = P.tc32 ? launch_project_tc32(tp, kTcCtas, L.smem, st) : launch_project_tc(tp, kTcCtas, L.smem, st);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "project");
-    {
-      TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
-      e = launch_project_reduce(b->dev, (int)P.max_kd, a_out, w, st);
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
+  }
+  {
+    TimedScope ts(b, FMAP_KIND_PROJECT_REDUCE, st);
+    e = launch_project_tc_reduce(b->dev.shapes, b->d_tc_items, b->d_tc_groups, (int)P.tc_groups.size(),
+                                 P.tc_max_group_elems, a_out, w, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "project_reduce");
   return FMAP_OK;

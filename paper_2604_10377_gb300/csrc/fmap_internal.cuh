@@ -29,11 +29,8 @@ struct ShapeDev {
   int64_t ld_feat;
   void* dfeat;
   int64_t a_off;       // float offset of A_s in the flat A buffer
-  int64_t part_off;    // float offset of this shape's split-K partials in the workspace
-  int32_t nchunk;      // number of vertex chunks (split-K slices)
   int32_t slot_beg;    // [slot_beg, slot_end): entries of slot_list holding dA contributions
   int32_t slot_end;
-  int32_t pad_;
 };
 
 // Device copy of a pair descriptor plus workspace offsets.
@@ -64,16 +61,6 @@ struct PairDev {
   int64_t sx_off;      // float offset (workspace) of this pair's dA_x contribution (k x d)
   int64_t sy_off;      // float offset (workspace) of this pair's dA_y contribution (k x d)
   int64_t fac_off;     // float offset of saved factors (k packed triangles), or -1
-};
-
-// Work item of the projection kernels: a vertex range of one shape and an
-// output tile of A (rows kk0.., cols f0..).
-struct ProjTile {
-  int32_t shape;
-  int32_t chunk;
-  int32_t kk0;
-  int32_t f0;
-  int64_t v0, v1;
 };
 
 // Work item of the backward projection: a vertex tile and a feature tile of dF.
@@ -169,10 +156,6 @@ cudaError_t launch_project_tc_reduce(const ShapeDev* shapes, const TcItem* items
                                      cudaStream_t st);
 
 // ---- launchers (each enqueues on `st`; return cudaError_t of the launch) ----
-cudaError_t launch_project_simt(const BatchDev& b, const ProjTile* tiles, int ntiles, float* ws,
-                                cudaStream_t st);
-cudaError_t launch_project_reduce(const BatchDev& b, int max_kd, float* a_out, const float* ws,
-                                  cudaStream_t st);
 // with_r = false computes G only (the adjoint solves never read R)
 cudaError_t launch_gram(const BatchDev& b, int max_k, const float* a, float* ws, cudaStream_t st,
                         bool with_r = true);

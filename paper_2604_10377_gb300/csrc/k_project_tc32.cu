@@ -12,7 +12,8 @@
 //
 // Same schedule as the BF16 kernel (one persistent CTA per SM over a stream-K range of
 // (shape, feature group) segments, partials reduced in a fixed order by a second
-// kernel), with 32-vertex stages:
+// kernel), with 32-vertex stages and two TMEM accumulators (segments are short, so the
+// epilogue of one overlaps the MMAs of the next):
 //   warp 0      TMA-loads the F tile (FP32, MN-major: 32-feature boxes, 128-byte
 //               swizzle), the Phi tile (FP32, 32-column boxes) and the 32 masses;
 //   warps 2-9   form P = M * Phi and write Ph, Pl as K-major 128-byte-swizzled B tiles
@@ -74,9 +75,9 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
   uint64_t* full_f = bars;
   uint64_t* full_p = bars + S;
   uint64_t* empty = bars + 2 * S;
-  uint64_t* acc_full = bars + 3 * S;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint64_t* acc_full = bars + 3 * S;    // [2]: accumulators double-buffered in TMEM
+  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -86,8 +87,10 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
       tc::mbar_init(&full_p[s], kConvWarps);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, kConvWarps);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], kConvWarps);
+    }
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -140,10 +143,13 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t stage = 0, phase = 0, acc_phase = 0;
+      uint32_t stage = 0, phase = 0;
+      uint32_t acc_phase[2] = {0, 0};
+      int buf = 0;
+      const uint32_t half_cols = P.tmem_cols / 2;
       for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
         const TcItem item = P.items[it];
-        if (!tc::mbar_wait(acc_empty, acc_phase ^ 1, abort_flag)) break;
+        if (!tc::mbar_wait(&acc_empty[buf], acc_phase[buf] ^ 1, abort_flag)) break;
         tc::tc_fence_after();
         const uint32_t idesc = idesc_tf32(128, (uint32_t)item.npad);
         const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
             for (int m = 0; m < item.fg; ++m) {
               const uint64_t af = tc::smem_desc(f_base + m * kGroupBytes + kk * 32, 16, 1024, tc::kLayoutSW128);
               const uint64_t al = tc::smem_desc(fl_base + m * kGroupBytes + kk * 32, 16, 1024, tc::kLayoutSW128);
-              const uint32_t d = tmem_base + (uint32_t)(m * item.npad);
+              const uint32_t d = tmem_base + (uint32_t)buf * half_cols + (uint32_t)(m * item.npad);
               mma_tf32(d, af, bh, idesc, (st | kk) != 0 ? 1u : 0u);
               mma_tf32(d, af, bl, idesc, 1u);
               mma_tf32(d, al, bh, idesc, 1u);
@@ -174,15 +180,19 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
           if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
         }
         if (!ok) break;
-        tc::mma_commit(acc_full);
-        acc_phase ^= 1;
+        tc::mma_commit(&acc_full[buf]);
+        acc_phase[buf] ^= 1;
+        buf ^= 1;
       }
     }
   } else {
     // ------------------------------------------------------------ converters + epilogue
     const int ct = threadIdx.x - 64;   // 0 .. 255
     const int cw = warp - 2;
-    uint32_t stage = 0, phase = 0, acc_phase = 0;
+    uint32_t stage = 0, phase = 0;
+    uint32_t acc_phase[2] = {0, 0};
+    int buf = 0;
+    const uint32_t half_cols = P.tmem_cols / 2;
     for (int it = P.cta_first[blockIdx.x]; it < P.cta_first[blockIdx.x + 1]; ++it) {
       const TcItem item = P.items[it];
       const ShapeDev s = P.shapes[item.shape];
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
         if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
       }
       // epilogue: accumulators -> this item's partial A (nk x stride, row-major)
-      if (!tc::mbar_wait(acc_full, acc_phase, abort_flag)) goto conv_done;
+      if (!tc::mbar_wait(&acc_full[buf], acc_phase[buf], abort_flag)) goto conv_done;
       tc::tc_fence_after();
       {
         const int quarter = warp & 3, half = cw >> 2;
@@ -267,7 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
           const bool fok = item.f0 + fl < s.d;
           for (int ch = half; ch < item.npad / 16; ch += 2) {
             float v[16];
-            tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(m * item.npad + ch * 16), v);
+            tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * half_cols +
+                              (uint32_t)(m * item.npad + ch * 16), v);
             if (fok) {
 #pragma unroll
               for (int t = 0; t < 16; ++t) {
@@ -280,8 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
       }
       tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty);
-      acc_phase ^= 1;
+      if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+      acc_phase[buf] ^= 1;
+      buf ^= 1;
     }
   conv_done:;
   }
