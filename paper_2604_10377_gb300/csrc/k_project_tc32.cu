@@ -208,15 +208,17 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
         const int64_t vbase = item.v0 + (int64_t)st * kStageV;
         // F: read this thread's chunks (feature row f, vertices 4c .. 4c+3) out of the
         // vertex-row TMA boxes, then (after every converter has read) write Fh in place and
-        // Fl beside it as K-major 128-byte-swizzled A tiles (row f, 32 vertices)
+        // Fl beside it as K-major 128-byte-swizzled A tiles (row f, 32 vertices). The 32
+        // lanes of a warp take 32 consecutive features of one box and one vertex quad, so
+        // each read touches 32 distinct banks.
         float fx[kMaxFg * 4][4];
         const int nfc = item.fg * 128 * 8;
 #pragma unroll
         for (int r = 0; r < kMaxFg * 4; ++r) {
           const int q = ct + 32 * kConvWarps * r;
           if (q < nfc) {
-            const int f = q >> 3, c = q & 7;
-            const int box = f >> 5, ff = f & 31;
+            const int c = (q >> 5) & 7, box = q >> 8;
+            const int ff = q & 31, f = 32 * box + ff;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const int v = 4 * c + j;
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
         for (int r = 0; r < kMaxFg * 4; ++r) {
           const int q = ct + 32 * kConvWarps * r;
           if (q < nfc) {
-            const int f = q >> 3, c = q & 7;
+            const int c = (q >> 5) & 7, f = 32 * (q >> 8) + (q & 31);
             float h[4], l[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -242,9 +244,11 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
             *reinterpret_cast<float4*>(ftile + (size_t)item.fg * kGroupBytes + off) = make_float4(l[0], l[1], l[2], l[3]);
           }
         }
-        // Ph, Pl: 16-byte chunk (row n, vertices 4c .. 4c+3) of the K-major swizzled B tiles
-        for (int q = ct; q < item.npad * 8; q += 32 * kConvWarps) {
-          const int n = q >> 3, c = q & 7;
+        // Ph, Pl: 16-byte chunk (row n, vertices 4c .. 4c+3) of the K-major swizzled B tiles;
+        // a warp takes 32 consecutive basis functions of one box and one vertex quad
+        for (int q = ct; q < kb * 32 * 8; q += 32 * kConvWarps) {
+          const int n = 32 * (q >> 8) + (q & 31), c = (q >> 5) & 7;
+          if (n >= item.npad) continue;
           float hv[4], lv[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
