@@ -17,10 +17,10 @@ LIB = os.path.join(HERE, "libfmap.so")
 
 SOURCES = [
     "fmap_api.cu",
-    "k_project_bwd_simt.cu",
     "k_project_tc.cu",
     "k_project_tc32.cu",
     "k_project_bwd_tc.cu",
+    "k_project_bwd_tc32.cu",
     "k_gram.cu",
     "k_solve.cu",
     "k_chol.cu",

@@ -24,7 +24,6 @@ int32_t cuda_fail(cudaError_t e, const char* where) {
 }
 
 constexpr int64_t kAlignFloats = 64;   // 256-byte alignment of workspace regions
-constexpr int kTile = 64;
 constexpr int64_t kTcChunkV = 8192;    // vertices per work item of the tensor-core backward projection
 constexpr int kTcCtas = 152;           // persistent CTAs of the projection (one per GB300 SM)
 constexpr int64_t kStageV = 64;        // vertices per projection pipeline stage
@@ -76,7 +75,6 @@ struct Plan {
   std::vector<ShapeDev> shapes;
   std::vector<PairDev> pairs;
   std::vector<int64_t> a_off, c_off, slot_list;
-  std::vector<BwdTile> btiles;
   std::vector<int2> systems;
   std::vector<SolveGroup> groups;
   int max_k = 0, max_d = 0;
@@ -85,7 +83,8 @@ struct Plan {
   int64_t loss_part_off = 0;
   // tensor-core projection
   bool tc32 = false;      // FP32 features: three-pass TF32 kernel
-  bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features)
+  bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features: 2-CTA clusters)
+  bool tc_bwd32 = false;  // backward projection on the tensor cores (FP32 features: three TF32 passes)
   std::vector<TcItem> tc_items;
   std::vector<int32_t> tc_cta_first;   // kTcCtas + 1 entries per launch
   std::vector<TcLaunch> tc_launches;
@@ -178,6 +177,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   int64_t cur = kAlignFloats;
   P.tc32 = opt.precision == FMAP_PREC_FP32;
   P.tc_bwd = opt.precision == FMAP_PREC_BF16;
+  P.tc_bwd32 = opt.precision == FMAP_PREC_FP32;
   {
     // (shape, feature group) units, grouped by spectral-size class (k padded to 32, 64,
     // 128, 256); every class is one launch with its own pipeline depth, and within a
@@ -396,6 +396,67 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     if (!P.bw_items.empty() && P.bw_stages < 2) return FMAP_ERR_UNSUPPORTED;
     P.bw_smem = fixed + out_staging + (int)P.bw_b_bytes + P.bw_stages * 16384;
   }
+  if (P.tc_bwd32) {
+    // FP32 features: one CTA per SM over (shape, feature group, vertex chunk) items; a
+    // group is 64 features (32 when the basis needs more than 6 blocks of 32, so that the
+    // TF32 head and remainder images of dA^T plus two Phi stages fit), with its two
+    // images contiguous in the workspace. Items sorted by cost, dealt round-robin.
+    int kb_max = 1;
+    for (int s = 0; s < n_shapes; ++s)
+      if (P.shapes[s].dfeat) kb_max = std::max(kb_max, (P.shapes[s].k + 31) / 32);
+    const int nf_g = kb_max <= 6 ? 64 : 32;
+    int64_t bw_work = 0;
+    for (int s = 0; s < n_shapes; ++s)
+      if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + nf_g - 1) / nf_g);
+    const int64_t bw_chunk = opt.bwd_chunk_v ? (int64_t)opt.bwd_chunk_v
+                                             : std::min<int64_t>(kTcChunkV, std::max<int64_t>(
+                                                   1024, (bw_work / (4 * kTcCtas) + 127) / 128 * 128));
+    std::vector<TcBwdItem> items;
+    for (int s = 0; s < n_shapes; ++s) {
+      const ShapeDev& sd = P.shapes[s];
+      if (!sd.dfeat) continue;
+      const int kb = (sd.k + 31) / 32;
+      for (int f0 = 0; f0 < sd.d; f0 += nf_g) {
+        TcBwdGroup bg{};
+        bg.shape = s; bg.f0 = f0; bg.nf = std::min(nf_g, sd.d - f0); bg.kb = kb;
+        bg.img_off = cur;
+        cur = align_up(cur + 2 * (int64_t)kb * bg.nf * 32, kAlignFloats);
+        P.bw_groups.push_back(bg);
+        P.bw_max_img = std::max(P.bw_max_img, kb * bg.nf * 32);
+        P.bw_b_bytes = std::max<uint32_t>(P.bw_b_bytes, (uint32_t)(kb * bg.nf * 128));
+        for (int64_t v0 = 0; v0 < sd.n; v0 += bw_chunk) {
+          TcBwdItem it{};
+          it.shape = s; it.f0 = f0; it.nf = bg.nf; it.kb = kb;
+          it.v0 = v0; it.v1 = std::min<int64_t>(sd.n, v0 + bw_chunk);
+          it.img_off = bg.img_off;
+          items.push_back(it);
+        }
+      }
+    }
+    if (!items.empty()) {
+      std::vector<int32_t> order(items.size());
+      for (size_t i = 0; i < items.size(); ++i) order[i] = (int32_t)i;
+      auto bcost = [&](const TcBwdItem& it) {
+        return (double)(it.v1 - it.v0) * (4.0 * P.shapes[it.shape].k + 4.0 * it.nf);
+      };
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const double cx = bcost(items[a]), cy = bcost(items[b]);
+        if (cx != cy) return cx > cy;
+        return a < b;
+      });
+      P.bw_cta_first.assign(kTcCtas + 1, 0);
+      for (int c = 0; c < kTcCtas; ++c) {
+        P.bw_cta_first[c] = (int32_t)P.bw_items.size();
+        for (size_t j = c; j < order.size(); j += kTcCtas) P.bw_items.push_back(items[order[j]]);
+      }
+      P.bw_cta_first[kTcCtas] = (int32_t)P.bw_items.size();
+    }
+    const int fixed = 1024 + 512;
+    const int out_staging = 8 * 4096;   // FP32 dF staging of the eight epilogue warps
+    P.bw_stages = std::min(6, (kSmemBudget - fixed - out_staging - 2 * (int)P.bw_b_bytes) / 32768);
+    if (!P.bw_items.empty() && P.bw_stages < 2) return FMAP_ERR_UNSUPPORTED;
+    P.bw_smem = fixed + out_staging + 2 * (int)P.bw_b_bytes + P.bw_stages * 32768;
+  }
   const int64_t ws_bwd = std::max(cur, ws_fwd);
 
   // ---- saved factors
@@ -417,18 +478,6 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       if (pd.y == s) P.slot_list.push_back(pd.sy_off);
     }
     P.shapes[s].slot_end = (int32_t)P.slot_list.size();
-  }
-
-  // ---- projection work lists
-  for (int s = 0; s < n_shapes; ++s) {
-    const ShapeDev& sd = P.shapes[s];
-    if (sd.dfeat && !P.tc_bwd)
-      for (int64_t v0 = 0; v0 < sd.n; v0 += kTile)
-        for (int f0 = 0; f0 < sd.d; f0 += kTile) {
-          BwdTile t;
-          t.shape = s; t.f0 = f0; t.v0 = v0;
-          P.btiles.push_back(t);
-        }
   }
 
   // ---- row systems, grouped by block size, largest k first
@@ -487,7 +536,6 @@ struct fmap_batch {
   Timing timing;
   void* dev_mem = nullptr;
   BatchDev dev{};
-  const BwdTile* d_btiles = nullptr;
   const int2* d_systems = nullptr;
   const CUtensorMap* d_fmaps = nullptr;
   const TcItem* d_tc_items = nullptr;
@@ -496,6 +544,7 @@ struct fmap_batch {
   const CUtensorMap* d_phimaps_fwd = nullptr;
   const CUtensorMap* d_massmaps = nullptr;
   const CUtensorMap* d_dfmaps = nullptr;
+  const CUtensorMap* d_phimaps_bwd = nullptr;
   const TcBwdItem* d_bw_items = nullptr;
   const int32_t* d_bw_cta_first = nullptr;
   const TcBwdGroup* d_bw_groups = nullptr;
@@ -615,8 +664,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_sh = 0;
   const int64_t o_pr = o_sh + bytes_of(P.shapes.size(), sizeof(ShapeDev));
   const int64_t o_sl = o_pr + bytes_of(P.pairs.size(), sizeof(PairDev));
-  const int64_t o_bt = o_sl + bytes_of(P.slot_list.size(), sizeof(int64_t));
-  const int64_t o_sy = o_bt + bytes_of(P.btiles.size(), sizeof(BwdTile));
+  const int64_t o_sy = o_sl + bytes_of(P.slot_list.size(), sizeof(int64_t));
   const int64_t o_tm = o_sy + bytes_of(P.systems.size(), sizeof(int2));
   const int64_t o_ti = o_tm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
   const int64_t o_to = o_ti + bytes_of(P.tc_items.size(), sizeof(TcItem));
@@ -624,7 +672,8 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_fp = o_tg + bytes_of(P.tc_groups.size(), sizeof(TcRedGroup));
   const int64_t o_mm = o_fp + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
   const int64_t o_dm = o_mm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
-  const int64_t o_bi = o_dm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
+  const int64_t o_pb = o_dm + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
+  const int64_t o_bi = o_pb + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
   const int64_t o_bg = o_bo + bytes_of(P.bw_cta_first.size(), sizeof(int32_t));
   const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
@@ -636,7 +685,6 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   put(o_sh, P.shapes.data(), P.shapes.size() * sizeof(ShapeDev));
   put(o_pr, P.pairs.data(), P.pairs.size() * sizeof(PairDev));
   put(o_sl, P.slot_list.data(), P.slot_list.size() * sizeof(int64_t));
-  put(o_bt, P.btiles.data(), P.btiles.size() * sizeof(BwdTile));
   put(o_sy, P.systems.data(), P.systems.size() * sizeof(int2));
   if (n_shapes > 0) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
@@ -691,12 +739,26 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
         return FMAP_ERR_CUDA;
       }
       put(o_mm + s * (int64_t)sizeof(CUtensorMap), &mm, sizeof(mm));
-      // BF16 dF: box 16 features x 32 vertices, stored by the backward projection
+      // FP32 basis, box 32 basis x 64 vertices: the halves of the backward projection's
+      // 128-vertex tiles
+      CUtensorMap pb;
+      cuuint32_t bbox[2] = {32, 64};
+      r = encode(&pb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sd.phi), pdim, pstride, bbox, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        cudaFree(b->dev_mem); delete b;
+        std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "cuTensorMapEncodeTiled(phi bwd) failed (%d)", (int)r);
+        return FMAP_ERR_CUDA;
+      }
+      put(o_pb + s * (int64_t)sizeof(CUtensorMap), &pb, sizeof(pb));
+      // dF (BF16 or FP32): box 16 features x 32 vertices, stored by the backward projection
       CUtensorMap dm;
       std::memset(&dm, 0, sizeof(dm));
-      if (sd.dfeat && P.tc_bwd) {
+      if (sd.dfeat && (P.tc_bwd || P.tc_bwd32)) {
         cuuint32_t dbox[2] = {16, 32};
-        r = encode(&dm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sd.dfeat, gdim, gstride, dbox, estr,
+        r = encode(&dm, P.tc_bwd32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sd.dfeat,
+                   gdim, gstride, dbox, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -711,7 +773,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
     put(o_bo, P.bw_cta_first.data(), P.bw_cta_first.size() * sizeof(int32_t));
     put(o_bg, P.bw_groups.data(), P.bw_groups.size() * sizeof(TcBwdGroup));
     if (!P.bw_items.empty()) {
-      e = project_bwd_tc_set_smem(P.bw_smem);
+      e = P.tc_bwd32 ? project_bwd_tc32_set_smem(P.bw_smem) : project_bwd_tc_set_smem(P.bw_smem);
       if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project bwd)"); }
     }
     put(o_ti, P.tc_items.data(), P.tc_items.size() * sizeof(TcItem));
@@ -733,7 +795,6 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->dev.feat_bf16 = ctx->opt.precision == FMAP_PREC_BF16 ? 1 : 0;
   b->dev.ir_steps = ctx->opt.ir_steps;
   b->dev.ir_steps_adj = ctx->opt.adjoint_ir_steps;
-  b->d_btiles = reinterpret_cast<const BwdTile*>(base + o_bt);
   b->d_systems = reinterpret_cast<const int2*>(base + o_sy);
   b->d_fmaps = reinterpret_cast<const CUtensorMap*>(base + o_tm);
   b->d_tc_items = reinterpret_cast<const TcItem*>(base + o_ti);
@@ -742,6 +803,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_phimaps_fwd = reinterpret_cast<const CUtensorMap*>(base + o_fp);
   b->d_massmaps = reinterpret_cast<const CUtensorMap*>(base + o_mm);
   b->d_dfmaps = reinterpret_cast<const CUtensorMap*>(base + o_dm);
+  b->d_phimaps_bwd = reinterpret_cast<const CUtensorMap*>(base + o_pb);
   b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
   b->d_bw_cta_first = reinterpret_cast<const int32_t*>(base + o_bo);
   b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
@@ -920,30 +982,28 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     e = launch_gather_da(b->dev, (int)b->plan.max_kd, da, w, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "gather dA");
-  if (!b->plan.btiles.empty()) {
-    TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
-    e = launch_project_bwd_simt(b->dev, b->d_btiles, (int)b->plan.btiles.size(), da, st);
-  }
-  if (e == cudaSuccess && !b->plan.bw_items.empty()) {
+  if (!b->plan.bw_items.empty()) {
     const Plan& P = b->plan;
     {
       TimedScope ts(b, FMAP_KIND_GATHER, st);
-      e = launch_build_dat_image(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st);
+      e = P.tc_bwd32
+              ? launch_build_dat_image32(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st)
+              : launch_build_dat_image(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "dA image");
     TcBwdParams bp{};
     bp.shapes = b->dev.shapes;
-    bp.phimaps = b->d_phimaps_fwd;
+    bp.phimaps = b->d_phimaps_bwd;
     bp.dfmaps = b->d_dfmaps;
     bp.items = b->d_bw_items;
     bp.cta_first = b->d_bw_cta_first;
     bp.stages = P.bw_stages;
     bp.b_bytes_max = P.bw_b_bytes;
-    bp.tmem_cols = 256;
+    bp.tmem_cols = P.tc_bwd32 ? 128 : 256;   // two accumulators of <= 64 or <= 128 columns
     bp.ws = w;
     bp.err = static_cast<int*>(ws);
     TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
-    e = launch_project_bwd_tc(bp, kTcCtas, P.bw_smem, st);
+    e = P.tc_bwd32 ? launch_project_bwd_tc32(bp, kTcCtas, P.bw_smem, st) : launch_project_bwd_tc(bp, kTcCtas, P.bw_smem, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "project backward");
   return FMAP_OK;

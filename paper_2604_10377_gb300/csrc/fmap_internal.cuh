@@ -63,13 +63,6 @@ struct PairDev {
   int64_t fac_off;     // float offset of saved factors (k packed triangles), or -1
 };
 
-// Work item of the backward projection: a vertex tile and a feature tile of dF.
-struct BwdTile {
-  int32_t shape;
-  int32_t f0;
-  int64_t v0;
-};
-
 struct BatchDev {
   const ShapeDev* shapes;
   const PairDev* pairs;
@@ -131,7 +124,7 @@ struct TcBwdGroup {
 struct TcBwdParams {
   const ShapeDev* shapes;
   const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 64, 128-byte swizzle
-  const CUtensorMap* dfmaps;   // per shape: BF16 dF, box 16 x 32, no swizzle (TMA stores)
+  const CUtensorMap* dfmaps;   // per shape: dF (BF16 or FP32), box 16 x 32, no swizzle (TMA stores)
   const TcBwdItem* items;       // item j of a cluster: [2 j] for CTA rank 0, [2 j + 1] for rank 1
   const int32_t* cta_first;     // cluster c (CTAs 2c, 2c + 1) owns items [cta_first[c], cta_first[c + 1])
   int32_t stages;
@@ -145,6 +138,10 @@ cudaError_t project_bwd_tc_set_smem(int bytes);
 cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* groups, int n_groups, int max_elems,
                                    const float* d_a, float* ws, cudaStream_t st);
 cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st);
+cudaError_t project_bwd_tc32_set_smem(int bytes);
+cudaError_t launch_build_dat_image32(const ShapeDev* shapes, const TcBwdGroup* groups, int n_groups, int max_elems,
+                                     const float* d_a, float* ws, cudaStream_t st);
+cudaError_t launch_project_bwd_tc32(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st);
 
 cudaError_t project_tc_set_smem(int bytes);
 cudaError_t project_tc32_set_smem(int bytes);
@@ -175,8 +172,6 @@ cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* sys
 cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
                                  float* d_mask, float* d_lambda, float* ws, cudaStream_t st);
 cudaError_t launch_gather_da(const BatchDev& b, int max_kd, float* d_a, const float* ws, cudaStream_t st);
-cudaError_t launch_project_bwd_simt(const BatchDev& b, const BwdTile* tiles, int ntiles, const float* d_a,
-                                    cudaStream_t st);
 cudaError_t launch_loss_orth(const BatchDev& b, int max_k, const float* c, const float* c_gt, float* loss,
                              float* d_c, float* ws, float* partial, cudaStream_t st);
 cudaError_t launch_status_clear(int32_t* status, int n, cudaStream_t st);

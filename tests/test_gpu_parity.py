@@ -195,6 +195,19 @@ def test_backward_against_oracle(feat_dtype, use_saved):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= gtol
 
 
+@pytest.mark.parametrize("d,ks", [(16, [4, 8]), (64, [20, 30]), (384, [64, 100]), (256, [200, 230])])
+def test_backward_fp32_feature_groups(d, ks):
+    """FP32 backward projection on the tensor cores (three TF32 passes): feature groups of
+    64 (32 when the basis needs more than six 32-blocks), partial last groups, vertex
+    counts ending inside a tile; gradients within the FP32-mode tolerance."""
+    wl = synth.make_small(15, 2 * len(ks), (260, 3000), ks, d, feat_dtype="fp32")
+    out = _gpu_backward(wl)
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
+
+
 @pytest.mark.parametrize("d", [16, 48, 384, 640])
 def test_backward_bf16_feature_groups(d):
     """BF16 backward projection with feature counts that leave the second group of a
