@@ -356,15 +356,14 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
   }
 
   if (mode == kSolveAdjoint && fac != nullptr) {
-    if (use_gs) {
-      __syncthreads();   // barrier initialised
-      if (tid == 0) {
-        tc::mbar_arrive_expect_tx(&s_bar, gs_bytes);
-        tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
-      }
+    // the saved factor (packed rows and inverse blocks) and, for refinement, G: bulk copies
+    __syncthreads();   // barrier initialised
+    if (tid == 0) {
+      tc::mbar_arrive_expect_tx(&s_bar, (uint32_t)fsz * 4u + gs_bytes);
+      tc::bulk_g2s(S, fac, (uint32_t)fsz * 4u, &s_bar);
+      if (use_gs) tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
     }
-    for (int e = tid; e < fsz / 4; e += NT) reinterpret_cast<float4*>(S)[e] = reinterpret_cast<const float4*>(fac)[e];
-    if (use_gs && !tc::mbar_wait(&s_bar, 0, &s_abort)) {
+    if (!tc::mbar_wait(&s_bar, 0, &s_abort)) {
       if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
       const uint64_t t0 = tc::globaltimer();
       while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}

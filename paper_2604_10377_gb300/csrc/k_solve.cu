@@ -22,10 +22,10 @@ constexpr int kStage = 16;
 
 // W = Gamma^T C + C^T Gamma (k x k), and the mask gradient dD = -lambda Gamma o C.
 __global__ void __launch_bounds__(256) adjoint_w_kernel(BatchDev b, const float* c_flat, float* d_mask, float* ws) {
-  __shared__ float sG[kStage][kTile + 4];   // Gamma[m][a-tile]
-  __shared__ float sC[kStage][kTile + 4];   // C[m][a-tile]
-  __shared__ float sGb[kStage][kTile + 4];  // Gamma[m][b-tile]
-  __shared__ float sCb[kStage][kTile + 4];  // C[m][b-tile]
+  __shared__ __align__(16) float sG[kStage][kTile + 4];   // Gamma[m][a-tile]
+  __shared__ __align__(16) float sC[kStage][kTile + 4];   // C[m][a-tile]
+  __shared__ __align__(16) float sGb[kStage][kTile + 4];  // Gamma[m][b-tile]
+  __shared__ __align__(16) float sCb[kStage][kTile + 4];  // C[m][b-tile]
   const PairDev pd = b.pairs[blockIdx.z];
   const int k = pd.k;
   const int nt = (k + kTile - 1) / kTile;
@@ -47,13 +47,16 @@ __global__ void __launch_bounds__(256) adjoint_w_kernel(BatchDev b, const float*
     __syncthreads();
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
+      const float4 g4 = *reinterpret_cast<const float4*>(&sG[mm][ty * 4]);
+      const float4 c4 = *reinterpret_cast<const float4*>(&sC[mm][ty * 4]);
+      const float4 gb4 = *reinterpret_cast<const float4*>(&sGb[mm][tx * 4]);
+      const float4 cb4 = *reinterpret_cast<const float4*>(&sCb[mm][tx * 4]);
+      const float ga[4] = {g4.x, g4.y, g4.z, g4.w}, ca[4] = {c4.x, c4.y, c4.z, c4.w};
+      const float gb[4] = {gb4.x, gb4.y, gb4.z, gb4.w}, cb[4] = {cb4.x, cb4.y, cb4.z, cb4.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float ga = sG[mm][ty * 4 + i], ca = sC[mm][ty * 4 + i];
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          acc[i][j] = fmaf(ga, sCb[mm][tx * 4 + j], fmaf(ca, sGb[mm][tx * 4 + j], acc[i][j]));
-      }
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ga[i], cb[j], fmaf(ca[i], gb[j], acc[i][j]));
     }
     __syncthreads();
   }
@@ -101,10 +104,12 @@ __global__ void __launch_bounds__(256) adjoint_dlambda_kernel(BatchDev b, const 
 //   which 0: dA_x = Gamma^T A_y - W A_x   (into sx_off)
 //   which 1: dA_y = Gamma A_x             (into sy_off)
 __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float* a_flat, float* ws) {
-  __shared__ float sX[kTile][kStage + 1];   // left operand [a][m]
-  __shared__ float sY[kStage][kTile + 4];   // right operand [m][f]
-  __shared__ float sX2[kTile][kStage + 1];
-  __shared__ float sY2[kStage][kTile + 4];
+  // both operands stored m-major in shared memory, so that a thread's 4 rows and 4
+  // columns of one step are two float4 reads
+  __shared__ __align__(16) float sX[kStage][kTile + 4];    // left operand [m][a]
+  __shared__ __align__(16) float sY[kStage][kTile + 4];    // right operand [m][f]
+  __shared__ __align__(16) float sX2[kStage][kTile + 4];
+  __shared__ __align__(16) float sY2[kStage][kTile + 4];
   const PairDev pd = b.pairs[blockIdx.z];
   const int k = pd.k, d = pd.d;
   const int ntf = (d + kTile - 1) / kTile, nta = (k + kTile - 1) / kTile;
@@ -122,16 +127,16 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
       // Gamma^T[a][m] = Gamma[m][a]: consecutive threads take consecutive a (coalesced)
       const int aa = e % kTile, mm = e / kTile;
       const int a = a0 + aa, m = m0 + mm;
-      if (which == 0) sX[aa][mm] = (a < k && m < k) ? gam[(int64_t)m * k + a] : 0.f;
+      if (which == 0) sX[mm][aa] = (a < k && m < k) ? gam[(int64_t)m * k + a] : 0.f;
     }
     for (int e = tid; e < kTile * kStage; e += 256) {
       const int aa = e / kStage, mm = e % kStage;
       const int a = a0 + aa, m = m0 + mm;
       const bool ok = a < k && m < k;
       if (which == 0)
-        sX2[aa][mm] = ok ? -w[(int64_t)a * k + m] : 0.f;     // -W[a][m]
+        sX2[mm][aa] = ok ? -w[(int64_t)a * k + m] : 0.f;     // -W[a][m]
       else
-        sX[aa][mm] = ok ? gam[(int64_t)a * k + m] : 0.f;     // Gamma[a][m]
+        sX[mm][aa] = ok ? gam[(int64_t)a * k + m] : 0.f;     // Gamma[a][m]
     }
     for (int e = tid; e < kStage * kTile; e += 256) {
       const int mm = e / kTile, ff = e % kTile;
@@ -147,22 +152,24 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
     __syncthreads();
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
+      const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
+      const float4 yb = *reinterpret_cast<const float4*>(&sY[mm][tx * 4]);
+      const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float xa = sX[ty * 4 + i][mm];
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa, sY[mm][tx * 4 + j], acc[i][j]);
-      }
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
     }
     if (which == 0) {
 #pragma unroll
       for (int mm = 0; mm < kStage; ++mm) {
+        const float4 xa = *reinterpret_cast<const float4*>(&sX2[mm][ty * 4]);
+        const float4 yb = *reinterpret_cast<const float4*>(&sY2[mm][tx * 4]);
+        const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float xa = sX2[ty * 4 + i][mm];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa, sY2[mm][tx * 4 + j], acc[i][j]);
-        }
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
       }
     }
     __syncthreads();
@@ -198,8 +205,8 @@ __global__ void gather_da_kernel(BatchDev b, float* d_a, const float* ws) {
 
 __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_flat, const float* gt_flat,
                                                       float* ws, float* partial) {
-  __shared__ float sX[kTile][kStage + 1];   // C[a][m]
-  __shared__ float sY[kStage][kTile + 4];   // C^T[m][b] = C[b][m]
+  __shared__ __align__(16) float sX[kStage][kTile + 4];   // C^T[m][a] = C[a][m]
+  __shared__ __align__(16) float sY[kStage][kTile + 4];   // C^T[m][b] = C[b][m]
   __shared__ float red[256];
   const int p = blockIdx.z;
   const PairDev pd = b.pairs[p];
@@ -214,23 +221,21 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
   float acc[4][4] = {};
   for (int m0 = 0; m0 < k; m0 += kStage) {
     for (int q = tid; q < kTile * kStage; q += 256) {
+      // rows of C read in 16-element segments (consecutive threads, consecutive m)
       const int r = q / kStage, mm = q % kStage;
-      sX[r][mm] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
-    }
-    for (int q = tid; q < kStage * kTile; q += 256) {
-      // C^T[m][b] = C[b][m]: consecutive threads take consecutive m (one row segment)
-      const int mm = q % kStage, r = q / kStage;
+      sX[mm][r] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
       sY[mm][r] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
+      const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
+      const float4 yb = *reinterpret_cast<const float4*>(&sY[mm][tx * 4]);
+      const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float xa = sX[ty * 4 + i][mm];
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa, sY[mm][tx * 4 + j], acc[i][j]);
-      }
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -261,8 +266,8 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
 __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float* c_flat, const float* gt_flat,
                                                          float* loss, float* d_c, const float* ws,
                                                          const float* partial) {
-  __shared__ float sX[kTile][kStage + 1];   // E[a][m]
-  __shared__ float sY[kStage][kTile + 4];   // C[m][b]
+  __shared__ __align__(16) float sX[kStage][kTile + 4];   // E^T[m][a] = E[a][m]
+  __shared__ __align__(16) float sY[kStage][kTile + 4];   // C[m][b]
   const int p = blockIdx.z;
   const PairDev pd = b.pairs[p];
   const int k = pd.k;
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
   for (int m0 = 0; m0 < k; m0 += kStage) {
     for (int q = tid; q < kTile * kStage; q += 256) {
       const int r = q / kStage, mm = q % kStage;
-      sX[r][mm] = (a0 + r < k && m0 + mm < k) ? e[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+      sX[mm][r] = (a0 + r < k && m0 + mm < k) ? e[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
     }
     for (int q = tid; q < kStage * kTile; q += 256) {
       const int mm = q / kTile, r = q % kTile;
@@ -292,12 +297,13 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
     __syncthreads();
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
+      const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
+      const float4 yb = *reinterpret_cast<const float4*>(&sY[mm][tx * 4]);
+      const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float xa = sX[ty * 4 + i][mm];
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa, sY[mm][tx * 4 + j], acc[i][j]);
-      }
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(xv[i], yv[jj], acc[i][jj]);
     }
     __syncthreads();
   }
