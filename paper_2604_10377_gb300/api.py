@@ -310,6 +310,82 @@ class FmapBatch:
         return loss, d_c
 
 
+class UploadPipeline:
+    """Host -> device input staging that overlaps the upload of the next step with the
+    compute of the current one.
+
+    The pipeline owns two or more FmapBatch objects of one layout (buffers). `prefetch`
+    enqueues the upload of one step's inputs into the next buffer on a copy stream, after
+    the last step that computed on that buffer has finished; `acquire` makes the current
+    stream wait for the oldest prefetched upload and returns its batch; `release` marks the
+    end of the current stream's work on it. A loop of
+        prefetch(step 0); for each step: acquire, prefetch(next step), compute, release
+    moves every step's inputs from host to device once, and with two buffers the copy of
+    step i+1 runs while step i computes. Buffers are named by index (`batches[j]`);
+    `next_buffer` is the one the next prefetch fills, so that per-buffer extras (targets,
+    labels) can be passed as `extra` pairs (device tensor, host tensor) copied with it.
+    """
+
+    def __init__(self, batches: Sequence[FmapBatch]):
+        if len(batches) < 2:
+            raise ValueError("an upload pipeline needs at least two batches")
+        self.batches = list(batches)
+        self.device = self.batches[0].device
+        self.copy_stream = torch.cuda.Stream(self.device)
+        n = len(self.batches)
+        self._done: List[Optional[torch.cuda.Event]] = [None] * n
+        self._ready: List[Optional[torch.cuda.Event]] = [None] * n
+        self._next = 0
+        self._queued: List[int] = []
+        self._cur: Optional[int] = None
+
+    def prefetch(self, host: dict, extra: Sequence = ()) -> int:
+        """Enqueue the upload of `host` (pinned tensors, as for FmapBatch.upload) into the
+        next buffer; returns the buffer's index."""
+        if len(self._queued) >= len(self.batches):
+            raise RuntimeError("every buffer already holds an upload that was not acquired")
+        j = self._next
+        self._next = (j + 1) % len(self.batches)
+        cs = self.copy_stream
+        if self._done[j] is not None:
+            cs.wait_event(self._done[j])
+        with torch.cuda.stream(cs):
+            self.batches[j].upload(host, non_blocking=True)
+            for dst, src in extra:
+                dst.copy_(src, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(cs)
+        self._ready[j] = ev
+        self._queued.append(j)
+        return j
+
+    @property
+    def next_buffer(self) -> int:
+        return self._next
+
+    def acquire(self) -> int:
+        """Index of the buffer of the oldest prefetched upload; the current stream waits
+        for that upload."""
+        if not self._queued:
+            raise RuntimeError("acquire without a prefetched upload")
+        if self._cur is not None:
+            raise RuntimeError("the previous batch was not released")
+        j = self._queued.pop(0)
+        torch.cuda.current_stream(self.device).wait_event(self._ready[j])
+        self._cur = j
+        return j
+
+    def release(self) -> None:
+        """End of the current stream's work on the acquired batch: the next upload into its
+        buffer starts after this point."""
+        if self._cur is None:
+            raise RuntimeError("release without an acquired batch")
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(self.device))
+        self._done[self._cur] = ev
+        self._cur = None
+
+
 def batch_from_workload(wl, device="cuda:0", with_grad=True, **kw) -> FmapBatch:
     """Allocate a batch for a synth.Workload and upload its inputs."""
     lay = BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)

@@ -30,6 +30,9 @@
 namespace fmap {
 namespace {
 
+// Rounds of 128 columns that cover a row of G in the refinement residual.
+constexpr int kResRounds = (kMaxK + 127) / 128;
+
 // Offset of row a in the packed, skewed lower storage.
 __host__ __device__ __forceinline__ int rowoff(int a) {
   const int q = a >> 3, s = a & 7;
@@ -519,12 +522,16 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
     block_fwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
   }
   block_bwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
-  for (int a = tid; a < kp; a += NT) xs[a] = v[a];
+  float* ycol = pan + 4 * kp;   // past the 16-row inverse blocks (mo holds at most 4 kp floats)
+  for (int a = tid; a < kp; a += NT) {
+    xs[a] = v[a];
+    ycol[a] = 0.f;
+  }
   __syncthreads();
 
   // iterative refinement: x += S^{-1} (rhs - S x). With G in shared memory every thread
-  // forms one row's residual (float4 reads, four partial sums); otherwise each warp
-  // reduces rows of G read from global memory, four rows in flight.
+  // forms one row's residual (float4 reads, four partial sums); otherwise the warps read
+  // the lower triangle of G from global memory, four rows in flight per warp.
   const float* Gres = use_gs ? Gs : G;
   for (int it = 0; it < n_ir; ++it) {
     if (use_gs) {
@@ -552,9 +559,26 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
       __syncthreads();
       continue;
     }
+    // G is symmetric: only its lower triangle is read. Row a's entries c <= a give the row
+    // part of (G x)_a (reduced across the warp into v[a]); each entry c < a also gives
+    // G_ac x_a to (G x)_c, summed per lane over the warp's rows (column c = lane + 32 j in
+    // colacc[j]) and added into ycol warp by warp in a fixed order (reproducible sums).
+    float colacc[4 * kResRounds];
+#pragma unroll
+    for (int j = 0; j < 4 * kResRounds; ++j) colacc[j] = 0.f;
     for (int a0 = warp; a0 < kp; a0 += 4 * NW) {
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int c0 = 0; c0 < k; c0 += 128) {   // 128 columns (four per lane) per round
+      float xa[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int a = a0 + u * NW;
+        xa[u] = a < k ? xs[a] : 0.f;
+      }
+      const int amax = min(a0 + 3 * NW, k - 1);   // the longest row of the group
+#pragma unroll
+      for (int r = 0; r < kResRounds; ++r) {       // 128 columns (four per lane) per round
+        const int c0 = 128 * r;
+        if (c0 > amax) break;
         if (Ghl) {
           float2 g[4][4];
 #pragma unroll
@@ -563,7 +587,7 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int c = c0 + lane + 32 * q;
-              g[u][q] = (a < k && c < k) ? Ghl[(int64_t)a * k + c] : make_float2(0.f, 0.f);
+              g[u][q] = (a < k && c <= a) ? Ghl[(int64_t)a * k + c] : make_float2(0.f, 0.f);
             }
           }
 #pragma unroll
@@ -571,7 +595,11 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
             const int c = c0 + lane + 32 * q;
             const float xv = c < k ? xs[c] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q].y, xv, fmaf(g[u][q].x, xv, sum[u]));
+            for (int u = 0; u < 4; ++u) {
+              sum[u] = fmaf(g[u][q].y, xv, fmaf(g[u][q].x, xv, sum[u]));
+              const float xo = (c < a0 + u * NW) ? xa[u] : 0.f;   // off-diagonal entries only
+              colacc[4 * r + q] = fmaf(g[u][q].y, xo, fmaf(g[u][q].x, xo, colacc[4 * r + q]));
+            }
           }
         } else {
           float g[4][4];
@@ -581,7 +609,7 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int c = c0 + lane + 32 * q;
-              g[u][q] = (a < k && c < k) ? Gres[(int64_t)a * ldg + c] : 0.f;
+              g[u][q] = (a < k && c <= a) ? Gres[(int64_t)a * ldg + c] : 0.f;
             }
           }
 #pragma unroll
@@ -589,7 +617,11 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
             const int c = c0 + lane + 32 * q;
             const float xv = c < k ? xs[c] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) sum[u] = fmaf(g[u][q], xv, sum[u]);
+            for (int u = 0; u < 4; ++u) {
+              sum[u] = fmaf(g[u][q], xv, sum[u]);
+              const float xo = (c < a0 + u * NW) ? xa[u] : 0.f;
+              colacc[4 * r + q] = fmaf(g[u][q], xo, colacc[4 * r + q]);
+            }
           }
         }
       }
@@ -598,14 +630,28 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum[u] += __shfl_xor_sync(0xffffffffu, sum[u], o);
         const int a = a0 + u * NW;
-        if (lane == 0 && a < kp)
-          v[a] = a < k ? rh[a] - fmaf(dg[a], xs[a], sum[u]) : 0.f;
+        if (lane == 0 && a < kp) v[a] = sum[u];
       }
     }
+    for (int w = 0; w < NW; ++w) {
+      if (warp == w) {
+#pragma unroll
+        for (int j = 0; j < 4 * kResRounds; ++j) {
+          const int c = 32 * j + lane;
+          if (c < k) ycol[c] += colacc[j];
+        }
+      }
+      __syncthreads();
+    }
+    for (int a = tid; a < kp; a += NT)
+      v[a] = a < k ? rh[a] - fmaf(dg[a], xs[a], v[a] + ycol[a]) : 0.f;
     __syncthreads();
     block_fwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
     block_bwd<NT>(S, linv, mo, v, Q, tid, lane, warp);
-    for (int a = tid; a < kp; a += NT) xs[a] += v[a];
+    for (int a = tid; a < kp; a += NT) {
+      xs[a] += v[a];
+      ycol[a] = 0.f;
+    }
     __syncthreads();
   }
 

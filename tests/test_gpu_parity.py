@@ -360,3 +360,59 @@ def test_config4_sampled_pairs():
         c = orc.solve(ax, ay, orc.mask_from_evals(sx["evals"], sy["evals"]), pr["lam"])
         assert rel_fro(a_gpu[pr["x"]], ax) <= TOL["bf16"]
         assert rel_fro(c_gpu[p], c) <= TOL["bf16"], (p, ks[p])
+
+
+def test_upload_pipeline_steps_match_serial_steps():
+    """api.UploadPipeline (two input buffers, the next upload on a copy stream) gives every
+    step exactly the results of the same step run serially; each step's inputs differ, so
+    a step that computed on the wrong buffer would show."""
+    from paper_2604_10377_gb300 import api
+    wl = synth.make_small(31, 4, (2000, 20000), [30, 50], 64, feat_dtype="fp32")
+    lay = api.BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], "fp32")
+    pairs = [(p.x, p.y, p.lam) for p in wl.pairs]
+    base = lay.pack_host(wl.shapes)
+    hosts = []
+    for s in range(4):
+        h = dict(base)
+        h["feat"] = (base["feat"] * np.float32(1.0 + 0.25 * s)).astype(np.float32)
+        hosts.append({k: api.host_to_torch(v).pin_memory() for k, v in h.items()})
+
+    def mk():
+        return api.FmapBatch(lay, pairs, device="cuda:0", precision="fp32", with_grad=True)
+
+    def compute(bb):
+        a = bb.project()
+        c = bb.solve(a)
+        dc = torch.ones_like(c)
+        bb.solve_backward(dc, a, c)
+        return c.clone(), bb.dfeat.clone()
+
+    ref = mk()
+    want = []
+    for h in hosts:
+        ref.upload(h)
+        want.append(compute(ref))
+    torch.cuda.synchronize()
+
+    pipe = api.UploadPipeline([mk(), mk()])
+    with pytest.raises(RuntimeError):
+        pipe.acquire()
+    with pytest.raises(RuntimeError):
+        pipe.release()
+    got = []
+    pipe.prefetch(hosts[0])
+    for s in range(len(hosts)):
+        j = pipe.acquire()
+        if s + 1 < len(hosts):
+            pipe.prefetch(hosts[s + 1])
+        got.append(compute(pipe.batches[j]))
+        pipe.release()
+    torch.cuda.synchronize()
+    for (c, df), (c_ref, df_ref) in zip(got, want):
+        assert torch.equal(c, c_ref)
+        assert torch.equal(df, df_ref)
+    assert not torch.equal(want[0][0], want[1][0])
+    pipe.prefetch(hosts[0])
+    pipe.prefetch(hosts[1])
+    with pytest.raises(RuntimeError):
+        pipe.prefetch(hosts[2])
