@@ -37,13 +37,30 @@ struct ShapeDev {
 // Row stride (floats) of the FP32 Gram matrix G in the workspace: k rounded up to a
 // multiple of 4 (every row starts on a 16-byte boundary, for bulk copies into shared
 // memory) with an odd number of 16-byte quads (rows read by consecutive threads as
-// float4 then fall on distinct bank groups). The region holds k rows plus 8 floats of
-// slack past the last row.
+// float4 then fall on distinct bank groups).
 __host__ __device__ __forceinline__ int gram_ld(int k) {
   const int q = (k + 3) >> 2;
   return 4 * (q | 1);
 }
-__host__ __device__ __forceinline__ int64_t gram_floats(int k) { return (int64_t)k * gram_ld(k) + 8; }
+
+// Packed, skewed lower storage of a row system (the row solves' shared-memory layout):
+// row a holds columns 0 .. (a | 7), i.e. up to the end of its 8 x 8 diagonal block, in
+// 8 (a / 8 + 1) + 4 floats, so a row's 8-column segment is two aligned float4 and
+// consecutive rows of a block start on different banks. rowoff(a) is the offset of row
+// a; rowoff(a) is a multiple of 4 for every a.
+__host__ __device__ __forceinline__ int rowoff(int a) {
+  const int q = a >> 3, s = a & 7;
+  return 32 * q * (q + 2) + s * (8 * q + 12);
+}
+
+// The Gram region of a pair: G row-major (k rows of gram_ld(k) floats, then 8 floats of
+// slack), then, from gram_packed_off(k) (a multiple of 32 floats), rows 0 .. k-1 of G
+// in the packed layout above (rowoff(k) floats), which the row solves copy into shared
+// memory with one bulk copy.
+__host__ __device__ __forceinline__ int64_t gram_packed_off(int k) {
+  return ((int64_t)k * gram_ld(k) + 8 + 31) / 32 * 32;
+}
+__host__ __device__ __forceinline__ int64_t gram_floats(int k) { return gram_packed_off(k) + rowoff(k); }
 
 struct PairDev {
   int32_t x, y;

@@ -2,10 +2,10 @@
 //
 // One thread block per row system S_i = G + lambda diag(D_i) (row i of pair p).
 // S_i is padded to kp = k rounded up to 8 (identity in the padding) and kept in
-// shared memory as packed lower rows: row a holds 8 (a/8 + 1) + 4 floats, so a
+// shared memory as packed lower rows (rowoff: row a holds 8 (a/8 + 1) + 4 floats, so a
 // row's 8-column tile segment is two aligned float4 and consecutive rows fall on
-// different banks. Each row's segment is copied from G by 16-byte asynchronous copies
-// (cp.async) spread over the block, then lambda D_i is added to the diagonal. The factorisation is a blocked
+// different banks). The Gram kernel leaves G in that layout too, so one bulk copy
+// loads it; then lambda D_i is added to the diagonal. The factorisation is a blocked
 // right-looking Cholesky in FP32 with 8-column panels and one panel of lookahead:
 //   TRSM     every thread solves one row of panel J below its diagonal block,
 //            x = s L_JJ^-T, as a product with the stored inverse block; one warp
@@ -32,12 +32,6 @@ namespace {
 
 // Rounds of 128 columns that cover a row of G in the refinement residual.
 constexpr int kResRounds = (kMaxK + 127) / 128;
-
-// Offset of row a in the packed, skewed lower storage.
-__host__ __device__ __forceinline__ int rowoff(int a) {
-  const int q = a >> 3, s = a & 7;
-  return 32 * q * (q + 2) + s * (8 * q + 12);
-}
 
 // Floats of one factor: the packed rows plus the Q inverse diagonal blocks.
 __host__ __device__ __forceinline__ int factor_floats(int Q) { return 32 * Q * (Q + 2) + 64 * Q; }
@@ -106,15 +100,6 @@ __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lan
   bad = __shfl_sync(0xffffffffu, bad ? 1 : 0, 0) != 0;
   __syncwarp();
   return !bad;
-}
-
-// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned), and the
-// wait for every such copy issued by this thread.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // Row index of entry t of a lower triangle enumerated row by row (t = a(a+1)/2 + b).
@@ -374,32 +359,23 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
     }
     __syncthreads();
   } else {
-    // S = G + lambda diag(D_i). Row a's packed segment (columns 0 .. end of its
-    // diagonal block) is copied from G in 16-byte asynchronous copies spread over all
-    // threads (8-row block q holds rows of 2q + 2 chunks); the entries above the diagonal
-    // inside a diagonal block are never read. Padding rows are identity rows.
+    // S = G + lambda diag(D_i). The Gram kernel left rows 0 .. k-1 of G in this packed
+    // layout (each row up to the end of its diagonal block; the entries above the
+    // diagonal inside a diagonal block are never read): one bulk copy brings them in
+    // (with G itself for the residual when it stays in shared memory). Padding rows are
+    // identity rows, written meanwhile.
     __syncthreads();   // barrier initialised
-    if (use_gs && tid == 0) {
-      tc::mbar_arrive_expect_tx(&s_bar, gs_bytes);
-      tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
-    }
-    {
-      const int nch = 8 * Q * (Q + 1);
-      for (int t = tid; t < nch; t += NT) {
-        int q = (int)((sqrtf(1.f + 0.5f * (float)t) - 1.f) * 0.5f);
-        while (8 * (q + 1) * (q + 2) <= t) ++q;
-        while (8 * q * (q + 1) > t) --q;
-        const int rem = t - 8 * q * (q + 1), len = 2 * q + 2;
-        const int a = 8 * q + rem / len, ch = rem - (rem / len) * len;
-        if (a < k) cp_async16(S + rowoff(a) + 4 * ch, G + (int64_t)a * ldg + 4 * ch);
-      }
-      cp_async_commit_wait_all();
+    if (tid == 0) {
+      const uint32_t s_bytes = (uint32_t)rowoff(k) * 4u;
+      tc::mbar_arrive_expect_tx(&s_bar, s_bytes + gs_bytes);
+      tc::bulk_g2s(S, G + gram_packed_off(k), s_bytes, &s_bar);
+      if (use_gs) tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
     }
     for (int a = k + tid; a < kp; a += NT) {
       float* row = S + rowoff(a);
       for (int c = 0; c < (a & ~7) + 8; ++c) row[c] = (c == a) ? 1.f : 0.f;
     }
-    if (use_gs && !tc::mbar_wait(&s_bar, 0, &s_abort)) {
+    if (!tc::mbar_wait(&s_bar, 0, &s_abort)) {
       // a copy that never completed: report, give it a bounded time to land, leave
       if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
       const uint64_t t0 = tc::globaltimer();
@@ -426,38 +402,49 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
         __syncwarp();
         if (lane < 8) v[r0 + lane] = y;
       }
-      // TRSM: rows below the diagonal block, x = s L_JJ^-T
-      for (int a = r0 + 8 + tid; a < kp; a += NT) {
-        float4* ra = reinterpret_cast<float4*>(S + rowoff(a) + r0);
+      // TRSM: rows below the diagonal block, x = s L_JJ^-T. Thread t owns row r0 + 8 + t
+      // (every launch has NT >= kp threads) here and in (a), which reuses x.
+      const int ar = r0 + 8 + tid;
+      float x[8];
+      if (ar < kp) {
+        float4* ra = reinterpret_cast<float4*>(S + rowoff(ar) + r0);
         const float4 s0 = ra[0], s1 = ra[1];
         const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-        float x[8];
+        const float4* l4 = reinterpret_cast<const float4*>(li);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
+          const float4 q0 = l4[2 * c];
+          float lr[8] = {q0.x, q0.y, q0.z, q0.w, 0.f, 0.f, 0.f, 0.f};
+          if (c >= 4) {
+            const float4 q1 = l4[2 * c + 1];
+            lr[4] = q1.x; lr[5] = q1.y; lr[6] = q1.z; lr[7] = q1.w;
+          }
           float t = 0.f;
 #pragma unroll
-          for (int m = 0; m <= c; ++m) t = fmaf(sv[m], li[c * 8 + m], t);
+          for (int m = 0; m <= c; ++m) t = fmaf(sv[m], lr[m], t);
           x[c] = t;
         }
         ra[0] = make_float4(x[0], x[1], x[2], x[3]);
         ra[1] = make_float4(x[4], x[5], x[6], x[7]);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) pan[c * kp + a] = x[c];
+        for (int c = 0; c < 8; ++c) pan[c * kp + ar] = x[c];
       }
       __syncthreads();
       if (J + 1 == Q) break;
       // (a) the next column block, one row per thread; the row's right-hand side
       // takes the panel's contribution, v_a -= L_aJ y_J
       const int n0 = r0 + 8;
-      for (int a = n0 + tid; a < kp; a += NT) {
-        float4* ra = reinterpret_cast<float4*>(S + rowoff(a) + n0);
+      if (ar < kp) {
+        float4* ra = reinterpret_cast<float4*>(S + rowoff(ar) + n0);
         const float4 u0 = ra[0], u1 = ra[1];
         float acc[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-        float va = v[a];
+        const float4 y0 = reinterpret_cast<const float4*>(v + r0)[0], y1 = reinterpret_cast<const float4*>(v + r0)[1];
+        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+        float va = v[ar];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const float la = pan[c * kp + a];
-          va = fmaf(-la, v[r0 + c], va);
+          const float la = x[c];
+          va = fmaf(-la, yv[c], va);
           const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + n0);
           const float4 b0 = pb[0], b1 = pb[1];
           acc[0] = fmaf(-la, b0.x, acc[0]); acc[1] = fmaf(-la, b0.y, acc[1]);
@@ -467,7 +454,7 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
         }
         ra[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         ra[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-        v[a] = va;
+        v[ar] = va;
       }
       // (a) writes column block J+1 and (b)'s tiles touch only blocks J+2.. (both read the
       // panel), so no block barrier separates them: warp 0 updated the diagonal block's
@@ -478,8 +465,8 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
         if (!diag_block(S, linv, J + 1, lane) && lane == 0) s_bad = 1;
       } else {
         // trailing blocks (A, B), J+2 <= B <= A < Q, as 8x4 or 4x4 register tiles: the
-        // size whose rounds over the NT - 32 threads cost the fewest instructions (an 8x8
-        // tile would save ~1% of the instructions and spill registers at two blocks/SM)
+        // size whose rounds over the NT - 32 threads cost the fewest instructions (8x8
+        // tiles fit the registers only with a partly rolled panel loop and ran slower)
         const int m = Q - J - 2;
         const int nb = NT - 32, t0 = tid - 32, base = 8 * (J + 2);
         const int T84 = m * (m + 1), T44 = m * (2 * m + 1);
@@ -694,6 +681,9 @@ cudaError_t solve_set_smem_limits() {
 cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode, const float* rhs_flat,
                          float* out_flat, float* saved, int32_t* status, float* ws, cudaStream_t st) {
   if (g.count <= 0) return cudaSuccess;
+  // one thread per row: the substitutions, the TRSM and the (a) update assume NT >= kp
+  const int nt = (g.threads == 64 || g.threads == 128 || g.threads == 256) ? g.threads : 320;
+  if (8 * ((g.kmax + 7) / 8) > nt) return cudaErrorInvalidValue;
   const size_t smem = chol_smem_bytes(g.kmax);
   const int gs = g.kmax <= kGsMaxK ? 1 : 0;
   switch (g.threads) {

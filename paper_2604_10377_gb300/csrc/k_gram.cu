@@ -2,7 +2,9 @@
 //   G = A_x A_x^T and R = A_y A_x^T, both k x k, per pair.
 // 64 x 64 output tiles, 4 x 4 outputs per thread, the feature dimension staged
 // through shared memory 16 columns at a time. G is symmetric: only its lower
-// tiles are computed and each is written twice (transposed).
+// tiles are computed and each is written twice (transposed), and once more into a packed
+// copy of the lower rows (each row up to the end of its 8 x 8 diagonal block) that the
+// row solves load into shared memory with a single bulk copy.
 // For pairs flagged hi_gram (large k) G is accumulated in double-float
 // arithmetic: every product is split exactly (fma) and summed with an
 // error-free transformation, which keeps ~48 significant bits, as an FP64
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
     if (ti >= nt) return;
     const int i0 = ti * kT, j0 = tj * kT;
     float* g = ws + pd.g_off;
+    float* gp = g + gram_packed_off(k);   // the same values in the row solves' packed layout
     const int ldg = gram_ld(k);
     float2* ghl = pd.hi_gram ? reinterpret_cast<float2*>(ws) + pd.g64_off : nullptr;
     if (pd.hi_gram)
@@ -101,6 +104,8 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
         }
         g[(int64_t)i * ldg + j] = v;
         g[(int64_t)j * ldg + i] = v;
+        if (j <= (i | 7)) gp[rowoff(i) + j] = v;
+        if (i <= (j | 7)) gp[rowoff(j) + i] = v;
         if (ghl) {
           ghl[(int64_t)i * k + j] = make_float2(v, e);
           ghl[(int64_t)j * k + i] = make_float2(v, e);
