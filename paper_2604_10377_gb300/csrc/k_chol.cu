@@ -158,25 +158,44 @@ __device__ __forceinline__ void trail_tile(float* S, const float* pan, int kp, i
 // 8 rows when Q is odd). The inverse of a 16-row diagonal block is formed from the two
 // 8x8 inverses A^-1, B^-1 and the block below the diagonal L21:
 //   [A 0; L21 B]^-1 = [A^-1 0; M B^-1] with M = -B^-1 L21 A^-1,
-// and M (64 floats per 16-row block) is computed once per factor, by every thread.
+// and M (64 floats per 16-row block) is computed once per factor: one thread per column j
+// of a block forms T = L21 (column j of A^-1), then column j of M = -B^-1 T.
+__device__ __forceinline__ void load8(const float* src, float (&d)[8]) {
+  const float4 u0 = reinterpret_cast<const float4*>(src)[0], u1 = reinterpret_cast<const float4*>(src)[1];
+  d[0] = u0.x; d[1] = u0.y; d[2] = u0.z; d[3] = u0.w;
+  d[4] = u1.x; d[5] = u1.y; d[6] = u1.z; d[7] = u1.w;
+}
+
 __device__ __forceinline__ void pair_blocks_prepare(const float* S, const float* linv, float* mo, int Q, int tid,
                                                     int nt) {
   const int np = Q >> 1;   // 16-row blocks with two 8-row halves
-  for (int e = tid; e < np * 64; e += nt) {
-    const int p = e >> 6, i = (e >> 3) & 7, j = e & 7;
+  for (int e = tid; e < np * 8; e += nt) {
+    const int p = e >> 3, j = e & 7;
     const float* Ai = linv + (2 * p) * 64;        // A^-1, row-major
     const float* Bi = linv + (2 * p + 1) * 64;    // B^-1
-    float acc = 0.f;
+    float ac[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) ac[l] = Ai[l * 8 + j];
+    float T[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       // (L21 A^-1)[m][j]
-      const float* l21 = S + rowoff(16 * p + 8 + m) + 16 * p;
+      float l21[8];
+      load8(S + rowoff(16 * p + 8 + m) + 16 * p, l21);
       float t = 0.f;
 #pragma unroll
-      for (int l = 0; l < 8; ++l) t = fmaf(l21[l], Ai[l * 8 + j], t);
-      acc = fmaf(Bi[i * 8 + m], t, acc);
+      for (int l = 0; l < 8; ++l) t = fmaf(l21[l], ac[l], t);
+      T[m] = t;
     }
-    mo[e] = -acc;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float bi[8];
+      load8(Bi + i * 8, bi);
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) acc = fmaf(bi[m], T[m], acc);
+      mo[p * 64 + i * 8 + j] = -acc;
+    }
   }
 }
 
@@ -186,15 +205,20 @@ __device__ __forceinline__ void apply_inv_fwd(const float* linv, const float* mo
   const bool two = 2 * p + 1 < Q;
   float y = 0.f;
   if (lane < 8) {
-    const float* Ai = linv + (2 * p) * 64 + lane * 8;
+    float a[8], vt[8];
+    load8(linv + (2 * p) * 64 + lane * 8, a);
+    load8(v + r0, vt);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) y = fmaf(Ai[j], v[r0 + j], y);
+    for (int j = 0; j < 8; ++j) y = fmaf(a[j], vt[j], y);
   } else if (lane < 16 && two) {
     const int i = lane - 8;
-    const float* Mi = mo + p * 64 + i * 8;
-    const float* Bi = linv + (2 * p + 1) * 64 + i * 8;
+    float mi[8], bi[8], vt[8], vb[8];
+    load8(mo + p * 64 + i * 8, mi);
+    load8(linv + (2 * p + 1) * 64 + i * 8, bi);
+    load8(v + r0, vt);
+    load8(v + r0 + 8, vb);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) y = fmaf(Mi[j], v[r0 + j], fmaf(Bi[j], v[r0 + 8 + j], y));
+    for (int j = 0; j < 8; ++j) y = fmaf(mi[j], vt[j], fmaf(bi[j], vb[j], y));
   }
   __syncwarp();
   if (lane < (two ? 16 : 8)) v[r0 + lane] = y;
@@ -208,17 +232,23 @@ __device__ __forceinline__ void apply_inv_bwd(const float* linv, const float* mo
   float x = 0.f;
   if (i >= 0 && i < 8) {
     const float* Ai = linv + (2 * p) * 64;
+    float vt[8];
+    load8(v + r0, vt);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x = fmaf(Ai[j * 8 + i], v[r0 + j], x);
+    for (int j = 0; j < 8; ++j) x = fmaf(Ai[j * 8 + i], vt[j], x);
     if (two) {
       const float* Mp = mo + p * 64;
+      float vb[8];
+      load8(v + r0 + 8, vb);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x = fmaf(Mp[j * 8 + i], v[r0 + 8 + j], x);
+      for (int j = 0; j < 8; ++j) x = fmaf(Mp[j * 8 + i], vb[j], x);
     }
   } else if (i >= 8 && i < 16 && two) {
     const float* Bi = linv + (2 * p + 1) * 64;
+    float vb[8];
+    load8(v + r0 + 8, vb);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x = fmaf(Bi[j * 8 + (i - 8)], v[r0 + 8 + j], x);
+    for (int j = 0; j < 8; ++j) x = fmaf(Bi[j * 8 + (i - 8)], vb[j], x);
   }
   __syncwarp();
   if (i >= 0 && i < (two ? 16 : 8)) v[r0 + i] = x;
@@ -272,12 +302,15 @@ __device__ __forceinline__ void block_bwd(const float* S, const float* linv, con
     const int w = (r0 + 16 <= kp) ? 16 : 8;
     if (tid < r0) {
       float t = v[tid];
+      float vt[8];
+      load8(v + r0, vt);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], vt[m], t);
       if (w == 16) {
+        float vb[8];
+        load8(v + r0 + 8, vb);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], v[r0 + m], t);
-      } else {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) t = fmaf(-S[rowoff(r0 + m) + tid], v[r0 + m], t);
+        for (int m = 0; m < 8; ++m) t = fmaf(-S[rowoff(r0 + 8 + m) + tid], vb[m], t);
       }
       v[tid] = t;
     }
