@@ -41,13 +41,27 @@ __device__ __forceinline__ void gram_tile(const float* X, const float* Y, int k,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) { hi[a][b] = 0.f; lo[a][b] = 0.f; }
+  // the next slab is loaded into registers while this one computes
+  constexpr int kPer = kT * kS / 256;
+  float rx[kPer], ry[kPer];
+  auto fetch = [&](int f0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = tid + 256 * u, r = e / kS, c = e % kS, f = f0 + c;
+      rx[u] = (i0 + r < k && f < d) ? X[(int64_t)(i0 + r) * d + f] : 0.f;
+      ry[u] = (j0 + r < k && f < d) ? Y[(int64_t)(j0 + r) * d + f] : 0.f;
+    }
+  };
+  fetch(0);
   for (int f0 = 0; f0 < d; f0 += kS) {
-    for (int e = tid; e < kT * kS; e += 256) {
-      const int r = e / kS, c = e % kS, f = f0 + c;
-      sX[c][r] = (i0 + r < k && f < d) ? X[(int64_t)(i0 + r) * d + f] : 0.f;
-      sY[c][r] = (j0 + r < k && f < d) ? Y[(int64_t)(j0 + r) * d + f] : 0.f;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = tid + 256 * u, r = e / kS, c = e % kS;
+      sX[c][r] = rx[u];
+      sY[c][r] = ry[u];
     }
     __syncthreads();
+    if (f0 + kS < d) fetch(f0 + kS);
 #pragma unroll
     for (int c = 0; c < kS; ++c) {
       const float4 xa = *reinterpret_cast<const float4*>(&sX[c][ty * 4]);

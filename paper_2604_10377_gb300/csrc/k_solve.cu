@@ -18,6 +18,7 @@ __device__ __forceinline__ float mask_entry(const PairDev& pd, const float* evx,
 // ---------------------------------------------------------------- adjoint GEMMs
 constexpr int kTile = 64;
 constexpr int kStage = 16;
+constexpr int kPer = kTile * kStage / 256;   // stage elements per thread and operand
 
 
 // W = Gamma^T C + C^T Gamma (k x k), and the mask gradient dD = -lambda Gamma o C.
@@ -35,16 +36,31 @@ __global__ void __launch_bounds__(256) adjoint_w_kernel(BatchDev b, const float*
   const float* cm = c_flat + pd.c_off;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float acc[4][4] = {};
-  for (int m0 = 0; m0 < k; m0 += kStage) {
-    for (int e = tid; e < kStage * kTile; e += 256) {
-      const int mm = e / kTile, cc = e % kTile, m = m0 + mm;
+  // the next stage's operands are loaded into registers while this stage computes
+  float rg[kPer], rc[kPer], rgb[kPer], rcb[kPer];
+  auto fetch = [&](int m0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = tid + 256 * u, mm = e / kTile, cc = e % kTile, m = m0 + mm;
       const bool okm = m < k;
-      sG[mm][cc] = (okm && a0 + cc < k) ? gam[(int64_t)m * k + a0 + cc] : 0.f;
-      sC[mm][cc] = (okm && a0 + cc < k) ? cm[(int64_t)m * k + a0 + cc] : 0.f;
-      sGb[mm][cc] = (okm && b0 + cc < k) ? gam[(int64_t)m * k + b0 + cc] : 0.f;
-      sCb[mm][cc] = (okm && b0 + cc < k) ? cm[(int64_t)m * k + b0 + cc] : 0.f;
+      rg[u] = (okm && a0 + cc < k) ? gam[(int64_t)m * k + a0 + cc] : 0.f;
+      rc[u] = (okm && a0 + cc < k) ? cm[(int64_t)m * k + a0 + cc] : 0.f;
+      rgb[u] = (okm && b0 + cc < k) ? gam[(int64_t)m * k + b0 + cc] : 0.f;
+      rcb[u] = (okm && b0 + cc < k) ? cm[(int64_t)m * k + b0 + cc] : 0.f;
+    }
+  };
+  fetch(0);
+  for (int m0 = 0; m0 < k; m0 += kStage) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = tid + 256 * u, mm = e / kTile, cc = e % kTile;
+      sG[mm][cc] = rg[u];
+      sC[mm][cc] = rc[u];
+      sGb[mm][cc] = rgb[u];
+      sCb[mm][cc] = rcb[u];
     }
     __syncthreads();
+    if (m0 + kStage < k) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 g4 = *reinterpret_cast<const float4*>(&sG[mm][ty * 4]);
@@ -122,34 +138,45 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
   const float* ay = a_flat + b.shapes[pd.y].a_off;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float acc[4][4] = {};
-  for (int m0 = 0; m0 < k; m0 += kStage) {
-    for (int e = tid; e < kTile * kStage; e += 256) {
-      // Gamma^T[a][m] = Gamma[m][a]: consecutive threads take consecutive a (coalesced)
-      const int aa = e % kTile, mm = e / kTile;
-      const int a = a0 + aa, m = m0 + mm;
-      if (which == 0) sX[mm][aa] = (a < k && m < k) ? gam[(int64_t)m * k + a] : 0.f;
-    }
-    for (int e = tid; e < kTile * kStage; e += 256) {
-      const int aa = e / kStage, mm = e % kStage;
-      const int a = a0 + aa, m = m0 + mm;
-      const bool ok = a < k && m < k;
-      if (which == 0)
-        sX2[mm][aa] = ok ? -w[(int64_t)a * k + m] : 0.f;     // -W[a][m]
-      else
-        sX[mm][aa] = ok ? gam[(int64_t)a * k + m] : 0.f;     // Gamma[a][m]
-    }
-    for (int e = tid; e < kStage * kTile; e += 256) {
-      const int mm = e / kTile, ff = e % kTile;
-      const int m = m0 + mm, f = f0 + ff;
-      const bool ok = m < k && f < d;
-      if (which == 0) {
-        sY[mm][ff] = ok ? ay[(int64_t)m * d + f] : 0.f;
-        sY2[mm][ff] = ok ? ax[(int64_t)m * d + f] : 0.f;
-      } else {
-        sY[mm][ff] = ok ? ax[(int64_t)m * d + f] : 0.f;
+  // the next stage's operands are loaded into registers while this stage computes
+  float r1[kPer], r2[kPer], r3[kPer], r4[kPer];
+  auto fetch = [&](int m0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = tid + 256 * u;
+      {
+        // Gamma^T[a][m] = Gamma[m][a]: consecutive threads take consecutive a (coalesced)
+        const int aa = e % kTile, mm = e / kTile, a = a0 + aa, m = m0 + mm;
+        r1[u] = (which == 0 && a < k && m < k) ? gam[(int64_t)m * k + a] : 0.f;
+      }
+      {
+        const int aa = e / kStage, mm = e % kStage, a = a0 + aa, m = m0 + mm;
+        const bool ok = a < k && m < k;
+        r2[u] = !ok ? 0.f : (which == 0 ? -w[(int64_t)a * k + m] : gam[(int64_t)a * k + m]);   // -W[a][m] | Gamma[a][m]
+      }
+      {
+        const int mm = e / kTile, ff = e % kTile, m = m0 + mm, f = f0 + ff;
+        const bool ok = m < k && f < d;
+        r3[u] = ok ? (which == 0 ? ay : ax)[(int64_t)m * d + f] : 0.f;
+        r4[u] = (ok && which == 0) ? ax[(int64_t)m * d + f] : 0.f;
       }
     }
+  };
+  fetch(0);
+  for (int m0 = 0; m0 < k; m0 += kStage) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = tid + 256 * u;
+      if (which == 0) sX[e / kTile][e % kTile] = r1[u];
+      if (which == 0)
+        sX2[e % kStage][e / kStage] = r2[u];
+      else
+        sX[e % kStage][e / kStage] = r2[u];
+      sY[e / kTile][e % kTile] = r3[u];
+      if (which == 0) sY2[e / kTile][e % kTile] = r4[u];
+    }
     __syncthreads();
+    if (m0 + kStage < k) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
@@ -219,14 +246,27 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
   float* e = ws + pd.e_off;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float acc[4][4] = {};
-  for (int m0 = 0; m0 < k; m0 += kStage) {
-    for (int q = tid; q < kTile * kStage; q += 256) {
+  // the next stage's operands are loaded into registers while this stage computes
+  float rx[kPer], ry[kPer];
+  auto fetch = [&](int m0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
       // rows of C read in 16-element segments (consecutive threads, consecutive m)
-      const int r = q / kStage, mm = q % kStage;
-      sX[mm][r] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
-      sY[mm][r] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
+      const int q = tid + 256 * u, r = q / kStage, mm = q % kStage;
+      rx[u] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+      ry[u] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
+    }
+  };
+  fetch(0);
+  for (int m0 = 0; m0 < k; m0 += kStage) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = tid + 256 * u, r = q / kStage, mm = q % kStage;
+      sX[mm][r] = rx[u];
+      sY[mm][r] = ry[u];
     }
     __syncthreads();
+    if (m0 + kStage < k) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
@@ -285,16 +325,32 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
   const float* e = ws + pd.e_off;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float acc[4][4] = {};
-  for (int m0 = 0; m0 < k; m0 += kStage) {
-    for (int q = tid; q < kTile * kStage; q += 256) {
-      const int r = q / kStage, mm = q % kStage;
-      sX[mm][r] = (a0 + r < k && m0 + mm < k) ? e[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+  // the next stage's operands are loaded into registers while this stage computes
+  float rx[kPer], ry[kPer];
+  auto fetch = [&](int m0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = tid + 256 * u;
+      {
+        const int r = q / kStage, mm = q % kStage;
+        rx[u] = (a0 + r < k && m0 + mm < k) ? e[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+      }
+      {
+        const int mm = q / kTile, r = q % kTile;
+        ry[u] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(m0 + mm) * k + b0 + r] : 0.f;
+      }
     }
-    for (int q = tid; q < kStage * kTile; q += 256) {
-      const int mm = q / kTile, r = q % kTile;
-      sY[mm][r] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(m0 + mm) * k + b0 + r] : 0.f;
+  };
+  fetch(0);
+  for (int m0 = 0; m0 < k; m0 += kStage) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = tid + 256 * u;
+      sX[q % kStage][q / kStage] = rx[u];
+      sY[q / kTile][q % kTile] = ry[u];
     }
     __syncthreads();
+    if (m0 + kStage < k) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
