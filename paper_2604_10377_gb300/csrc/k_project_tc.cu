@@ -273,12 +273,23 @@ __global__ void project_tc_reduce_kernel(const ShapeDev* shapes, const TcItem* i
                                          float* a_out, const float* ws) {
   const TcRedGroup g = groups[blockIdx.y];
   const ShapeDev s = shapes[g.shape];
-  const int64_t total = (int64_t)g.nk * g.dspan;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = e / g.dspan, f = e % g.dspan;
-    float acc = 0.f;
-    for (int i = g.it_beg; i < g.it_end; ++i) acc += ws[items[i].part_off + n * g.stride + f];
-    a_out[s.a_off + (g.n0 + n) * s.d + g.f0 + f] = acc;
+  // four consecutive features per thread (dspan, f0, d are multiples of 16 and the
+  // partials are 256-byte aligned; float4 stores when the output buffer is 16-byte aligned)
+  const int q4 = g.dspan >> 2, total = g.nk * q4;
+  const bool vec = (reinterpret_cast<uintptr_t>(a_out) & 15) == 0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int n = e / q4, f = (e - n * q4) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = g.it_beg; i < g.it_end; ++i) {
+      const float4 u = *reinterpret_cast<const float4*>(ws + items[i].part_off + (int64_t)n * g.stride + f);
+      acc.x += u.x; acc.y += u.y; acc.z += u.z; acc.w += u.w;
+    }
+    float* o = a_out + s.a_off + (int64_t)(g.n0 + n) * s.d + g.f0 + f;
+    if (vec) {
+      *reinterpret_cast<float4*>(o) = acc;
+    } else {
+      o[0] = acc.x; o[1] = acc.y; o[2] = acc.z; o[3] = acc.w;
+    }
   }
 }
 
@@ -300,7 +311,7 @@ cudaError_t launch_project_tc_reduce(const ShapeDev* shapes, const TcItem* items
                                      int n_groups, int64_t max_elems, float* a_out, const float* ws,
                                      cudaStream_t st) {
   if (n_groups <= 0) return cudaSuccess;
-  dim3 grid((unsigned)std::min<int64_t>((max_elems + 255) / 256, 4096), (unsigned)n_groups);
+  dim3 grid((unsigned)std::min<int64_t>((max_elems / 4 + 255) / 256, 4096), (unsigned)n_groups);
   project_tc_reduce_kernel<<<grid, 256, 0, st>>>(shapes, items, groups, a_out, ws);
   return cudaGetLastError();
 }

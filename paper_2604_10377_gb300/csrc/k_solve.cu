@@ -22,7 +22,7 @@ constexpr int kPer = kTile * kStage / 256;   // stage elements per thread and op
 
 
 // W = Gamma^T C + C^T Gamma (k x k), and the mask gradient dD = -lambda Gamma o C.
-__global__ void __launch_bounds__(256) adjoint_w_kernel(BatchDev b, const float* c_flat, float* d_mask, float* ws) {
+__global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const float* c_flat, float* d_mask, float* ws) {
   __shared__ __align__(16) float sG[kStage][kTile + 4];   // Gamma[m][a-tile]
   __shared__ __align__(16) float sC[kStage][kTile + 4];   // C[m][a-tile]
   __shared__ __align__(16) float sGb[kStage][kTile + 4];  // Gamma[m][b-tile]
@@ -214,14 +214,29 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
   }
 }
 
-// dA_s = sum of the shape's contributions, in pair order.
+// dA_s = sum of the shape's contributions, in pair order. Each thread sums four
+// consecutive entries (one float4 per contribution when the shape's output is 16-byte
+// aligned; the contribution slots always are).
 __global__ void gather_da_kernel(BatchDev b, float* d_a, const float* ws) {
   const ShapeDev s = b.shapes[blockIdx.y];
   const int64_t kd = (int64_t)s.k * s.d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < kd; e += (int64_t)gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int q = s.slot_beg; q < s.slot_end; ++q) acc += ws[b.slot_list[q] + e];
-    d_a[s.a_off + e] = acc;
+  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (e0 >= kd) return;
+  float* out = d_a + s.a_off;
+  const bool vec = ((kd & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  if (vec) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = s.slot_beg; q < s.slot_end; ++q) {
+      const float4 u = *reinterpret_cast<const float4*>(ws + b.slot_list[q] + e0);
+      acc.x += u.x; acc.y += u.y; acc.z += u.z; acc.w += u.w;
+    }
+    *reinterpret_cast<float4*>(out + e0) = acc;
+  } else {
+    for (int j = 0; j < 4 && e0 + j < kd; ++j) {
+      float acc = 0.f;
+      for (int q = s.slot_beg; q < s.slot_end; ++q) acc += ws[b.slot_list[q] + e0 + j];
+      out[e0 + j] = acc;
+    }
   }
 }
 
@@ -401,7 +416,7 @@ cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const 
 
 cudaError_t launch_gather_da(const BatchDev& b, int max_kd, float* d_a, const float* ws, cudaStream_t st) {
   if (b.n_shapes <= 0) return cudaSuccess;
-  gather_da_kernel<<<dim3((max_kd + 255) / 256, b.n_shapes), 256, 0, st>>>(b, d_a, ws);
+  gather_da_kernel<<<dim3((max_kd + 1023) / 1024, b.n_shapes), 256, 0, st>>>(b, d_a, ws);
   return cudaGetLastError();
 }
 
