@@ -132,6 +132,20 @@ def test_ir_steps_and_hi_gram():
         _check_forward(wl, ir_steps=ir, hi_gram_min_k=50)
 
 
+@pytest.mark.parametrize("ks,hi_min,ir", [((129, 150, 199), 200, 1), ((150, 256), 1000, 2)])
+def test_refinement_with_fp32_gram_from_global(ks, hi_min, ir):
+    """Row systems above the shared-memory copy of G (k > 128) with the FP32 Gram: the
+    refinement residual reads the lower triangle of G from global memory, for one and two
+    refinement steps (d >= 2k, well-conditioned FP32 systems)."""
+    rng = np.random.default_rng(17)
+    shapes, pairs = [], []
+    for i, k in enumerate(ks):
+        shapes += [_shape(rng, 3000 + 7 * i, k, 512), _shape(rng, 2500 + 5 * i, k, 512)]
+        pairs.append(synth.Pair(x=2 * i, y=2 * i + 1, lam=1e-2))
+    wl = synth.Workload("gram_global", shapes, pairs, "fp32")
+    _check_forward(wl, ir_steps=ir, hi_gram_min_k=hi_min)
+
+
 def test_bitwise_reproducible():
     wl = synth.make_small(7, 3, (3000, 20000), [30, 64, 100], 64)
     from paper_2604_10377_gb300 import api
