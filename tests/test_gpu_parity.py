@@ -192,6 +192,28 @@ def _oracle_backward(wl):
     return shapes, pairs, fwd, losses, dcs, g
 
 
+@pytest.mark.parametrize("use_saved,adj_ir", [(True, 1), (False, 1), (True, 2)])
+def test_backward_with_adjoint_refinement(use_saved, adj_ir):
+    """Refinement steps in the adjoint row solves (off by default): k below and above the
+    shared-memory Gram copy, FP32 and double-float Gram, saved or recomputed factors."""
+    rng = np.random.default_rng(23)
+    shapes, pairs = [], []
+    for i, k in enumerate((60, 150, 210)):
+        shapes += [_shape(rng, 2000 + 11 * i, k, 448), _shape(rng, 1800 + 13 * i, k, 448)]
+        pairs.append(synth.Pair(x=2 * i, y=2 * i + 1, lam=1e-2,
+                                c_gt=synth.random_orthogonal(40 + i, k)))
+    wl = synth.Workload("adj_ir", shapes, pairs, "fp32")
+    out = _gpu_backward(wl, use_saved=use_saved, adjoint_ir_steps=adj_ir)
+    shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert rel_fro(out["C"][p], fwd["C"][p]) <= TOL["fp32"]
+        assert rel_fro(out["dD"][p], g["pair"][p]["dD"]) <= GTOL["fp32"]
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["fp32"]
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
+
+
 @pytest.mark.parametrize("feat_dtype,use_saved", [("fp32", True), ("fp32", False), ("bf16", True)])
 def test_backward_against_oracle(feat_dtype, use_saved):
     wl = synth.make_small(8, 4, (500, 6000), [12, 30, 64, 100], 256, feat_dtype=feat_dtype)
