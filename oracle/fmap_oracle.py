@@ -15,7 +15,9 @@ arXiv 2604.10377, Sec. 3.1 "Batched Functional Map Solver"):
 * Eq. 3: with Delta diagonal in its eigenbasis, the commutativity term is the
   entry-wise weight D_ij = (Lambda_Y(i) - Lambda_X(j))^2.
 * Eq. 4: normal equations C A A^T + lambda (D o C) = B A^T.
-* Eq. 5-7: row i of C solves (A A^T + lambda diag(D_i)) c_i = (B A^T)_i.
+* Eq. 5-7: row i of C solves (A A^T + lambda diag(D_i)) c_i = (B A^T)_i. C maps the
+  k_X coefficients of shape X to the k_Y of shape Y (k_Y x k_X); the paper's shapes share
+  k, and with k_X != k_Y the same equations give k_Y row systems of size k_X.
 * Eq. 8-9: the rows are independent, so all of them are solved as one batch.
 
 The solve uses a Cholesky factorisation written out below (the row systems are
@@ -132,13 +134,16 @@ def cholesky_solve(l, rhs):
 # Eq. 4-9 — the row-wise (batched) regularised solve
 # --------------------------------------------------------------------------
 def row_systems(a, d_mask, lam):
-    """S_i = A A^T + lambda diag(D_i) for every row i, stacked as (k, k, k) (Eq. 5, Eq. 8)."""
+    """S_i = A A^T + lambda diag(D_i) for every row i of C, stacked as (k_Y, k_X, k_X)
+    (Eq. 5, Eq. 8). A is k_X x d; D is k_Y x k_X, one row per row of C, so a map between
+    bases of different sizes (C of k_Y x k_X) has k_Y systems of size k_X."""
     a = np.asarray(a, dtype=np.float64)
     d_mask = np.asarray(d_mask, dtype=np.float64)
     g = a @ a.T
-    k = g.shape[0]
-    s = np.broadcast_to(g, (k, k, k)).copy()
-    idx = np.arange(k)
+    kx = g.shape[0]
+    ky = d_mask.shape[0]
+    s = np.broadcast_to(g, (ky, kx, kx)).copy()
+    idx = np.arange(kx)
     s[:, idx, idx] += lam * d_mask
     return s
 

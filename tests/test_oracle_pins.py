@@ -47,6 +47,84 @@ def test_vectorised_least_squares(k, d):
     np.testing.assert_allclose(c, c_ref, rtol=1e-9, atol=1e-11)
 
 
+def _rand_rect(seed, kx, ky, d):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((kx, d))
+    b = rng.standard_normal((ky, d))
+    ex = np.sort(rng.uniform(0, 10, kx))
+    ey = np.sort(rng.uniform(0, 10, ky))
+    return a, b, ex, ey, rng.uniform(0.05, 2.0)
+
+
+@pytest.mark.parametrize("kx,ky,d", [(2, 5, 3), (5, 2, 7), (4, 7, 6), (7, 3, 2), (1, 4, 2)])
+def test_vectorised_least_squares_rectangular(kx, ky, d):
+    """Maps between bases of different sizes (C is k_Y x k_X): the Kronecker form of
+    Eq. 2, vec(C A) = (A^T kron I_kY) vec(C) with penalty rows sqrt(lambda D_ij), solved
+    by LAPACK lstsq, equals the k_Y row systems of size k_X."""
+    a, b, ex, ey, lam = _rand_rect(kx * 100 + ky * 10 + d, kx, ky, d)
+    dm = orc.mask_from_evals(ex, ey)
+    assert dm.shape == (ky, kx)
+    top = np.kron(a.T, np.eye(ky))                     # (ky d, ky kx)
+    pen = np.diag(np.sqrt(lam * dm.flatten(order="F")))
+    rhs = np.concatenate([b.flatten(order="F"), np.zeros(ky * kx)])
+    vec_c, *_ = np.linalg.lstsq(np.vstack([top, pen]), rhs, rcond=None)
+    c_ref = vec_c.reshape((ky, kx), order="F")
+    c = orc.solve(a, b, dm, lam)
+    assert c.shape == (ky, kx)
+    np.testing.assert_allclose(c, c_ref, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("kx,ky,d", [(3, 6, 9), (6, 3, 9)])
+def test_energy_stationary_rectangular(kx, ky, d):
+    """Eq. 2 with Delta_X (k_X) and Delta_Y (k_Y): zero finite-difference gradient at the
+    rectangular solution, and random perturbations raise the energy."""
+    a, b, ex, ey, lam = _rand_rect(31 + kx + ky, kx, ky, d)
+    c = orc.solve(a, b, orc.mask_from_evals(ex, ey), lam)
+    e0 = orc.energy(c, a, b, ex, ey, lam)
+    h = 1e-6
+    for i in range(ky):
+        for j in range(kx):
+            dlt = np.zeros_like(c); dlt[i, j] = h
+            g = (orc.energy(c + dlt, a, b, ex, ey, lam) - orc.energy(c - dlt, a, b, ex, ey, lam)) / (2 * h)
+            assert abs(g) < 1e-5 * max(1.0, e0)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        assert orc.energy(c + 1e-3 * rng.standard_normal(c.shape), a, b, ex, ey, lam) > e0
+
+
+def test_rectangular_gradients_fd():
+    """Adjoint of the rectangular solve (dA, dB, dD, dlambda) against central differences of
+    the training loss through the solve."""
+    kx, ky, d = 4, 6, 7
+    a, b, ex, ey, lam = _rand_rect(77, kx, ky, d)
+    dm = orc.mask_from_evals(ex, ey)
+    gt = np.random.default_rng(5).standard_normal((ky, kx))
+
+    def loss(aa, bb, dd, ll):
+        return orc.loss_orth_gt(orc.solve(aa, bb, dd, ll), gt)[0]
+
+    c = orc.solve(a, b, dm, lam)
+    _, dc = orc.loss_orth_gt(c, gt)
+    g = orc.solve_backward(a, b, c, dm, lam, dc)
+    assert g["dA"].shape == a.shape and g["dB"].shape == b.shape and g["dD"].shape == dm.shape
+    h = 1e-5
+    rng = np.random.default_rng(6)
+    for name, x, gx in (("A", a, g["dA"]), ("B", b, g["dB"]), ("D", dm, g["dD"])):
+        for _ in range(4):
+            v = rng.standard_normal(x.shape)
+            def shifted(t):
+                if name == "A":
+                    return a + t * v, b, dm
+                if name == "B":
+                    return a, b + t * v, dm
+                return a, b, dm + t * v
+            fd = (loss(*shifted(h), lam) - loss(*shifted(-h), lam)) / (2 * h)
+            an = float(np.sum(gx * v))
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, fd, an)
+    fd_lam = (loss(a, b, dm, lam + h) - loss(a, b, dm, lam - h)) / (2 * h)
+    assert abs(fd_lam - g["dlam"]) <= 1e-6 * max(1.0, abs(fd_lam))
+
+
 @pytest.mark.parametrize("k,d", [(3, 7), (10, 30), (30, 64)])
 def test_lambda_zero_closed_form(k, d):
     """Data term only (lambda = 0): C = B A^T (A A^T)^{-1}."""
