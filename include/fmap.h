@@ -102,15 +102,18 @@ typedef struct fmap_shape_desc {
 
 typedef struct fmap_pair_desc {
     int32_t shape_x;       /* source shape (basis of the columns of C) */
-    int32_t shape_y;       /* target shape (basis of the rows of C); k_x == k_y, d_x == d_y */
+    int32_t shape_y;       /* target shape (basis of the rows of C); d_x == d_y. The basis
+                              sizes may differ: C is k_y x k_x, with k_y row systems of
+                              size k_x (the paper's pairs have k_x == k_y) */
     float lambda;          /* regularisation weight, >= 0 */
-    const float* mask;     /* device k x k FP32 mask D (row i = target basis index), or NULL:
-                              D_ij = (evals_y[i] - evals_x[j])^2 */
+    const float* mask;     /* device k_y x k_x FP32 mask D (row i = target basis index), or
+                              NULL: D_ij = (evals_y[i] - evals_x[j])^2 */
 } fmap_pair_desc;
 
 /* Sizes of a batch's buffers. Offsets: A of shape s starts at float a_offset(s) of
  * the flat A buffer (k_s x d_s, row-major); C of pair p at float c_offset(p) of the
- * flat C buffer (k_p x k_p, row-major). Offsets are prefix sums in input order. */
+ * flat C buffer (k_y x k_x of the pair, row-major). Offsets are prefix sums in input
+ * order. */
 typedef struct fmap_sizes {
     int64_t a_floats;        /* length of the flat A buffer (also dA) */
     int64_t c_floats;        /* length of the flat C buffer (also dC, mask gradients) */
@@ -227,7 +230,8 @@ FMAP_API int32_t fmap_batch_read_timing(fmap_batch* batch, float* ms, int32_t* l
  * application owns all device memory): the same Gram and row-system Cholesky kernels
  * as fmap_solve for ONE pair, with every scratch byte taken from a 2 MiB array that
  * the library defines on each GPU that loads it (held until the process exits). It
- * needs no batch, no workspace, and never calls cudaMalloc or cudaFree.
+ * needs no batch, no workspace, and never calls cudaMalloc or cudaFree. Square maps
+ * only (both bases of size k).
  *   a_x, a_y   device, k x d FP32 row-major descriptor matrices A and B (fmap_project's
  *              output for the source and the target shape), 4-byte aligned
  *   evals_x/y  device k FP32 eigenvalues, or NULL when mask is given

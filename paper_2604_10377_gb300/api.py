@@ -88,7 +88,8 @@ def host_to_torch(arr: np.ndarray, dtype_name: str = "") -> torch.Tensor:
 class FmapBatch:
     """A ragged batch of shape pairs bound to flat device buffers.
 
-    pairs: list of (x, y, lam); masks: optional list (per pair) of k x k arrays or None."""
+    pairs: list of (x, y, lam); masks: optional list (per pair) of k_Y x k_X arrays or None
+    (k_X = the basis size of shape x, k_Y of shape y; C_p is k_Y x k_X)."""
 
     def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
                  with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
@@ -104,8 +105,10 @@ class FmapBatch:
         self.feat = torch.zeros(lay.feat_len, dtype=lay.torch_feat_dtype(), device=dev)
         self.dfeat = torch.zeros_like(self.feat) if with_grad else None
         self.pairs = [(int(x), int(y), float(lam)) for (x, y, lam) in pairs]
+        # C_p maps the k_X coefficients of shape x to the k_Y of shape y: k_Y x k_X
         self.ks = [lay.ks[x] for (x, _, _) in self.pairs]
-        self.c_off_host = np.concatenate([[0], np.cumsum([k * k for k in self.ks])]).astype(np.int64)
+        self.kys = [lay.ks[y] for (_, y, _) in self.pairs]
+        self.c_off_host = np.concatenate([[0], np.cumsum([ky * k for k, ky in zip(self.ks, self.kys)])]).astype(np.int64)
         self.mask = None
         if masks is not None and any(m is not None for m in masks):
             host = np.zeros(int(self.c_off_host[-1]), np.float32)
@@ -268,8 +271,8 @@ class FmapBatch:
         return flat[int(self.a_off[s]):int(self.a_off[s + 1])].view(k, d)
 
     def c_view(self, flat: torch.Tensor, p: int) -> torch.Tensor:
-        k = self.ks[p]
-        return flat[int(self.c_off[p]):int(self.c_off[p + 1])].view(k, k)
+        """Pair p's k_Y x k_X block of a flat C-layout buffer."""
+        return flat[int(self.c_off[p]):int(self.c_off[p + 1])].view(self.kys[p], self.ks[p])
 
     # ------------------------------------------------------------------ calls
     def project(self, a_out: Optional[torch.Tensor] = None) -> torch.Tensor:
@@ -397,7 +400,7 @@ def batch_from_workload(wl, device="cuda:0", with_grad=True, **kw) -> FmapBatch:
 
 
 def flat_c(batch: FmapBatch, mats: List[np.ndarray]) -> torch.Tensor:
-    """Pack per-pair k x k matrices into the flat C layout of `batch`."""
+    """Pack per-pair k_Y x k_X matrices into the flat C layout of `batch`."""
     host = np.zeros(int(batch.c_off[-1]), np.float32)
     for p, m in enumerate(mats):
         host[batch.c_off[p]:batch.c_off[p + 1]] = np.asarray(m, np.float32).reshape(-1)

@@ -159,17 +159,17 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     if (q.shape_x < 0 || q.shape_x >= n_shapes || q.shape_y < 0 || q.shape_y >= n_shapes) return FMAP_ERR_INVALID_ARG;
     const fmap_shape_desc& sx = shapes[q.shape_x];
     const fmap_shape_desc& sy = shapes[q.shape_y];
-    if (sx.k != sy.k || sx.d != sy.d) return FMAP_ERR_INVALID_ARG;
+    if (sx.d != sy.d) return FMAP_ERR_INVALID_ARG;
     if (!(q.lambda >= 0.f) || !std::isfinite(q.lambda)) return FMAP_ERR_INVALID_ARG;
     if (!q.mask && (!sx.evals || !sy.evals)) return FMAP_ERR_INVALID_ARG;
     if (q.mask && !aligned(q.mask, 4)) return FMAP_ERR_UNSUPPORTED;
     PairDev& pd = P.pairs[p];
     std::memset(&pd, 0, sizeof(pd));
-    pd.x = q.shape_x; pd.y = q.shape_y; pd.k = sx.k; pd.d = sx.d;
+    pd.x = q.shape_x; pd.y = q.shape_y; pd.k = sx.k; pd.d = sx.d;   // C is sy.k x sx.k
     pd.lam = q.lambda; pd.mask = q.mask;
     pd.hi_gram = sx.k >= opt.hi_gram_min_k ? 1 : 0;
     pd.c_off = P.c_off[p];
-    P.c_off[p + 1] = P.c_off[p] + (int64_t)sx.k * sx.k;
+    P.c_off[p + 1] = P.c_off[p] + (int64_t)sy.k * sx.k;
   }
 
   // ---- workspace layout (floats, 256-byte aligned regions); the first 256 bytes
@@ -300,10 +300,11 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     }
   }
   for (auto& pd : P.pairs) {
-    const int64_t kk = (int64_t)pd.k * pd.k;
+    const int64_t ky = P.shapes[pd.y].k;   // rows of C (k_Y); pd.k = k_X
+    const int64_t kk = (int64_t)pd.k * pd.k, yk = ky * pd.k, yy = ky * ky;
     pd.g_off = cur; cur = align_up(cur + gram_floats(pd.k), kAlignFloats);
-    pd.r_off = cur; cur = align_up(cur + kk, kAlignFloats);
-    pd.e_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    pd.r_off = cur; cur = align_up(cur + yk, kAlignFloats);
+    pd.e_off = cur; cur = align_up(cur + yy, kAlignFloats);
     if (pd.hi_gram) {
       pd.g64_off = cur / 2;
       cur = align_up(cur + 2 * kk, kAlignFloats);
@@ -315,11 +316,12 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   cur = align_up(cur + (int64_t)n_pairs * kMaxLossTiles, kAlignFloats);
   const int64_t ws_fwd = cur;
   for (auto& pd : P.pairs) {
-    const int64_t kk = (int64_t)pd.k * pd.k, kd = (int64_t)pd.k * pd.d;
-    pd.gam_off = cur; cur = align_up(cur + kk, kAlignFloats);
+    const int64_t ky = P.shapes[pd.y].k;
+    const int64_t kk = (int64_t)pd.k * pd.k, yk = ky * pd.k;
+    pd.gam_off = cur; cur = align_up(cur + yk, kAlignFloats);
     pd.w_off = cur; cur = align_up(cur + kk, kAlignFloats);
-    pd.sx_off = cur; cur = align_up(cur + kd, kAlignFloats);
-    pd.sy_off = cur; cur = align_up(cur + kd, kAlignFloats);
+    pd.sx_off = cur; cur = align_up(cur + (int64_t)pd.k * pd.d, kAlignFloats);
+    pd.sy_off = cur; cur = align_up(cur + ky * pd.d, kAlignFloats);
   }
   P.da_int_off = cur;
   cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
@@ -464,7 +466,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   for (auto& pd : P.pairs) {
     if (pd.k <= opt.store_factors_max_k) {
       pd.fac_off = fac;
-      fac = align_up(fac + (int64_t)pd.k * chol_factor_floats(pd.k), kAlignFloats);
+      fac = align_up(fac + (int64_t)P.shapes[pd.y].k * chol_factor_floats(pd.k), kAlignFloats);
     } else {
       pd.fac_off = -1;
     }
@@ -499,7 +501,8 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     std::stable_sort(members.begin(), members.end(), [&](int a, int b) { return P.pairs[a].k > P.pairs[b].k; });
     for (int p : members) {
       g.kmax = std::max(g.kmax, P.pairs[p].k);
-      for (int i = 0; i < P.pairs[p].k; ++i) P.systems.push_back(make_int2(p, i));
+      const int ky = P.shapes[P.pairs[p].y].k;   // one row system per row of C
+      for (int i = 0; i < ky; ++i) P.systems.push_back(make_int2(p, i));
     }
     g.count = (int32_t)P.systems.size() - g.first;
     if (g.count > 0) P.groups.push_back(g);

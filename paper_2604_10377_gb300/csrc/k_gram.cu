@@ -1,5 +1,5 @@
 // Gram matrix and right-hand sides of the row systems (Eq. 4):
-//   G = A_x A_x^T and R = A_y A_x^T, both k x k, per pair.
+//   G = A_x A_x^T (k_X x k_X) and R = A_y A_x^T (k_Y x k_X), per pair.
 // 64 x 64 output tiles, 4 x 4 outputs per thread, the feature dimension staged
 // through shared memory 16 columns at a time. G is symmetric: only its lower
 // tiles are computed and each is written twice (transposed), and once more into a packed
@@ -30,9 +30,9 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
   lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
 
-// out[i][j] = sum_f X[i0 + i][f] Y[j0 + j][f] for one 64 x 64 tile.
+// out[i][j] = sum_f X[i0 + i][f] Y[j0 + j][f] for one 64 x 64 tile (X has kx rows, Y ky).
 template <bool kDF>
-__device__ __forceinline__ void gram_tile(const float* X, const float* Y, int k, int d, int i0, int j0,
+__device__ __forceinline__ void gram_tile(const float* X, const float* Y, int kx, int ky, int d, int i0, int j0,
                                           float (&hi)[4][4], float (&lo)[4][4]) {
   __shared__ float sX[kS][kT + 4];
   __shared__ float sY[kS][kT + 4];
@@ -48,8 +48,8 @@ __device__ __forceinline__ void gram_tile(const float* X, const float* Y, int k,
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = tid + 256 * u, r = e / kS, c = e % kS, f = f0 + c;
-      rx[u] = (i0 + r < k && f < d) ? X[(int64_t)(i0 + r) * d + f] : 0.f;
-      ry[u] = (j0 + r < k && f < d) ? Y[(int64_t)(j0 + r) * d + f] : 0.f;
+      rx[u] = (i0 + r < kx && f < d) ? X[(int64_t)(i0 + r) * d + f] : 0.f;
+      ry[u] = (j0 + r < ky && f < d) ? Y[(int64_t)(j0 + r) * d + f] : 0.f;
     }
   };
   fetch(0);
@@ -102,9 +102,9 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
     const int ldg = gram_ld(k);
     float2* ghl = pd.hi_gram ? reinterpret_cast<float2*>(ws) + pd.g64_off : nullptr;
     if (pd.hi_gram)
-      gram_tile<true>(ax, ax, k, d, i0, j0, hi, lo);
+      gram_tile<true>(ax, ax, k, k, d, i0, j0, hi, lo);
     else
-      gram_tile<false>(ax, ax, k, d, i0, j0, hi, lo);
+      gram_tile<false>(ax, ax, k, k, d, i0, j0, hi, lo);
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -126,17 +126,18 @@ __global__ void __launch_bounds__(256) gram_kernel(BatchDev b, const float* a, f
         }
       }
   } else {
-    // R = A_y A_x^T: every tile
-    if ((int)blockIdx.x >= nt * nt) return;
+    // R = A_y A_x^T (ky x k): every tile
+    const int ky = b.shapes[pd.y].k, nty = (ky + kT - 1) / kT;
+    if ((int)blockIdx.x >= nty * nt) return;
     const int i0 = (blockIdx.x / nt) * kT, j0 = (blockIdx.x % nt) * kT;
-    gram_tile<false>(ay, ax, k, d, i0, j0, hi, lo);
+    gram_tile<false>(ay, ax, ky, k, d, i0, j0, hi, lo);
     float* r = ws + pd.r_off;
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int i = i0 + ty * 4 + rr, j = j0 + tx * 4 + c;
-        if (i < k && j < k) r[(int64_t)i * k + j] = hi[rr][c];
+        if (i < ky && j < k) r[(int64_t)i * k + j] = hi[rr][c];
       }
   }
 }

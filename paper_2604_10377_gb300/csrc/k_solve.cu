@@ -1,3 +1,6 @@
+// A pair's map C is k_Y x k_X: k_X = pd.k (shape x, row-system size, columns of C) and
+// k_Y = the basis size of shape y (rows of C); the paper's maps are square.
+//
 // Adjoint of the row-wise solve (given Gamma from the adjoint row solves):
 // W = Gamma^T C + C^T Gamma, dA_x = Gamma^T A_y - W A_x, dA_y = Gamma A_x,
 // dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C); the per-shape gather of
@@ -21,14 +24,14 @@ constexpr int kStage = 16;
 constexpr int kPer = kTile * kStage / 256;   // stage elements per thread and operand
 
 
-// W = Gamma^T C + C^T Gamma (k x k), and the mask gradient dD = -lambda Gamma o C.
-__global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const float* c_flat, float* d_mask, float* ws) {
+// W = Gamma^T C + C^T Gamma (k_X x k_X; Gamma and C are k_Y x k_X).
+__global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const float* c_flat, float* ws) {
   __shared__ __align__(16) float sG[kStage][kTile + 4];   // Gamma[m][a-tile]
   __shared__ __align__(16) float sC[kStage][kTile + 4];   // C[m][a-tile]
   __shared__ __align__(16) float sGb[kStage][kTile + 4];  // Gamma[m][b-tile]
   __shared__ __align__(16) float sCb[kStage][kTile + 4];  // C[m][b-tile]
   const PairDev pd = b.pairs[blockIdx.z];
-  const int k = pd.k;
+  const int k = pd.k, ky = b.shapes[pd.y].k;   // Gamma, C: ky x k
   const int nt = (k + kTile - 1) / kTile;
   if ((int)blockIdx.x >= nt * nt) return;
   const int a0 = (blockIdx.x / nt) * kTile, b0 = (blockIdx.x % nt) * kTile;
@@ -42,7 +45,7 @@ __global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const flo
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = tid + 256 * u, mm = e / kTile, cc = e % kTile, m = m0 + mm;
-      const bool okm = m < k;
+      const bool okm = m < ky;
       rg[u] = (okm && a0 + cc < k) ? gam[(int64_t)m * k + a0 + cc] : 0.f;
       rc[u] = (okm && a0 + cc < k) ? cm[(int64_t)m * k + a0 + cc] : 0.f;
       rgb[u] = (okm && b0 + cc < k) ? gam[(int64_t)m * k + b0 + cc] : 0.f;
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const flo
     }
   };
   fetch(0);
-  for (int m0 = 0; m0 < k; m0 += kStage) {
+  for (int m0 = 0; m0 < ky; m0 += kStage) {
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = tid + 256 * u, mm = e / kTile, cc = e % kTile;
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const flo
       sCb[mm][cc] = rcb[u];
     }
     __syncthreads();
-    if (m0 + kStage < k) fetch(m0 + kStage);
+    if (m0 + kStage < ky) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 g4 = *reinterpret_cast<const float4*>(&sG[mm][ty * 4]);
@@ -86,24 +89,28 @@ __global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const flo
       const int c = b0 + tx * 4 + j;
       if (c >= k) continue;
       w[(int64_t)a * k + c] = acc[i][j];
-      if (d_mask) d_mask[pd.c_off + (int64_t)a * k + c] = -pd.lam * gam[(int64_t)a * k + c] * cm[(int64_t)a * k + c];
     }
   }
 }
 
-// dlambda_p = -sum_ij D_ij Gamma_ij C_ij, fixed-order block reduction (one block per pair).
-__global__ void __launch_bounds__(256) adjoint_dlambda_kernel(BatchDev b, const float* c_flat, float* d_lambda,
-                                                              const float* ws) {
+// The mask gradient dD = -lambda Gamma o C (when d_mask is given) and
+// dlambda_p = -sum_ij D_ij Gamma_ij C_ij (when d_lambda is given), over the k_Y x k_X
+// entries; fixed-order block reduction (one block per pair).
+__global__ void __launch_bounds__(256) adjoint_dlambda_kernel(BatchDev b, const float* c_flat, float* d_mask,
+                                                              float* d_lambda, const float* ws) {
   __shared__ float red[256];
   const int p = blockIdx.x;
   const PairDev pd = b.pairs[p];
-  const int k = pd.k;
+  const int k = pd.k, n = b.shapes[pd.y].k * pd.k;   // the ky x k entries
   const float* gam = ws + pd.gam_off;
   const float* cm = c_flat + pd.c_off;
   const float* evx = b.shapes[pd.x].evals;
   const float* evy = b.shapes[pd.y].evals;
+  if (d_mask)
+    for (int e = threadIdx.x; e < n; e += 256) d_mask[pd.c_off + e] = -pd.lam * gam[e] * cm[e];
+  if (!d_lambda) return;
   float acc = 0.f;
-  for (int e = threadIdx.x; e < k * k; e += 256) {
+  for (int e = threadIdx.x; e < n; e += 256) {
     const int i = e / k, j = e % k;
     acc = fmaf(mask_entry(pd, evx, evy, i, j) * gam[e], cm[e], acc);
   }
@@ -116,9 +123,10 @@ __global__ void __launch_bounds__(256) adjoint_dlambda_kernel(BatchDev b, const 
   if (threadIdx.x == 0) d_lambda[p] = -red[0];
 }
 
-// Per-pair contributions:
-//   which 0: dA_x = Gamma^T A_y - W A_x   (into sx_off)
-//   which 1: dA_y = Gamma A_x             (into sy_off)
+// Per-pair contributions (Gamma is k_Y x k_X, W k_X x k_X):
+//   which 0: dA_x = Gamma^T A_y - W A_x   (k_X x d, into sx_off; the two products share
+//            one loop over max(k_X, k_Y), each operand zero past its own length)
+//   which 1: dA_y = Gamma A_x             (k_Y x d, into sy_off)
 __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float* a_flat, float* ws) {
   // both operands stored m-major in shared memory, so that a thread's 4 rows and 4
   // columns of one step are two float4 reads
@@ -127,11 +135,13 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
   __shared__ __align__(16) float sX2[kStage][kTile + 4];
   __shared__ __align__(16) float sY2[kStage][kTile + 4];
   const PairDev pd = b.pairs[blockIdx.z];
-  const int k = pd.k, d = pd.d;
-  const int ntf = (d + kTile - 1) / kTile, nta = (k + kTile - 1) / kTile;
+  const int k = pd.k, ky = b.shapes[pd.y].k, d = pd.d;
+  const int which = blockIdx.y;
+  const int rows = which == 0 ? k : ky;                    // rows of the contribution
+  const int mlen = which == 0 ? max(k, ky) : k;            // length of the reduction
+  const int ntf = (d + kTile - 1) / kTile, nta = (rows + kTile - 1) / kTile;
   if ((int)blockIdx.x >= ntf * nta) return;
   const int a0 = (blockIdx.x / ntf) * kTile, f0 = (blockIdx.x % ntf) * kTile;
-  const int which = blockIdx.y;
   const float* gam = ws + pd.gam_off;
   const float* w = ws + pd.w_off;
   const float* ax = a_flat + b.shapes[pd.x].a_off;
@@ -147,23 +157,26 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
       {
         // Gamma^T[a][m] = Gamma[m][a]: consecutive threads take consecutive a (coalesced)
         const int aa = e % kTile, mm = e / kTile, a = a0 + aa, m = m0 + mm;
-        r1[u] = (which == 0 && a < k && m < k) ? gam[(int64_t)m * k + a] : 0.f;
+        r1[u] = (which == 0 && a < k && m < ky) ? gam[(int64_t)m * k + a] : 0.f;
       }
       {
+        // which 0: -W[a][m] (a, m < k_X); which 1: Gamma[a][m] (a < k_Y, m < k_X)
         const int aa = e / kStage, mm = e % kStage, a = a0 + aa, m = m0 + mm;
-        const bool ok = a < k && m < k;
-        r2[u] = !ok ? 0.f : (which == 0 ? -w[(int64_t)a * k + m] : gam[(int64_t)a * k + m]);   // -W[a][m] | Gamma[a][m]
+        const bool ok = a < rows && m < k;
+        r2[u] = !ok ? 0.f : (which == 0 ? -w[(int64_t)a * k + m] : gam[(int64_t)a * k + m]);
       }
       {
+        // which 0: A_y[m] (m < k_Y) beside A_x[m] (m < k_X); which 1: A_x[m] (m < k_X)
         const int mm = e / kTile, ff = e % kTile, m = m0 + mm, f = f0 + ff;
-        const bool ok = m < k && f < d;
-        r3[u] = ok ? (which == 0 ? ay : ax)[(int64_t)m * d + f] : 0.f;
-        r4[u] = (ok && which == 0) ? ax[(int64_t)m * d + f] : 0.f;
+        const bool okf = f < d;
+        r3[u] = which == 0 ? ((okf && m < ky) ? ay[(int64_t)m * d + f] : 0.f)
+                           : ((okf && m < k) ? ax[(int64_t)m * d + f] : 0.f);
+        r4[u] = (which == 0 && okf && m < k) ? ax[(int64_t)m * d + f] : 0.f;
       }
     }
   };
   fetch(0);
-  for (int m0 = 0; m0 < k; m0 += kStage) {
+  for (int m0 = 0; m0 < mlen; m0 += kStage) {
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = tid + 256 * u;
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
       if (which == 0) sY2[e / kTile][e % kTile] = r4[u];
     }
     __syncthreads();
-    if (m0 + kStage < k) fetch(m0 + kStage);
+    if (m0 + kStage < mlen) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(256) adjoint_da_kernel(BatchDev b, const float
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int a = a0 + ty * 4 + i;
-    if (a >= k) continue;
+    if (a >= rows) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int f = f0 + tx * 4 + j;
@@ -252,10 +265,12 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
   __shared__ float red[256];
   const int p = blockIdx.z;
   const PairDev pd = b.pairs[p];
-  const int k = pd.k;
-  const int nt = (k + kTile - 1) / kTile;
-  if ((int)blockIdx.x >= nt * nt) return;
-  const int a0 = (blockIdx.x / nt) * kTile, b0 = (blockIdx.x % nt) * kTile;
+  const int k = pd.k, ky = b.shapes[pd.y].k;   // C is ky x k, E = C C^T - I is ky x ky
+  // tiles over ky rows and max(ky, k) columns: E where the column is < ky, the
+  // ||C - C_gt||^2 term where it is < k
+  const int nta = (ky + kTile - 1) / kTile, ntb = (max(ky, k) + kTile - 1) / kTile;
+  if ((int)blockIdx.x >= nta * ntb) return;
+  const int a0 = (blockIdx.x / ntb) * kTile, b0 = (blockIdx.x % ntb) * kTile;
   const float* c = c_flat + pd.c_off;
   const float* gt = gt_flat + pd.c_off;
   float* e = ws + pd.e_off;
@@ -268,8 +283,8 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
     for (int u = 0; u < kPer; ++u) {
       // rows of C read in 16-element segments (consecutive threads, consecutive m)
       const int q = tid + 256 * u, r = q / kStage, mm = q % kStage;
-      rx[u] = (a0 + r < k && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
-      ry[u] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
+      rx[u] = (a0 + r < ky && m0 + mm < k) ? c[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+      ry[u] = (b0 + r < ky && m0 + mm < k) ? c[(int64_t)(b0 + r) * k + m0 + mm] : 0.f;
     }
   };
   fetch(0);
@@ -298,15 +313,19 @@ __global__ void __launch_bounds__(256) loss_e_kernel(BatchDev b, const float* c_
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int a = a0 + ty * 4 + i;
-    if (a >= k) continue;
+    if (a >= ky) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int bb = b0 + tx * 4 + j;
-      if (bb >= k) continue;
-      const float v = acc[i][j] - (a == bb ? 1.f : 0.f);
-      e[(int64_t)a * k + bb] = v;
-      const float r = c[(int64_t)a * k + bb] - gt[(int64_t)a * k + bb];
-      part = fmaf(v, v, fmaf(r, r, part));
+      if (bb < k) {
+        const float r = c[(int64_t)a * k + bb] - gt[(int64_t)a * k + bb];
+        part = fmaf(r, r, part);
+      }
+      if (bb < ky) {
+        const float v = acc[i][j] - (a == bb ? 1.f : 0.f);
+        e[(int64_t)a * ky + bb] = v;
+        part = fmaf(v, v, part);
+      }
     }
   }
   red[tid] = part;
@@ -325,16 +344,19 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
   __shared__ __align__(16) float sY[kStage][kTile + 4];   // C[m][b]
   const int p = blockIdx.z;
   const PairDev pd = b.pairs[p];
-  const int k = pd.k;
-  const int nt = (k + kTile - 1) / kTile;
-  if ((int)blockIdx.x >= nt * nt) return;
+  const int k = pd.k, ky = b.shapes[pd.y].k;
+  const int nta = (ky + kTile - 1) / kTile, ntb = (k + kTile - 1) / kTile;
   if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
+    // the partial sums of loss_e's tiles, in tile order
+    const int nte = nta * ((max(ky, k) + kTile - 1) / kTile);
     float total = 0.f;
-    for (int t = 0; t < nt * nt; ++t) total += partial[(int64_t)p * kMaxLossTiles + t];
+    for (int t = 0; t < nte; ++t) total += partial[(int64_t)p * kMaxLossTiles + t];
     loss[p] = total;
   }
   if (d_c == nullptr) return;
-  const int a0 = (blockIdx.x / nt) * kTile, b0 = (blockIdx.x % nt) * kTile;
+  // dC = 4 E C + 2 (C - C_gt): ky x k tiles, reduction over ky
+  if ((int)blockIdx.x >= nta * ntb) return;
+  const int a0 = (blockIdx.x / ntb) * kTile, b0 = (blockIdx.x % ntb) * kTile;
   const float* c = c_flat + pd.c_off;
   const float* gt = gt_flat + pd.c_off;
   const float* e = ws + pd.e_off;
@@ -348,16 +370,16 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
       const int q = tid + 256 * u;
       {
         const int r = q / kStage, mm = q % kStage;
-        rx[u] = (a0 + r < k && m0 + mm < k) ? e[(int64_t)(a0 + r) * k + m0 + mm] : 0.f;
+        rx[u] = (a0 + r < ky && m0 + mm < ky) ? e[(int64_t)(a0 + r) * ky + m0 + mm] : 0.f;
       }
       {
         const int mm = q / kTile, r = q % kTile;
-        ry[u] = (b0 + r < k && m0 + mm < k) ? c[(int64_t)(m0 + mm) * k + b0 + r] : 0.f;
+        ry[u] = (b0 + r < k && m0 + mm < ky) ? c[(int64_t)(m0 + mm) * k + b0 + r] : 0.f;
       }
     }
   };
   fetch(0);
-  for (int m0 = 0; m0 < k; m0 += kStage) {
+  for (int m0 = 0; m0 < ky; m0 += kStage) {
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int q = tid + 256 * u;
@@ -365,7 +387,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
       sY[q / kTile][q % kTile] = ry[u];
     }
     __syncthreads();
-    if (m0 + kStage < k) fetch(m0 + kStage);
+    if (m0 + kStage < ky) fetch(m0 + kStage);
 #pragma unroll
     for (int mm = 0; mm < kStage; ++mm) {
       const float4 xa = *reinterpret_cast<const float4*>(&sX[mm][ty * 4]);
@@ -381,7 +403,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(BatchDev b, const float*
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int a = a0 + ty * 4 + i;
-    if (a >= k) continue;
+    if (a >= ky) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int bb = b0 + tx * 4 + j;
@@ -403,11 +425,11 @@ cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const 
                                  float* d_mask, float* d_lambda, float* ws, cudaStream_t st) {
   if (b.n_pairs <= 0) return cudaSuccess;
   const int ntk = (max_k + kTile - 1) / kTile, ntd = (max_d + kTile - 1) / kTile;
-  adjoint_w_kernel<<<dim3(ntk * ntk, 1, b.n_pairs), 256, 0, st>>>(b, c, d_mask, ws);
+  adjoint_w_kernel<<<dim3(ntk * ntk, 1, b.n_pairs), 256, 0, st>>>(b, c, ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (d_lambda) {
-    adjoint_dlambda_kernel<<<b.n_pairs, 256, 0, st>>>(b, c, d_lambda, ws);
+  if (d_lambda || d_mask) {
+    adjoint_dlambda_kernel<<<b.n_pairs, 256, 0, st>>>(b, c, d_mask, d_lambda, ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   adjoint_da_kernel<<<dim3(ntk * ntd, 2, b.n_pairs), 256, 0, st>>>(b, a, ws);

@@ -132,8 +132,13 @@ def test_plan_rejects_bad_pairs(lib, pair, code):
     assert rc == code
 
 
-def test_plan_rejects_k_mismatch_and_missing_evals(lib):
-    rc, _ = _plan(lib, [dict(n=100, k=8, d=16), dict(n=100, k=9, d=16)], [(0, 1, 1e-3)])
+def test_plan_rectangular_maps_and_rejections(lib):
+    """Bases of different sizes give a k_y x k_x map; a feature-width mismatch and a
+    missing eigenvalue array (without a mask) are rejected."""
+    rc, sz = _plan(lib, [dict(n=100, k=8, d=16), dict(n=100, k=9, d=16)], [(0, 1, 1e-3), (1, 0, 1e-3)])
+    assert rc == 0
+    assert sz.c_floats == 9 * 8 + 8 * 9
+    rc, _ = _plan(lib, [dict(n=100, k=8, d=16), dict(n=100, k=8, d=32)], [(0, 1, 1e-3)])
     assert rc == 1
     rc, _ = _plan(lib, [dict(n=100, k=8, d=16, evals=None), dict(n=100, k=8, d=16)], [(0, 1, 1e-3)])
     assert rc == 1

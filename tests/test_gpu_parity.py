@@ -192,6 +192,37 @@ def _oracle_backward(wl):
     return shapes, pairs, fwd, losses, dcs, g
 
 
+@pytest.mark.parametrize("feat_dtype,use_saved", [("fp32", True), ("fp32", False), ("bf16", True)])
+def test_rectangular_maps(feat_dtype, use_saved):
+    """Pairs whose bases differ in size (C is k_Y x k_X: k_Y row systems of size k_X):
+    k_Y above and below k_X, system sizes on both sides of the 64/128/256 block classes,
+    the double-float Gram (k_X >= 200), an explicit k_Y x k_X mask, a shape shared by a
+    rectangular and a square pair. Forward and backward against the oracle."""
+    rng = np.random.default_rng(29)
+    ks = [30, 50, 60, 20, 130, 100, 210, 70, 40]
+    shapes = [_shape(rng, 600 + 37 * i, k, 448, feat_dtype) for i, k in enumerate(ks)]
+    pairs = [synth.Pair(x=0, y=1, lam=1e-2), synth.Pair(x=2, y=3, lam=1e-3), synth.Pair(x=4, y=5, lam=1e-2),
+             synth.Pair(x=6, y=7, lam=1e-3), synth.Pair(x=1, y=8, lam=1e-2), synth.Pair(x=8, y=8, lam=1e-2)]
+    mrng = np.random.default_rng(3)
+    pairs[1].mask = mrng.uniform(0.0, 50.0, (ks[3], ks[2])).astype(np.float32)
+    for i, p in enumerate(pairs):
+        p.c_gt = (mrng.standard_normal((ks[p.y], ks[p.x])) / np.sqrt(ks[p.x])).astype(np.float32)
+    wl = synth.Workload("rect", shapes, pairs, feat_dtype)
+    out = _gpu_backward(wl, use_saved=use_saved)
+    shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
+    tol, gtol = TOL[feat_dtype], GTOL[feat_dtype]
+    assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert out["C"][p].shape == (ks[wl.pairs[p].y], ks[wl.pairs[p].x])
+        assert rel_fro(out["C"][p], fwd["C"][p]) <= tol
+        assert abs(out["loss"][p] - losses[p]) <= tol * max(1.0, abs(losses[p]))
+        assert rel_fro(out["dD"][p], g["pair"][p]["dD"]) <= gtol
+        assert abs(out["dlam"][p] - g["pair"][p]["dlam"]) <= gtol * max(1.0, abs(g["pair"][p]["dlam"]))
+    for s_ in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s_], g["dA"][s_]) <= gtol
+        assert rel_fro(out["dF"][s_], g["dF"][s_]) <= gtol
+
+
 @pytest.mark.parametrize("use_saved,adj_ir", [(True, 1), (False, 1), (True, 2)])
 def test_backward_with_adjoint_refinement(use_saved, adj_ir):
     """Refinement steps in the adjoint row solves (off by default): k below and above the
