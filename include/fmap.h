@@ -224,6 +224,26 @@ enum fmap_kernel_kind {
 FMAP_API int32_t fmap_batch_set_timing(fmap_batch* batch, int32_t enable);
 FMAP_API int32_t fmap_batch_read_timing(fmap_batch* batch, float* ms, int32_t* launches, int32_t n_kinds);
 
+/* ---- Overlap-prediction metrics (Sec. "Overlap Prediction Metrics") ---------------
+ * For segments s = 0 .. n_segments-1 of flat per-vertex arrays (the vertices of one
+ * shape, or of one pair's predicted overlap region): a vertex is predicted overlapping
+ * when scores[v] > threshold (FP32 comparison), and is truly overlapping when
+ * labels[v] != 0. Counts, exact:
+ *   counts[4 s + 0..3] = TP, FP, FN, TN   (device int64[4 n_segments])
+ * and, when metrics is not NULL, in FP64 (device double[7 n_segments]):
+ *   metrics[7 s + 0..6] = IoU TP/(TP+FP+FN), balanced accuracy (recall + specificity)/2,
+ *   accuracy (TP+TN)/n, precision TP/(TP+FP), recall TP/(TP+FN), specificity
+ *   TN/(TN+FP), F1 2TP/(2TP+FP+FN); a ratio whose denominator is 0 is NaN.
+ *   scores       device float[seg_offsets[n_segments]] (any values; NaN never exceeds)
+ *   labels       device uint8[seg_offsets[n_segments]]
+ *   seg_offsets  device int64[n_segments + 1], non-decreasing, seg_offsets[0] >= 0;
+ *                segment s is [seg_offsets[s], seg_offsets[s+1])
+ *   max_segment_len  >= the longest segment (vertices past it are not counted)
+ * n_segments <= 65535 (UNSUPPORTED above). Enqueues on stream; no allocation. */
+FMAP_API int32_t fmap_overlap_metrics(const float* scores, const uint8_t* labels, const int64_t* seg_offsets,
+                                      int32_t n_segments, int64_t max_segment_len, float threshold,
+                                      int64_t* counts, double* metrics, void* stream);
+
 /* ---- Allocation-free single-pair solve (no counterpart in the paper) ---------------
  * For callers that cannot allocate device memory when they solve (a memory pool they
  * do not own is frozen, a real-time thread must not enter the allocator, or a host

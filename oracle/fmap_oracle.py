@@ -28,10 +28,16 @@ The backward pass (not in the paper) is the adjoint of Eq. 5 derived by hand:
 gamma_i = S_i^{-1} dL/dc_i, dB = Gamma A, dA = Gamma^T B - (Gamma^T C + C^T Gamma) A,
 dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C), dF = M Phi dA.
 
+Overlap metrics (Sec. "Overlap Prediction Metrics"): confusion counts of a thresholded
+per-vertex overlap prediction against binary labels, and IoU, accuracy, precision,
+recall, specificity, F1 and balanced accuracy from them.
+
 Parity pins: every function here is checked against something other than itself
 in tests/test_oracle_pins.py (Kronecker k^2 x k^2 solve, lambda = 0 closed form,
 identity case, energy minimality, exact rational solve, Moore-Penrose inverse,
-finite differences, LAPACK). No function is "parity unpinned".
+finite differences, LAPACK; for the overlap metrics the paper's closed forms for the
+Zeros / Ones / Random predictors and brute-force counting). No function is "parity
+unpinned".
 """
 from __future__ import annotations
 
@@ -223,3 +229,33 @@ def backward_batch(shapes, pairs, fwd, d_c_list):
         extra.append(g)
     d_f = [project_backward(s["phi"], s["mass"], da) for s, da in zip(shapes, d_a)]
     return dict(dA=d_a, dF=d_f, pair=extra)
+
+
+# --------------------------------------------------------------------------
+# Overlap-prediction metrics (Sec. "Overlap Prediction Metrics")
+# --------------------------------------------------------------------------
+def overlap_counts(scores, labels, threshold=0.5):
+    """(TP, FP, FN, TN) of one segment: a vertex is predicted overlapping when its FP32
+    score exceeds the FP32 threshold, truly overlapping when its label is nonzero."""
+    pred = np.asarray(scores, dtype=np.float32) > np.float32(threshold)
+    lab = np.asarray(labels) != 0
+    tp = int(np.count_nonzero(pred & lab))
+    fp = int(np.count_nonzero(pred & ~lab))
+    fn = int(np.count_nonzero(~pred & lab))
+    tn = int(np.count_nonzero(~pred & ~lab))
+    return tp, fp, fn, tn
+
+
+def _ratio(num, den):
+    return num / den if den > 0 else float("nan")
+
+
+def overlap_metrics(tp, fp, fn, tn):
+    """IoU, balanced accuracy, accuracy, precision, recall, specificity, F1 (FP64); a
+    ratio with a zero denominator is NaN. Balanced accuracy is the mean of sensitivity
+    TP/(TP+FN) and specificity TN/(TN+FP)."""
+    tp, fp, fn, tn = float(tp), float(fp), float(fn), float(tn)
+    recall = _ratio(tp, tp + fn)
+    spec = _ratio(tn, tn + fp)
+    return (_ratio(tp, tp + fp + fn), (recall + spec) * 0.5, _ratio(tp + tn, tp + fp + fn + tn),
+            _ratio(tp, tp + fp), recall, spec, _ratio(2.0 * tp, 2.0 * tp + fp + fn))

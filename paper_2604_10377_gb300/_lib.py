@@ -86,6 +86,8 @@ _PROTOS = {
     "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),
     "fmap_solve_pair_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                           c_float, c_int32, c_void_p, c_void_p, c_void_p]),
+    "fmap_overlap_metrics": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_float, c_void_p, c_void_p,
+                                       c_void_p]),
 }
 
 KIND_NAMES = ["project", "project_reduce", "gram", "solve", "adj_solve", "adj_gemm", "gather", "project_bwd",

@@ -389,6 +389,37 @@ class UploadPipeline:
         self._cur = None
 
 
+OVERLAP_METRICS = ("iou", "balanced_accuracy", "accuracy", "precision", "recall", "specificity", "f1")
+
+
+def overlap_metrics(scores: torch.Tensor, labels: torch.Tensor, seg_offsets, threshold: float = 0.5,
+                    with_metrics: bool = True):
+    """Overlap-prediction counts and metrics per segment (fmap_overlap_metrics).
+
+    scores: device float32 (n,); labels: device uint8 (n,), nonzero = truly overlapping;
+    seg_offsets: host sequence of n_seg + 1 non-decreasing offsets into them. Returns
+    (counts int64 (n_seg, 4) = TP, FP, FN, TN, metrics float64 (n_seg, 7) in the order of
+    OVERLAP_METRICS, or None), both on the scores' device; the call only enqueues."""
+    if scores.dtype != torch.float32 or labels.dtype != torch.uint8:
+        raise TypeError("scores must be float32 and labels uint8")
+    if not (scores.is_contiguous() and labels.is_contiguous()) or scores.numel() != labels.numel():
+        raise ValueError("scores and labels must be contiguous and of equal length")
+    off = np.asarray(seg_offsets, dtype=np.int64)
+    n_seg = len(off) - 1
+    if n_seg < 0 or (n_seg > 0 and (off[0] < 0 or np.any(np.diff(off) < 0) or off[-1] > scores.numel())):
+        raise ValueError("seg_offsets must be non-decreasing offsets within the arrays")
+    dev = scores.device
+    counts = torch.empty((max(n_seg, 1), 4), dtype=torch.int64, device=dev)
+    metrics = torch.empty((max(n_seg, 1), 7), dtype=torch.float64, device=dev) if with_metrics else None
+    off_dev = torch.from_numpy(off).to(dev)
+    max_len = int(np.max(np.diff(off))) if n_seg > 0 else 0
+    check(_lib.lib().fmap_overlap_metrics(_ptr(scores), _ptr(labels), _ptr(off_dev), n_seg, max_len,
+                                          float(threshold), _ptr(counts), _ptr(metrics), _stream(dev)),
+          "fmap_overlap_metrics")
+    counts = counts[:n_seg]
+    return counts, (metrics[:n_seg] if metrics is not None else None)
+
+
 def batch_from_workload(wl, device="cuda:0", with_grad=True, **kw) -> FmapBatch:
     """Allocate a batch for a synth.Workload and upload its inputs."""
     lay = BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)

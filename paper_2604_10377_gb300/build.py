@@ -24,6 +24,7 @@ SOURCES = [
     "k_gram.cu",
     "k_solve.cu",
     "k_chol.cu",
+    "k_overlap.cu",
     "fmap_noalloc.cu",
 ]
 

@@ -583,6 +583,12 @@ struct TimedScope {
 
 }  // namespace
 
+namespace fmap {
+// defined in k_overlap.cu
+cudaError_t launch_overlap_metrics(const float* scores, const uint8_t* labels, const int64_t* seg_off, int n_seg,
+                                   int64_t max_len, float thr, int64_t* counts, double* metrics, cudaStream_t st);
+}  // namespace fmap
+
 extern "C" {
 
 const char* fmap_version(void) { return "fmap-gb300 0.1 (sm_103a)"; }
@@ -602,6 +608,19 @@ const char* fmap_error_string(int32_t code) {
 }
 
 const char* fmap_last_cuda_error(void) { return g_last_cuda_error; }
+
+
+int32_t fmap_overlap_metrics(const float* scores, const uint8_t* labels, const int64_t* seg_offsets,
+                             int32_t n_segments, int64_t max_segment_len, float threshold, int64_t* counts,
+                             double* metrics, void* stream) {
+  if (n_segments < 0 || max_segment_len < 0 || !std::isfinite(threshold)) return FMAP_ERR_INVALID_ARG;
+  if (n_segments == 0) return FMAP_OK;
+  if (!seg_offsets || !counts || (max_segment_len > 0 && (!scores || !labels))) return FMAP_ERR_INVALID_ARG;
+  if (n_segments > 65535) return FMAP_ERR_UNSUPPORTED;
+  const cudaError_t e = launch_overlap_metrics(scores, labels, seg_offsets, n_segments, max_segment_len, threshold,
+                                               counts, metrics, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FMAP_OK : cuda_fail(e, "overlap metrics");
+}
 
 int32_t fmap_default_options(fmap_options* opt) {
   if (!opt) return FMAP_ERR_INVALID_ARG;

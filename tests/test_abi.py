@@ -218,3 +218,16 @@ def test_oracle_and_cuda_path_share_no_code():
     for path in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
         text = open(path).read()
         assert "paper_2604_10377_gb300" not in text and "libfmap" not in text, path
+
+
+def test_overlap_metrics_argument_checks(lib):
+    """Argument errors return before any launch (no GPU needed)."""
+    fake = ctypes.c_void_p(0x10000)
+    assert lib.fmap_overlap_metrics(None, None, None, 0, 0, 0.5, None, None, None) == 0
+    assert lib.fmap_overlap_metrics(fake, fake, fake, -1, 10, 0.5, fake, None, None) == 1
+    assert lib.fmap_overlap_metrics(fake, fake, fake, 3, -1, 0.5, fake, None, None) == 1
+    assert lib.fmap_overlap_metrics(fake, fake, None, 3, 10, 0.5, fake, None, None) == 1
+    assert lib.fmap_overlap_metrics(fake, fake, fake, 3, 10, 0.5, None, None, None) == 1
+    assert lib.fmap_overlap_metrics(None, fake, fake, 3, 10, 0.5, fake, None, None) == 1
+    assert lib.fmap_overlap_metrics(fake, fake, fake, 3, 10, float("nan"), fake, None, None) == 1
+    assert lib.fmap_overlap_metrics(fake, fake, fake, 70000, 10, 0.5, fake, None, None) == 2

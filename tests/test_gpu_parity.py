@@ -483,3 +483,36 @@ def test_upload_pipeline_steps_match_serial_steps():
     pipe.prefetch(hosts[1])
     with pytest.raises(RuntimeError):
         pipe.prefetch(hosts[2])
+
+
+def test_overlap_metrics_against_oracle():
+    """Overlap counts (exact) and metrics (FP64, bitwise) per segment against the oracle:
+    empty and one-vertex segments, lengths around the 4096-vertex block chunk, a long
+    segment, scores equal to the threshold and NaN scores, overlap ratios from 0 to 1."""
+    from paper_2604_10377_gb300 import api
+    rng = np.random.default_rng(41)
+    lens = [0, 1, 5, 4095, 4096, 4097, 250000, 33, 1000, 1000, 12288]
+    ratios = [0.5, 0.3, 0.0, 0.02, 0.5, 0.98, 0.25, 1.0, 0.5, 0.0, 0.7]
+    scores, labels = [], []
+    for n, r in zip(lens, ratios):
+        sc = rng.uniform(0, 1, n).astype(np.float32)
+        if n > 10:
+            sc[rng.integers(n, size=3)] = np.float32(0.25)
+            sc[rng.integers(n, size=2)] = np.nan
+        scores.append(sc)
+        labels.append((rng.uniform(0, 1, n) < r).astype(np.uint8))
+    scores[9][:] = 0.0                       # no predicted and no true positives: NaN ratios
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    s_all, l_all = np.concatenate(scores), np.concatenate(labels)
+    counts, metrics = api.overlap_metrics(torch.from_numpy(s_all).cuda(), torch.from_numpy(l_all).cuda(), off,
+                                          threshold=0.25)
+    counts, metrics = counts.cpu().numpy(), metrics.cpu().numpy()
+    for i in range(len(lens)):
+        c = orc.overlap_counts(s_all[off[i]:off[i + 1]], l_all[off[i]:off[i + 1]], threshold=0.25)
+        assert tuple(int(x) for x in counts[i]) == c, (i, counts[i], c)
+        m = np.array(orc.overlap_metrics(*c))
+        assert np.array_equal(np.isnan(m), np.isnan(metrics[i])), (i, m, metrics[i])
+        ok = ~np.isnan(m)
+        assert np.array_equal(m[ok], metrics[i][ok]), (i, m, metrics[i])
+    c0, m0 = api.overlap_metrics(torch.from_numpy(s_all).cuda(), torch.from_numpy(l_all).cuda(), [0], 0.5)
+    assert c0.shape == (0, 4) and m0.shape == (0, 7)

@@ -413,3 +413,76 @@ def test_planted_mistakes(monkeypatch):
         monkeypatch.setattr(orc, attr, fn)
         assert caught(), f"planted mistake not caught: {name}"
         monkeypatch.undo()
+
+
+# ---------------------------------------------------------------- overlap metrics
+@pytest.mark.parametrize("r", [0.05, 0.3, 0.5, 0.95])
+def test_overlap_degenerate_predictors_closed_forms(r):
+    """The paper's three degenerate predictors on N vertices with overlap ratio r:
+    Zeros (TP=0, FP=0, FN=rN, TN=(1-r)N), Ones (TP=rN, FP=(1-r)N, FN=TN=0) and Random
+    (half of each class predicted positive). Balanced accuracy is 1/2 for all three; IoU
+    is 0, r and r/(1+r)."""
+    n = 2000
+    npos = int(round(r * n))
+    labels = np.zeros(n, np.uint8)
+    labels[np.random.default_rng(1).permutation(n)[:npos]] = 1
+    pos, neg = np.flatnonzero(labels), np.flatnonzero(labels == 0)
+    zeros = np.zeros(n, np.float32)
+    ones = np.ones(n, np.float32)
+    half = np.zeros(n, np.float32)
+    half[pos[: len(pos) // 2]] = 1.0
+    half[neg[: len(neg) // 2]] = 1.0
+    tp, fp, fn, tn = orc.overlap_counts(zeros, labels)
+    assert (tp, fp, fn, tn) == (0, 0, npos, n - npos)
+    m = orc.overlap_metrics(tp, fp, fn, tn)
+    assert m[0] == 0.0 and m[1] == 0.5
+    tp, fp, fn, tn = orc.overlap_counts(ones, labels)
+    assert (tp, fp, fn, tn) == (npos, n - npos, 0, 0)
+    m = orc.overlap_metrics(tp, fp, fn, tn)
+    assert m[0] == pytest.approx(npos / n, abs=0) and m[1] == 0.5
+    tp, fp, fn, tn = orc.overlap_counts(half, labels)
+    assert (tp, fp, fn, tn) == (npos // 2, (n - npos) // 2, npos - npos // 2, (n - npos) - (n - npos) // 2)
+    m = orc.overlap_metrics(tp, fp, fn, tn)
+    assert m[1] == pytest.approx(0.5, abs=1e-3)
+    assert m[0] == pytest.approx(r / (1 + r), abs=2e-3)
+
+
+def test_overlap_counts_bruteforce_and_definitions():
+    """Counts by explicit loops; metrics by their textbook definitions; strict threshold
+    (a score equal to it is negative), NaN scores never positive; label/prediction
+    complement swaps TP<->TN and FP<->FN and keeps the balanced accuracy."""
+    rng = np.random.default_rng(9)
+    for trial in range(20):
+        n = int(rng.integers(1, 60))
+        scores = rng.uniform(0, 1, n).astype(np.float32)
+        scores[rng.integers(n)] = np.float32(0.5)
+        if n > 3:
+            scores[2] = np.nan
+        labels = (rng.uniform(0, 1, n) < rng.uniform(0.1, 0.9)).astype(np.uint8)
+        tp = fp = fn = tn = 0
+        for sc, lb in zip(scores.tolist(), labels.tolist()):
+            p = (sc == sc) and sc > 0.5
+            if p and lb: tp += 1
+            elif p: fp += 1
+            elif lb: fn += 1
+            else: tn += 1
+        assert orc.overlap_counts(scores, labels) == (tp, fp, fn, tn)
+        m = orc.overlap_metrics(tp, fp, fn, tn)
+        if tp + fp + fn:
+            assert m[0] == tp / (tp + fp + fn)
+        if tp + fn and tn + fp:
+            assert m[1] == pytest.approx(0.5 * (tp / (tp + fn) + tn / (tn + fp)), rel=1e-15)
+        assert m[2] == (tp + tn) / n
+        # complement: predictions and labels flipped (NaN scores stay negative, so keep finite ones)
+        fin = ~np.isnan(scores)
+        c = orc.overlap_counts(scores[fin], labels[fin])
+        cc = orc.overlap_counts(np.where(scores[fin] > 0.5, 0.0, 1.0).astype(np.float32), 1 - labels[fin])
+        assert cc == (c[3], c[2], c[1], c[0])
+        mc, mm = orc.overlap_metrics(*cc), orc.overlap_metrics(*c)
+        assert (np.isnan(mc[1]) and np.isnan(mm[1])) or mc[1] == pytest.approx(mm[1], rel=1e-15)
+
+
+def test_overlap_undefined_ratios_are_nan():
+    m = orc.overlap_metrics(0, 0, 0, 10)       # no positives predicted or present
+    assert np.isnan(m[0]) and np.isnan(m[3]) and np.isnan(m[4]) and np.isnan(m[6])
+    assert m[2] == 1.0 and m[5] == 1.0 and np.isnan(m[1])
