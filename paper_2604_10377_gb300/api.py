@@ -402,6 +402,8 @@ def overlap_metrics(scores: torch.Tensor, labels: torch.Tensor, seg_offsets, thr
     OVERLAP_METRICS, or None), both on the scores' device; the call only enqueues."""
     if scores.dtype != torch.float32 or labels.dtype != torch.uint8:
         raise TypeError("scores must be float32 and labels uint8")
+    if not (scores.is_cuda and labels.is_cuda) or scores.device != labels.device:
+        raise ValueError("scores and labels must be CUDA tensors on the same device")
     if not (scores.is_contiguous() and labels.is_contiguous()) or scores.numel() != labels.numel():
         raise ValueError("scores and labels must be contiguous and of equal length")
     off = np.asarray(seg_offsets, dtype=np.int64)

@@ -231,3 +231,17 @@ def test_overlap_metrics_argument_checks(lib):
     assert lib.fmap_overlap_metrics(None, fake, fake, 3, 10, 0.5, fake, None, None) == 1
     assert lib.fmap_overlap_metrics(fake, fake, fake, 3, 10, float("nan"), fake, None, None) == 1
     assert lib.fmap_overlap_metrics(fake, fake, fake, 70000, 10, 0.5, fake, None, None) == 2
+
+
+def test_overlap_metrics_python_checks():
+    """api.overlap_metrics rejects host tensors, wrong dtypes and bad offsets before any call."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_10377_gb300 import api
+    s = torch.zeros(10, dtype=torch.float32)
+    l = torch.zeros(10, dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        api.overlap_metrics(s, l, [0, 10])                  # host tensors
+    with pytest.raises(TypeError):
+        api.overlap_metrics(s.double(), l, [0, 10])
+    with pytest.raises(TypeError):
+        api.overlap_metrics(s, l.int(), [0, 10])
