@@ -11,15 +11,16 @@ from __future__ import annotations
 from typing import List, Sequence, Tuple
 
 
-def pair_cost(n_x: int, n_y: int, k: int, d: int, feat_bytes: int) -> float:
+def pair_cost(n_x: int, n_y: int, k: int, d: int, feat_bytes: int, k_y: int = None) -> float:
     """Estimated GPU time of one pair's forward+backward step, in microseconds:
     the bytes the projections stream (basis, mass and features of both shapes,
     read forward and backward, feature gradients written) at ~6.5 TB/s plus the
-    row-wise solves (k systems of size k, O(k^4 / 3) flops forward and adjoint)
-    at ~6 TFLOP/s. Only the ratio between pairs matters."""
-    n = n_x + n_y
-    stream = n * (2 * 4 * k + 2 * 4 + 3 * feat_bytes * d)
-    solve = 2.0 * k ** 4 / 3.0
+    row-wise solves (k_y systems of size k = k_x, O(k_y k^3 / 3) flops forward and
+    adjoint) at ~6 TFLOP/s. k_y defaults to k (square maps). Only the ratio between
+    pairs matters."""
+    ky = k if k_y is None else k_y
+    stream = n_x * (2 * 4 * k + 2 * 4 + 3 * feat_bytes * d) + n_y * (2 * 4 * ky + 2 * 4 + 3 * feat_bytes * d)
+    solve = 2.0 * ky * k ** 3 / 3.0
     return stream / 6.5e6 + solve / 6.0e6
 
 

@@ -126,3 +126,14 @@ def test_two_gloo_ranks_shard_without_exchange(tmp_path):
         value, ms_max, total = o["tp"]
         assert ms_max == 20.0 and total == float(len(wl.pairs))
         assert abs(value - len(wl.pairs) / 0.020) < 1e-9
+
+
+def test_pair_cost_rectangular():
+    """k_y systems of size k_x: the solve term scales with k_y k_x^3 and each shape streams
+    its own basis; the square case is unchanged."""
+    from paper_2604_10377_gb300 import shard
+    sq = shard.pair_cost(1000, 2000, 50, 128, 2)
+    assert shard.pair_cost(1000, 2000, 50, 128, 2, k_y=50) == sq
+    assert shard.pair_cost(1000, 2000, 50, 128, 2, k_y=100) > sq
+    # solve term only (no vertices): ratio k_y / k_x
+    assert abs(shard.pair_cost(0, 0, 40, 16, 2, k_y=80) / shard.pair_cost(0, 0, 40, 16, 2) - 2.0) < 1e-12
