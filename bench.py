@@ -155,16 +155,17 @@ def algorithmic_work(wl, ir_steps, saved_k_max):
     solve_flops, adj_flops, loss_flops = 0.0, 0.0, 0.0
     solve_bytes, adj_bytes = 0, 0
     for p in wl.pairs:
-        k, d = wl.shapes[p.x].k, wl.shapes[p.x].d
+        # C is ky x k: ky row systems of size k (square maps: ky == k)
+        k, ky = wl.shapes[p.x].k, wl.shapes[p.y].k
         kp = (k + 7) // 8 * 8
         q = kp // 8
-        fac = 4 * k * (32 * q * (q + 2) + 64 * q) if k <= saved_k_max else 0
-        solve_flops += k ** 4 / 3.0 + (2.0 + 4.0 * ir_steps) * k ** 3
-        adj_flops += (0.0 if k <= saved_k_max else k ** 4 / 3.0) + 2.0 * k ** 3
-        loss_flops += 4.0 * k ** 3
-        # G and R read once, C written once, saved factors written (forward) / read (adjoint)
-        solve_bytes += 4 * 3 * k * k + fac
-        adj_bytes += 4 * 2 * k * k + fac
+        fac = 4 * ky * (32 * q * (q + 2) + 64 * q) if k <= saved_k_max else 0
+        solve_flops += ky * k ** 3 / 3.0 + (2.0 + 4.0 * ir_steps) * ky * k ** 2
+        adj_flops += (0.0 if k <= saved_k_max else ky * k ** 3 / 3.0) + 2.0 * ky * k ** 2
+        loss_flops += 2.0 * ky * ky * k + 2.0 * ky * ky * k
+        # G, R and C move once each, saved factors written (forward) / read (adjoint)
+        solve_bytes += 4 * (k * k + 2 * ky * k) + fac
+        adj_bytes += 4 * 2 * ky * k + fac
     return dict(project=dict(bytes=proj_bytes, flops=proj_flops), project_bwd=dict(bytes=bwd_bytes, flops=proj_flops),
                 solve=dict(flops=solve_flops, bytes=solve_bytes), adj_solve=dict(flops=adj_flops, bytes=adj_bytes),
                 loss=dict(flops=loss_flops))

@@ -66,3 +66,12 @@ def test_algorithmic_work_counts():
     # FP32 features stream twice the feature bytes
     w32 = bench.algorithmic_work(_wl([(1000, 30, 256)], [], feat="fp32"), 1, 304)
     assert w32["project"]["bytes"] == 1000 * (4 * 30 + 4 + 4 * 256) + 4 * 30 * 256
+
+
+def test_algorithmic_work_rectangular():
+    """A k_Y x k_X map has k_Y row systems of size k_X."""
+    wl = _wl([(1000, 30, 64), (2000, 50, 64)], [(0, 1)])
+    w = bench.algorithmic_work(wl, ir_steps=1, saved_k_max=304)
+    assert w["solve"]["flops"] == 50 * 30 ** 3 / 3.0 + 6.0 * 50 * 30 ** 2
+    q = 4
+    assert w["solve"]["bytes"] == 4 * (30 * 30 + 2 * 50 * 30) + 4 * 50 * (32 * q * (q + 2) + 64 * q)
