@@ -145,6 +145,52 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- measured peaks
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "tf32_mma": 2, "bf16_mma": 3}
+
+
+def measure_peaks(dev, target_s: float = 0.25, reps: int = 3):
+    """The library's peak loops (fmap_peak_loop): FP32 and FP64 FMA chains on every SM,
+    tcgen05 kind::tf32 and kind::f16 (BF16) MMA loops with one CTA per SM. Each launch is
+    scaled to about `target_s` seconds; the best of `reps` CUDA-event timed launches is
+    kept. Returns TFLOP/s per kind, with the SM clock sampled while they ran."""
+    import ctypes
+    import torch
+    from paper_2604_10377_gb300 import _lib
+    L = _lib.lib()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(4 * sms, dtype=torch.int32, device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    out = {}
+    for name, kind in PEAK_KINDS.items():
+        blocks = sms if "mma" in name else 4 * sms
+        fl = ctypes.c_double(0.0)
+
+        def launch(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _lib.check(L.fmap_peak_loop(kind, blocks, int(iters), ctypes.c_void_p(sink.data_ptr()),
+                                        ctypes.byref(fl), st), "fmap_peak_loop")
+            e1.record()
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / 1000.0
+
+        iters = 1000
+        t = launch(iters)
+        while t < 0.02:
+            iters *= 8
+            t = launch(iters)
+        iters = max(1, int(iters * target_s / t))
+        best = 0.0
+        for _ in range(reps):
+            t = launch(iters)
+            best = max(best, fl.value / t / 1e12)
+        out[name] = best
+    if int(sink[0].item()) != 0:
+        raise RuntimeError("an MMA peak loop reported a timed-out wait")
+    return out
+
+
 # ---------------------------------------------------------------- algorithmic work
 def algorithmic_work(wl, ir_steps, saved_k_max):
     """Bytes (HBM) and flops per launch of each kernel kind, from the sizes alone."""
@@ -383,6 +429,18 @@ def run_ours(args):
         uuid = "GPU-" + uuid
     sampler = ClockSampler(uuid) if uuid else None
 
+    # measured peaks (the roofline denominators), with the clocks seen while they ran
+    measured = None
+    if not args.no_peaks:
+        psamp = ClockSampler(uuid) if uuid else None
+        if psamp:
+            psamp.start()
+        measured = measure_peaks(dev)
+        measured["clocks"] = psamp.stop() if psamp else None
+        measured["how"] = ("fmap_peak_loop: FP32/FP64 FMA chains (4 x SMs CTAs of 512 threads), tcgen05 "
+                           "kind::tf32 / kind::f16 M=128 N=256 MMA loops (one CTA per SM); ~0.25 s launches, "
+                           "best of 3, CUDA events")
+
     if sampler:
         sampler.start()
     # eager pass with the library's per-kind event timing (the kernel breakdown)
@@ -483,7 +541,12 @@ def run_ours(args):
                for k, v in ktime.items() if v[1] > 0}
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     launches_total = sum(v[1] for v in ktime.values())
-    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    if measured:
+        fp32_peak_tflops = measured["fp32_fma"]
+        fp32_peak_source = "measured FP32 FMA loop on this GPU (fmap_peak_loop)"
+    else:
+        fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        fp32_peak_source = "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
 
     traffic = load_traffic(args.workload)
 
@@ -492,9 +555,17 @@ def run_ours(args):
         per_step_ms = ktime[kind][0] / args.steps
         if kind in ("project", "project_bwd"):
             ach = work[kind]["bytes"] / (per_step_ms / 1000.0) / 1e9
-            return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic.get(kind),
-                    "peak_source": f"{peaks['source']} HBM copy bandwidth"}
+            r = {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic.get(kind),
+                 "peak_source": f"{peaks['source']} HBM copy bandwidth"}
+            if measured:
+                # tensor pipe: algorithmic flops over the measured MMA peak of the dtype the MMAs run in
+                # (BF16 features: kind::f16 forward, kind::tf32 backward; FP32 features: kind::tf32)
+                tflops = work[kind]["flops"] / (per_step_ms / 1000.0) / 1e12
+                mma = "bf16_mma" if (kind == "project" and wl.feat_dtype == "bf16") else "tf32_mma"
+                r["tensor"] = {"achieved_tflops": tflops, "peak_tflops": measured[mma], "peak": mma,
+                               "frac": tflops / measured[mma]}
+            return r
         flops = work.get(kind, {}).get("flops")
         if flops is None:
             return {"kernel": kind, "bound": "alu", "achieved": None, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
@@ -503,7 +574,7 @@ def run_ours(args):
         return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak_tflops, "traffic": traffic.get(kind),
                 "algorithmic_bytes": work.get(kind, {}).get("bytes"),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+                "peak_source": fp32_peak_source}
 
     roofline = roof_for(dom)
     others = {k: roof_for(k) for k in ("project", "project_bwd", "solve", "adj_solve") if k in kernels and k != dom}
@@ -551,6 +622,7 @@ def run_ours(args):
             "eager": {"value": rate_eager, "unit": "pairs/s", "ms_per_step": ms_eager},
             "roofline": roofline,
             "roofline_other": others,
+            "peaks_measured": measured,
             "kernels": kernels,
             "gpu_launches": int(launches_total),
             "cpu_baseline": cpu,
@@ -717,6 +789,7 @@ def main():
     ap.add_argument("--overlap", action="store_true", help="overlap-prediction metrics instead of the step")
     ap.add_argument("--copy-streams", type=int, default=4, help="side streams of the end-to-end host-to-device copies")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's built-in tiling choices")
+    ap.add_argument("--no-peaks", action="store_true", help="derive the FP32 peak instead of measuring it")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

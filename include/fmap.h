@@ -98,6 +98,11 @@ typedef struct fmap_shape_desc {
     int64_t ld_feat;       /* >= d, multiple of 8 */
     void* dfeat;           /* device, same layout and type as feat: receives dL/dF in
                               fmap_solve_backward; NULL = do not compute it */
+    float* dfeat_f32;      /* BF16 batches only (ignored in FP32 batches): device, n x ld_feat
+                              FP32, 16-byte aligned, or NULL. When given together with dfeat,
+                              fmap_solve_backward also writes dL/dF here in FP32, the values
+                              before their rounding to BF16 (a copy for checking the backward
+                              projection without the BF16 storage error) */
 } fmap_shape_desc;
 
 typedef struct fmap_pair_desc {
@@ -223,6 +228,29 @@ enum fmap_kernel_kind {
 };
 FMAP_API int32_t fmap_batch_set_timing(fmap_batch* batch, int32_t enable);
 FMAP_API int32_t fmap_batch_read_timing(fmap_batch* batch, float* ms, int32_t* launches, int32_t n_kinds);
+
+/* Peak-throughput loops, the measured denominators of the roofline fractions (no
+ * counterpart in the paper). One launch of `kind` with `blocks` CTAs and `iters` rounds
+ * is enqueued on `stream`; *flops_per_launch (host) receives the arithmetic it does, so
+ * that flops / (CUDA-event time of the launch) is the achieved rate:
+ *   FMAP_PEAK_FP32_FMA  512 threads per CTA, 8 independent FP32 FMA chains of 4 iters each:
+ *                       flops = blocks * 512 * iters * 64
+ *   FMAP_PEAK_FP64_FMA  the same in FP64
+ *   FMAP_PEAK_TF32_MMA  one CTA per SM (pass blocks <= the SM count), tcgen05.mma
+ *                       kind::tf32 M = 128, N = 256, K = 8, iters MMAs into one TMEM
+ *                       accumulator: flops = blocks * iters * 524288
+ *   FMAP_PEAK_BF16_MMA  the same with kind::f16 BF16 operands, K = 16:
+ *                       flops = blocks * iters * 1048576
+ * sink: device buffer of >= blocks 4-byte words, zeroed by the caller (the FMA loops may
+ * write there; the MMA loops set word 0 to FMAP_ERR_TIMEOUT if their bounded wait gave up). */
+enum fmap_peak_kind {
+    FMAP_PEAK_FP32_FMA = 0,
+    FMAP_PEAK_FP64_FMA = 1,
+    FMAP_PEAK_TF32_MMA = 2,
+    FMAP_PEAK_BF16_MMA = 3
+};
+FMAP_API int32_t fmap_peak_loop(int32_t kind, int32_t blocks, int64_t iters, void* sink, double* flops_per_launch,
+                                void* stream);
 
 /* ---- Overlap-prediction metrics (Sec. "Overlap Prediction Metrics") ---------------
  * For segments s = 0 .. n_segments-1 of flat per-vertex arrays (the vertices of one

@@ -8,9 +8,11 @@ it, and it shares no code, table or helper with the CUDA path.
 Everything is plain NumPy in float64, written from the paper (DeepShapeMatchingKit,
 arXiv 2604.10377, Sec. 3.1 "Batched Functional Map Solver"):
 
-* Eq. 1: spectral descriptors A = Phi_X^+ F_X, B = Phi_Y^+ F_Y. The pseudo-inverse
-  of an M-orthonormal basis is taken in the M inner product, Phi^+ = Phi^T M
-  (reading R1 of the design notes: it is the left inverse, Phi^T M Phi = I).
+* Eq. 1: spectral descriptors A = Phi_X^+ F_X, B = Phi_Y^+ F_Y. The paper writes the
+  Moore-Penrose pseudo-inverse Phi^+; for a basis that is orthonormal in the mass inner
+  product (Phi^T M Phi = I) the inverse used here is the M-weighted left inverse
+  Phi^+ = Phi^T M, which satisfies Phi^+ Phi = I and equals the Euclidean pseudo-inverse
+  when M is a multiple of the identity (both are pinned in the tests).
 * Eq. 2: the energy ||C A - B||^2 + lambda ||C Delta_X - Delta_Y C||^2.
 * Eq. 3: with Delta diagonal in its eigenbasis, the commutativity term is the
   entry-wise weight D_ij = (Lambda_Y(i) - Lambda_X(j))^2.

@@ -39,7 +39,7 @@ TUNING_FIELDS = ("proj_max_stages", "proj_seg_max_v", "bwd_group_features", "bwd
 class ShapeDesc(ctypes.Structure):
     _fields_ = [("n", c_int64), ("k", c_int32), ("d", c_int32), ("phi", c_void_p), ("ld_phi", c_int64),
                 ("mass", c_void_p), ("evals", c_void_p), ("feat", c_void_p), ("ld_feat", c_int64),
-                ("dfeat", c_void_p)]
+                ("dfeat", c_void_p), ("dfeat_f32", c_void_p)]
 
 
 class PairDesc(ctypes.Structure):
@@ -86,6 +86,7 @@ _PROTOS = {
     "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),
     "fmap_solve_pair_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                           c_float, c_int32, c_void_p, c_void_p, c_void_p]),
+    "fmap_peak_loop": (c_int32, [c_int32, c_int32, c_int64, c_void_p, POINTER(ctypes.c_double), c_void_p]),
     "fmap_overlap_metrics": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_float, c_void_p, c_void_p,
                                        c_void_p]),
 }

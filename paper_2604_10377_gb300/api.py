@@ -93,7 +93,8 @@ class FmapBatch:
 
     def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
                  with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
-                 store_factors_max_k: int = 304, adjoint_ir_steps: int = 0, tuning: Optional[dict] = None):
+                 store_factors_max_k: int = 304, adjoint_ir_steps: int = 0, tuning: Optional[dict] = None,
+                 grad_f32_copy: bool = False):
         self.layout = layout
         self.device = torch.device(device)
         self.precision = precision
@@ -104,6 +105,9 @@ class FmapBatch:
         self.evals = torch.zeros(lay.evals_len, dtype=torch.float32, device=dev)
         self.feat = torch.zeros(lay.feat_len, dtype=lay.torch_feat_dtype(), device=dev)
         self.dfeat = torch.zeros_like(self.feat) if with_grad else None
+        # BF16 batches: optional FP32 copy of dL/dF before its rounding to BF16 (for checking)
+        self.dfeat32 = (torch.zeros(lay.feat_len, dtype=torch.float32, device=dev)
+                        if with_grad and grad_f32_copy and lay.feat_dtype == "bf16" else None)
         self.pairs = [(int(x), int(y), float(lam)) for (x, y, lam) in pairs]
         # C_p maps the k_X coefficients of shape x to the k_Y of shape y: k_Y x k_X
         self.ks = [lay.ks[x] for (x, _, _) in self.pairs]
@@ -149,6 +153,7 @@ class FmapBatch:
             d.feat = self.feat.data_ptr() + fel * lay.feat_off[s]
             d.ld_feat = lay.ds[s]
             d.dfeat = (self.dfeat.data_ptr() + fel * lay.feat_off[s]) if self.dfeat is not None else None
+            d.dfeat_f32 = (self.dfeat32.data_ptr() + 4 * lay.feat_off[s]) if self.dfeat32 is not None else None
         pd = (_lib.PairDesc * max(1, len(self.pairs)))()
         for p, (x, y, lam) in enumerate(self.pairs):
             pd[p].shape_x, pd[p].shape_y, pd[p].lam = x, y, lam

@@ -26,6 +26,7 @@ SOURCES = [
     "k_chol.cu",
     "k_overlap.cu",
     "fmap_noalloc.cu",
+    "k_peaks.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

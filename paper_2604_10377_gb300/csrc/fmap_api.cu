@@ -83,7 +83,7 @@ struct Plan {
   int64_t loss_part_off = 0;
   // tensor-core projection
   bool tc32 = false;      // FP32 features: three-pass TF32 kernel
-  bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features: 2-CTA clusters)
+  bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features: CTA pairs)
   bool tc_bwd32 = false;  // backward projection on the tensor cores (FP32 features: three TF32 passes)
   std::vector<TcItem> tc_items;
   std::vector<int32_t> tc_cta_first;   // kTcCtas + 1 entries per launch
@@ -138,12 +138,14 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     if (d.ld_phi % 4 != 0 || d.ld_feat % 8 != 0) return FMAP_ERR_UNSUPPORTED;
     if (!aligned(d.phi, 16) || !aligned(d.feat, 16) || !aligned(d.mass, 4)) return FMAP_ERR_UNSUPPORTED;
     if (d.dfeat && !aligned(d.dfeat, 16)) return FMAP_ERR_UNSUPPORTED;
+    if (d.dfeat_f32 && !aligned(d.dfeat_f32, 16)) return FMAP_ERR_UNSUPPORTED;
     if (d.evals && !aligned(d.evals, 4)) return FMAP_ERR_UNSUPPORTED;
     ShapeDev& sd = P.shapes[s];
     std::memset(&sd, 0, sizeof(sd));
     sd.n = d.n; sd.k = d.k; sd.d = d.d;
     sd.phi = d.phi; sd.ld_phi = d.ld_phi; sd.mass = d.mass; sd.evals = d.evals;
     sd.feat = d.feat; sd.ld_feat = d.ld_feat; sd.dfeat = d.dfeat;
+    sd.dfeat32 = (opt.precision == FMAP_PREC_BF16 && d.dfeat) ? d.dfeat_f32 : nullptr;
     sd.a_off = P.a_off[s];
     P.a_off[s + 1] = P.a_off[s] + (int64_t)d.k * d.d;
     P.max_k = std::max(P.max_k, d.k);
@@ -326,19 +328,20 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   P.da_int_off = cur;
   cur = align_up(cur + P.a_off[n_shapes], kAlignFloats);
   if (P.tc_bwd) {
-    // Backward work runs on clusters of two CTAs that share each Phi tile (multicast):
-    // a shape's features split into an even number of groups of <= 128, and a work
-    // item is (shape, vertex chunk, pair of groups), one group per CTA of the
-    // cluster. Items are sorted by cost and dealt to the clusters round-robin.
-    const int n_clusters = kTcCtas / 2;
+    // Backward work runs on pairs of CTAs (2c, 2c + 1) that walk the same Phi tiles at
+    // the same time, so the second read of each tile hits L2: a shape's features split
+    // into an even number of groups of <= 128, and a work item is (shape, vertex chunk,
+    // pair of groups), one group per CTA of the pair. Items are sorted by cost and dealt
+    // to the CTA pairs round-robin.
+    const int n_ctapairs = kTcCtas / 2;
     int64_t bw_work = 0;
     for (int s = 0; s < n_shapes; ++s)
       if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + 255) / 256);
     const int64_t bw_chunk = opt.bwd_chunk_v ? (int64_t)opt.bwd_chunk_v
                                              : std::min<int64_t>(kTcChunkV, std::max<int64_t>(
-                                                   1024, (bw_work / (4 * n_clusters) + 127) / 128 * 128));
+                                                   1024, (bw_work / (4 * n_ctapairs) + 127) / 128 * 128));
     const int bw_gf = opt.bwd_group_features ? opt.bwd_group_features : 128;
-    std::vector<TcBwdItem> items;   // pairs: [2 j] for cluster rank 0, [2 j + 1] for rank 1
+    std::vector<TcBwdItem> items;   // pairs: [2 j] for CTA 2c, [2 j + 1] for CTA 2c + 1
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
       if (!sd.dfeat) continue;
@@ -381,16 +384,16 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         if (cx != cy) return cx > cy;
         return a < b;
       });
-      // cluster c takes pair-items c, c + n_clusters, ... of the sorted list, stored contiguously
-      P.bw_cta_first.assign(n_clusters + 1, 0);
-      for (int c = 0; c < n_clusters; ++c) {
+      // CTA pair c takes pair-items c, c + n_ctapairs, ... of the sorted list, stored contiguously
+      P.bw_cta_first.assign(n_ctapairs + 1, 0);
+      for (int c = 0; c < n_ctapairs; ++c) {
         P.bw_cta_first[c] = (int32_t)(P.bw_items.size() / 2);
-        for (size_t j = c; j < order.size(); j += n_clusters) {
+        for (size_t j = c; j < order.size(); j += n_ctapairs) {
           P.bw_items.push_back(items[2 * order[j]]);
           P.bw_items.push_back(items[2 * order[j] + 1]);
         }
       }
-      P.bw_cta_first[n_clusters] = (int32_t)(P.bw_items.size() / 2);
+      P.bw_cta_first[n_ctapairs] = (int32_t)(P.bw_items.size() / 2);
     }
     const int fixed = 1024 + 512;
     const int out_staging = 8 * 4096;   // BF16 dF staging of the eight epilogue warps

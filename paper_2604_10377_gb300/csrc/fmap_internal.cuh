@@ -28,6 +28,7 @@ struct ShapeDev {
   const void* feat;
   int64_t ld_feat;
   void* dfeat;
+  float* dfeat32;      // optional FP32 copy of dF before rounding (BF16 batches), row stride ld_feat
   int64_t a_off;       // float offset of A_s in the flat A buffer
   int32_t slot_beg;    // [slot_beg, slot_end): entries of slot_list holding dA contributions
   int32_t slot_end;
@@ -142,8 +143,10 @@ struct TcBwdParams {
   const ShapeDev* shapes;
   const CUtensorMap* phimaps;  // per shape: FP32 Phi, box 32 x 64, 128-byte swizzle
   const CUtensorMap* dfmaps;   // per shape: dF (BF16 or FP32), box 16 x 32, no swizzle (TMA stores)
-  const TcBwdItem* items;       // item j of a cluster: [2 j] for CTA rank 0, [2 j + 1] for rank 1
-  const int32_t* cta_first;     // cluster c (CTAs 2c, 2c + 1) owns items [cta_first[c], cta_first[c + 1])
+  const TcBwdItem* items;       // BF16: item j of CTA pair c is [2 j] for CTA 2c, [2 j + 1] for CTA 2c + 1;
+                                //   FP32: one item per entry
+  const int32_t* cta_first;     // BF16: CTA pair c owns items [cta_first[c], cta_first[c + 1]);
+                                //   FP32: CTA c
   int32_t stages;
   uint32_t b_bytes_max;
   uint32_t tmem_cols;

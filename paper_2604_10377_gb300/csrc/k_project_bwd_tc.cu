@@ -3,18 +3,18 @@
 //   dF_s (n x d) = diag(M_s) Phi_s (n x k) . dA_s (k x d)
 //
 // kind::tf32 MMA, M = 128 vertices, N = one feature group (<= 128 features),
-// K = the basis index in blocks of 32. The kernel runs as clusters of two CTAs on
-// two SMs: both CTAs of a cluster walk the same vertex tiles, each for its own
-// feature group, and each loads half of every FP32 Phi tile by TMA and multicasts
-// it to both, so a pair of feature groups reads Phi from HBM once. The B operand
-// is dA_s^T of the CTA's feature group, prepared once per backward pass as a
-// K-major swizzled FP32 image in the workspace and bulk-copied into shared memory
-// per work item. The mass is a per-row (per-TMEM-lane) scale applied in the
-// epilogue, which converts to BF16 and writes dF. TF32 keeps ~2^-11 relative
-// accuracy of each operand, far inside the BF16 storage of dF. Accumulators are
-// double-buffered in TMEM so that the epilogue of one vertex tile overlaps the
-// MMAs of the next. A Phi stage is refilled only after the MMAs of both CTAs
-// released it (multicast commit to both CTAs' empty barriers).
+// K = the basis index in blocks of 32. One persistent CTA per SM. CTAs 2c and 2c + 1
+// take the two feature groups of the same (shape, vertex chunk) items in the same
+// order, so they walk the same vertex tiles at about the same time: each loads the
+// whole FP32 Phi tile with plain TMA loads, and the second of the two reads of a tile
+// is served from L2, so HBM sees Phi about once per pair of groups. The B operand is
+// dA_s^T of the CTA's feature group, prepared once per backward pass as a K-major
+// swizzled FP32 image in the workspace and bulk-copied into shared memory per work
+// item. The mass is a per-row (per-TMEM-lane) scale applied in the epilogue, which
+// converts to BF16 and writes dF (and, when the shape asks for it, the same values
+// before rounding as an FP32 copy). TF32 keeps ~2^-11 relative accuracy of each
+// operand, far inside the BF16 storage of dF. Accumulators are double-buffered in
+// TMEM so that the epilogue of one vertex tile overlaps the MMAs of the next.
 //
 // Waits are bounded like the forward kernel's; a timeout sets the workspace
 // control word to FMAP_ERR_TIMEOUT.
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = P.stages;
   uint8_t* sB = smem;                                   // resident dA^T image of this CTA's feature group
-  uint8_t* sA = sB + P.b_bytes_max;                     // Phi tiles, S stages (same offset in both CTAs)
+  uint8_t* sA = sB + P.b_bytes_max;                     // Phi tiles, S stages
   uint8_t* sOut = sA + (size_t)S * kAStageBytes;        // BF16 dF staging, kOutWarpBytes per epilogue warp
   uint64_t* bars = reinterpret_cast<uint64_t*>(sOut + (size_t)kEpiWarps * kOutWarpBytes);
   uint64_t* a_full = bars;
@@ -64,13 +64,13 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = tc::cluster_ctarank();     // 0 or 1: which feature group of the pair
-  const int cl = blockIdx.x >> 1;                  // cluster index
+  const uint32_t rank = blockIdx.x & 1u;           // 0 or 1: which feature group of the item pair
+  const int cl = blockIdx.x >> 1;                  // CTA pair index
   const int it_beg = P.cta_first[cl], it_end = P.cta_first[cl + 1];
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&a_full[s], 1);
-      tc::mbar_init(&a_empty[s], 2);     // released by the MMAs of both CTAs
+      tc::mbar_init(&a_empty[s], 1);     // released by this CTA's MMAs
     }
     tc::mbar_init(b_full, 1);
     tc::mbar_init(b_empty, 1);
@@ -86,15 +86,13 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
     tc::tmem_relinquish();
     tc::tc_fence_before();
   }
-  // both CTAs' barriers exist before either multicasts into the other
-  tc::cluster_sync();
+  __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    // Each CTA loads its half (64 vertices) of every Phi tile and multicasts it to
-    // both CTAs, so the pair reads each tile from HBM once.
+    // The whole Phi tile (128 vertices) of every stage, as two boxes of 64 vertices.
     if (lane == 0) {
       uint32_t stage = 0, phase = 0, bphase = 0;
       for (int it = it_beg; it < it_end; ++it) {
@@ -114,18 +112,19 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
         bphase ^= 1;
         const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
         for (int t = 0; t < ntiles; ++t) {
-          const int y = (int)(item.v0 + (int64_t)t * kTileV) + (int)rank * (kTileV / 2);
+          const int y = (int)(item.v0 + (int64_t)t * kTileV);
           for (int kb = 0; kb < item.kb; ++kb) {
             if (!tc::mbar_wait(&a_empty[stage], phase ^ 1, abort_flag)) goto producer_done;
             tc::mbar_arrive_expect_tx(&a_full[stage], kAStageBytes);
-            tc::tma_load_2d_multicast(sA + (size_t)stage * kAStageBytes + rank * (kAStageBytes / 2), map,
-                                      &a_full[stage], kb * 32, y, (uint16_t)0x3);
+            uint8_t* dst = sA + (size_t)stage * kAStageBytes;
+            tc::tma_load_2d(dst, map, &a_full[stage], kb * 32, y);
+            tc::tma_load_2d(dst + kAStageBytes / 2, map, &a_full[stage], kb * 32, y + kTileV / 2);
             if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
           }
         }
       }
-      // every stage's last use has been released by both CTAs: no arrival from the
-      // peer is still on its way to this CTA's barriers
+      // every stage's last use has been released: no MMA still reads a stage when the
+      // CTA leaves
       for (int s = 0; s < S; ++s) {
         if (!tc::mbar_wait(&a_empty[stage], phase ^ 1, abort_flag)) break;
         if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
@@ -168,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
                 mma_tf32(d, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
               }
             }
-            tc::mma_commit_multicast(&a_empty[stage], (uint16_t)0x3);
+            tc::mma_commit(&a_empty[stage]);
             if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
@@ -207,6 +206,12 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
         for (int ch = half; ch < item.nf / 16; ch += 2, ++j) {
           float x[16];
           tc::tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + ch * 16), x);
+          if (s.dfeat32 != nullptr && v < item.v1) {
+            float4* d32 = reinterpret_cast<float4*>(s.dfeat32 + v * s.ld_feat + item.f0 + ch * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              d32[q] = make_float4(x[4 * q] * m, x[4 * q + 1] * m, x[4 * q + 2] * m, x[4 * q + 3] * m);
+          }
           uint32_t w[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q)
@@ -236,15 +241,15 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
   }
 
   __syncthreads();
-  // neither CTA leaves while the other may still multicast into it
-  tc::cluster_sync();
   if (warp == 1) tc::tmem_dealloc(tmem_base, P.tmem_cols);
   if (threadIdx.x == 0 && *abort_flag) atomicExch(P.err, (int)FMAP_ERR_TIMEOUT);
 }
 
 // dA_s^T of one feature group as the K-major, 128-byte-swizzled FP32 image the MMA
 // reads: block kb (basis 32kb..32kb+31) holds nf rows of 128 bytes (one feature per
-// row), 16-byte chunk c of row f stored at chunk c ^ (f & 7).
+// row), 16-byte chunk c of row f stored at chunk c ^ (f & 7). Each value is rounded to
+// the nearest TF32 here (the MMA would otherwise drop its low 13 bits), so the only
+// truncated operand of the product is Phi.
 __global__ void build_dat_image_kernel(const ShapeDev* shapes, const TcBwdGroup* groups, const float* d_a,
                                        float* ws) {
   const TcBwdGroup g = groups[blockIdx.y];
@@ -256,7 +261,10 @@ __global__ void build_dat_image_kernel(const ShapeDev* shapes, const TcBwdGroup*
     const int rem = e % (g.nf * 32);
     const int f = rem / 32, nl = rem % 32;
     const int n = kb * 32 + nl, fg = g.f0 + f;
-    const float val = (n < s.k && fg < s.d) ? d_a[s.a_off + (int64_t)n * s.d + fg] : 0.f;
+    const float raw = (n < s.k && fg < s.d) ? d_a[s.a_off + (int64_t)n * s.d + fg] : 0.f;
+    uint32_t r32;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r32) : "f"(raw));
+    const float val = __uint_as_float(r32);
     const int chunk = nl >> 2;
     img[(int64_t)kb * g.nf * 32 + f * 32 + ((chunk ^ (f & 7)) << 2) + (nl & 3)] = val;
   }
@@ -278,19 +286,8 @@ cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* gro
 
 cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = (size_t)smem_bytes;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, project_bwd_tc_kernel, p);
+  project_bwd_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace fmap

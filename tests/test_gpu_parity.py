@@ -2,7 +2,8 @@
 
 Tolerances (relative Frobenius error per shape / pair):
   FP32 features: A, C within 1e-5; dL/dF within 1e-4.
-  BF16 features: A, C within 3e-3; dL/dF (stored in BF16) within 3e-3.
+  BF16 features: A, C within 3e-3; dL/dF (stored in BF16) within 3e-3; the FP32 copy of
+  dL/dF taken before that rounding within GTOL_F32_COPY = 1e-3.
 """
 import dataclasses
 
@@ -18,6 +19,11 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-5, "bf16": 3e-3}
 GTOL = {"fp32": 1e-4, "bf16": 3e-3}
+# BF16 batches, dL/dF before its BF16 rounding: the backward projection multiplies TF32
+# operands (Phi truncated by the MMA, relative error in [0, 2^-10) with mean 2^-11 ~ 4.9e-4,
+# a common scale of every output; dA rounded to TF32 when its image is built, ~2^-12 on
+# average) after the adjoint's own FP32 error (~1e-4): about 6e-4 expected.
+GTOL_F32_COPY = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -178,6 +184,12 @@ def _gpu_backward(wl, use_saved=True, **kw):
         C=[b.c_view(c, p).cpu().numpy() for p in range(len(wl.pairs))],
         status=b.status[:len(wl.pairs)].cpu().numpy(),
     )
+    if b.dfeat32 is not None:
+        out["dF32"] = [b.layout.feat_view(b.dfeat32, s).cpu().numpy() for s in range(len(wl.shapes))]
+        # the BF16 gradient is the round-to-nearest-even of the FP32 copy, bit for bit
+        out["bf16_is_rounded_copy"] = all(
+            torch.equal(b.layout.feat_view(b.dfeat32, s).to(torch.bfloat16).view(torch.int16),
+                        b.layout.feat_view(b.dfeat, s).view(torch.int16)) for s in range(len(wl.shapes)))
     return out
 
 
@@ -286,6 +298,23 @@ def test_backward_bf16_feature_groups(d):
     assert np.all(out["status"] == 0)
     for s in range(len(wl.shapes)):
         assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["bf16"]
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
+
+
+@pytest.mark.parametrize("d,ks", [(16, [7, 12]), (48, [7, 30]), (256, [30, 100, 200]), (384, [100, 200])])
+def test_backward_bf16_fp32_copy(d, ks):
+    """The BF16 backward projection checked before its rounding: the optional FP32 copy of
+    dL/dF against the oracle gradient within GTOL_F32_COPY, and the BF16 gradient equal to
+    the round-to-nearest-even of that copy bit for bit. k on both sides of the 32-blocks of
+    the basis, up to the double-float Gram (k = 200); one or two feature groups per CTA pair
+    (d = 16 leaves the second group empty); vertex counts ending inside a tile."""
+    wl = synth.make_small(21, 2 * len(ks), (66, 5000), ks, d, feat_dtype="bf16")
+    out = _gpu_backward(wl, grad_f32_copy=True)
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    assert out["bf16_is_rounded_copy"]
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dF32"][s], g["dF"][s]) <= GTOL_F32_COPY, (s, rel_fro(out["dF32"][s], g["dF"][s]))
         assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
 
 
