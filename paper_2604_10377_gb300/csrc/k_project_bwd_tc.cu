@@ -286,8 +286,22 @@ cudaError_t launch_build_dat_image(const ShapeDev* shapes, const TcBwdGroup* gro
 
 cudaError_t launch_project_bwd_tc(const TcBwdParams& p, int grid, int smem_bytes, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  project_bwd_tc_kernel<<<grid, kThreads, smem_bytes, st>>>(p);
-  return cudaGetLastError();
+  // CTAs 2c and 2c + 1 (which walk the same Phi tiles) launch as a cluster of two: they
+  // start together on one GPC, so the second read of each tile finds it in L2. The kernel
+  // uses nothing of the cluster beyond that placement.
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, project_bwd_tc_kernel, p);
 }
 
 }  // namespace fmap

@@ -111,10 +111,14 @@ def m_orthonormalize(phi: np.ndarray, mass: np.ndarray, passes: int = 2) -> np.n
     return phi
 
 
+def _draw_n(rng, n_range) -> int:
+    lo, hi = n_range
+    return lo if lo == hi else int(round(_loguniform(rng, lo, hi)))
+
+
 def make_shape(seed: int, n_range, k: int, d: int, feat_dtype: str) -> Shape:
     rng = np.random.Generator(np.random.PCG64(seed))
-    lo, hi = n_range
-    n = lo if lo == hi else int(round(_loguniform(rng, lo, hi)))
+    n = _draw_n(rng, n_range)
     phi = rng.standard_normal((n, k))
     mass = rng.uniform(0.5, 1.5, n) / n
     evals = np.sort(rng.uniform(0.0, 100.0, k))
@@ -133,6 +137,31 @@ def random_orthogonal(seed: int, k: int) -> np.ndarray:
     return q.astype(np.float32)
 
 
+def _config_draws(config: int, replica: int):
+    cfg = CONFIGS[config]
+    base = BASE_SEED + 1000000 * replica
+    brng = np.random.Generator(np.random.PCG64(base + 1000 * config + 999))
+    ks, lams = [], []
+    for _ in range(cfg["pairs"]):
+        kk = cfg["k"]
+        ks.append(int(kk[0]) if len(kk) == 1 else int(kk[int(brng.integers(0, len(kk)))]))
+        lam = cfg["lam"]
+        lams.append(float(np.float32(lam[1] if lam[0] == "fixed" else _loguniform(brng, lam[1], lam[2]))))
+    return cfg, base, ks, lams
+
+
+def config_sizes(config: int, replica: int = 0):
+    """(n_x, n_y, k) of every pair of workload `config`, drawn exactly as make_config draws
+    them but without the arrays (for planning work, e.g. sharing pairs among processes)."""
+    cfg, base, ks, _ = _config_draws(config, replica)
+    out = []
+    for p in range(cfg["pairs"]):
+        ns = [_draw_n(np.random.Generator(np.random.PCG64(base + 1000 * config + 2 * p + side)), cfg["n"])
+              for side in (0, 1)]
+        out.append((ns[0], ns[1], ks[p]))
+    return out
+
+
 def make_config(config: int, pairs: Optional[Sequence[int]] = None, n_scale: float = 1.0,
                 with_gt: bool = True, replica: int = 0) -> Workload:
     """Draw workload `config` (0..4). `pairs` selects a subset of pair indices
@@ -141,16 +170,8 @@ def make_config(config: int, pairs: Optional[Sequence[int]] = None, n_scale: flo
     tests (the draws are otherwise unchanged). `replica` r > 0 draws an
     independent batch of the same recipe (all seeds shifted by 10^6 r), one per
     GPU when pairs are sharded over several GPUs."""
-    cfg = CONFIGS[config]
+    cfg, base, ks, lams = _config_draws(config, replica)
     npairs = cfg["pairs"]
-    base = BASE_SEED + 1000000 * replica
-    brng = np.random.Generator(np.random.PCG64(base + 1000 * config + 999))
-    ks, lams = [], []
-    for _ in range(npairs):
-        kk = cfg["k"]
-        ks.append(int(kk[0]) if len(kk) == 1 else int(kk[int(brng.integers(0, len(kk)))]))
-        lam = cfg["lam"]
-        lams.append(float(np.float32(lam[1] if lam[0] == "fixed" else _loguniform(brng, lam[1], lam[2]))))
     sel = list(range(npairs)) if pairs is None else list(pairs)
     shapes: List[Shape] = []
     plist: List[Pair] = []

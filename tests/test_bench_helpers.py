@@ -75,3 +75,21 @@ def test_algorithmic_work_rectangular():
     assert w["solve"]["flops"] == 50 * 30 ** 3 / 3.0 + 6.0 * 50 * 30 ** 2
     q = 4
     assert w["solve"]["bytes"] == 4 * (30 * 30 + 2 * 50 * 30) + 4 * 50 * (32 * q * (q + 2) + 64 * q)
+
+
+def test_oracle_pool_times_every_step_on_the_requested_workers():
+    """The CPU baseline's process pool (spawn, single-threaded BLAS per worker) returns one
+    wall time per step and never uses more workers than pairs."""
+    import bench
+    times, used = bench.oracle_pool_steps(0, [0], 2, 4)
+    assert used == 1 and len(times) == 2 and all(t > 0 for t in times)
+    times, used = bench.oracle_pool_steps(1, [0, 1, 2], 1, 2)
+    assert used == 2 and len(times) == 1
+
+
+def test_config_sizes_match_the_drawn_shapes():
+    from paper_2604_10377_gb300 import synth
+    sizes = synth.config_sizes(1)
+    wl = synth.make_config(1, pairs=[0, 5, 31], n_scale=1.0)
+    for j, p in enumerate([0, 5, 31]):
+        assert sizes[p] == (wl.shapes[2 * j].n, wl.shapes[2 * j + 1].n, wl.shapes[2 * j].k)
