@@ -146,7 +146,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- measured peaks
-PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "tf32_mma": 2, "bf16_mma": 3}
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "tf32_mma": 2, "bf16_mma": 3, "fp32x2_fma": 4}
 
 
 def measure_peaks(dev, target_s: float = 0.25, reps: int = 3):

@@ -247,7 +247,9 @@ enum fmap_peak_kind {
     FMAP_PEAK_FP32_FMA = 0,
     FMAP_PEAK_FP64_FMA = 1,
     FMAP_PEAK_TF32_MMA = 2,
-    FMAP_PEAK_BF16_MMA = 3
+    FMAP_PEAK_BF16_MMA = 3,
+    FMAP_PEAK_FP32X2_FMA = 4    /* the FP32 chains of FMAP_PEAK_FP32_FMA issued two lanes at a time
+                                   (packed fma.rn.f32x2): the same flops formula */
 };
 FMAP_API int32_t fmap_peak_loop(int32_t kind, int32_t blocks, int64_t iters, void* sink, double* flops_per_launch,
                                 void* stream);

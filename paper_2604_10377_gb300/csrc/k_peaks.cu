@@ -39,6 +39,31 @@ __global__ void fma32_loop_kernel(int64_t iters, float mul, float add, float* si
   if (s == 12345.678f) sink[blockIdx.x] = s;   // keeps the chains alive; never true in practice
 }
 
+// The same chains as pairs of FP32 lanes through the packed fma.rn.f32x2 instruction.
+__global__ void fma32x2_loop_kernel(int64_t iters, float mul, float add, float* sink) {
+  uint64_t x[kChains / 2];
+  const float2 m2 = make_float2(mul, mul), a2 = make_float2(add, add);
+  const uint64_t mm = *reinterpret_cast<const uint64_t*>(&m2), aa = *reinterpret_cast<const uint64_t*>(&a2);
+#pragma unroll
+  for (int j = 0; j < kChains / 2; ++j) {
+    const float2 v = make_float2((float)(threadIdx.x + 2 * j) * 1e-3f, (float)(threadIdx.x + 2 * j + 1) * 1e-3f);
+    x[j] = *reinterpret_cast<const uint64_t*>(&v);
+  }
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < kChains / 2; ++j) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[j]) : "l"(mm), "l"(aa));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kChains / 2; ++j) {
+    const float2 v = *reinterpret_cast<const float2*>(&x[j]);
+    s += v.x + v.y;
+  }
+  if (s == 12345.678f) sink[blockIdx.x] = s;
+}
+
 __global__ void fma64_loop_kernel(int64_t iters, double mul, double add, float* sink) {
   double x[kChains];
 #pragma unroll
@@ -130,6 +155,10 @@ extern "C" FMAP_API int32_t fmap_peak_loop(int32_t kind, int32_t blocks, int64_t
     case FMAP_PEAK_FP32_FMA:
       *flops_per_launch = (double)blocks * threads * (double)iters * 4.0 * kChains * 2.0;
       fma32_loop_kernel<<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-4f, static_cast<float*>(sink));
+      break;
+    case FMAP_PEAK_FP32X2_FMA:
+      *flops_per_launch = (double)blocks * threads * (double)iters * 4.0 * kChains * 2.0;
+      fma32x2_loop_kernel<<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-4f, static_cast<float*>(sink));
       break;
     case FMAP_PEAK_FP64_FMA:
       *flops_per_launch = (double)blocks * threads * (double)iters * 4.0 * kChains * 2.0;

@@ -301,14 +301,16 @@ def test_backward_bf16_feature_groups(d):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
 
 
-@pytest.mark.parametrize("d,ks", [(16, [7, 12]), (48, [7, 30]), (256, [30, 100, 200]), (384, [100, 200])])
-def test_backward_bf16_fp32_copy(d, ks):
+@pytest.mark.parametrize("d,ks,n_range", [(16, [7, 12], (66, 3000)), (48, [7, 30], (66, 3000)),
+                                         (256, [30, 100, 200], (300, 5000)), (384, [100, 200], (300, 5000))])
+def test_backward_bf16_fp32_copy(d, ks, n_range):
     """The BF16 backward projection checked before its rounding: the optional FP32 copy of
     dL/dF against the oracle gradient within GTOL_F32_COPY, and the BF16 gradient equal to
     the round-to-nearest-even of that copy bit for bit. k on both sides of the 32-blocks of
     the basis, up to the double-float Gram (k = 200); one or two feature groups per CTA pair
-    (d = 16 leaves the second group empty); vertex counts ending inside a tile."""
-    wl = synth.make_small(21, 2 * len(ks), (66, 5000), ks, d, feat_dtype="bf16")
+    (d = 16 leaves the second group empty); vertex counts ending inside a tile (n >= k, as
+    the M-orthonormal basis needs)."""
+    wl = synth.make_small(21, 2 * len(ks), n_range, ks, d, feat_dtype="bf16")
     out = _gpu_backward(wl, grad_f32_copy=True)
     shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
     assert np.all(out["status"] == 0)

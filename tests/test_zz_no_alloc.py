@@ -62,3 +62,50 @@ def test_noalloc_rejects_oversized_k():
     rc = lib.fmap_solve_pair_noalloc(_ptr(x), _ptr(x), 257, 16, _ptr(x), _ptr(x), None, ctypes.c_float(1e-3), 1,
                                      _ptr(x), None, None)
     assert rc == _lib.FMAP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("k,d,with_mask", [(1, 16, False), (40, 128, True), (256, 512, False)])
+def test_noalloc_matches_oracle_row_solve(k, d, with_mask):
+    """The allocation-free solve against the FP64 oracle's row solve (Eq. 4-5) on the same
+    descriptor matrices A and B, within the FP32 tolerance: k = 1, an explicit k x k mask
+    (no eigenvalues passed), and the largest k it takes (256). Two calls in a row on each
+    pair, so that the second reads scratch the first left behind."""
+    import os
+    from oracle import fmap_oracle as orc
+    from paper_2604_10377_gb300 import _lib, api, build, synth
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    lib = _lib.lib()
+    wl = synth.make_small(78 + k, 1, (600, 3000), [k], d, with_mask=with_mask)
+    b = api.batch_from_workload(wl)
+    a = b.project()
+    torch.cuda.synchronize()
+    pr = wl.pairs[0]
+    ax = b.a_view(a, pr.x).contiguous()
+    ay = b.a_view(a, pr.y).contiguous()
+    lam = float(np.float32(pr.lam))
+    if with_mask:
+        dm = pr.mask.astype(np.float64)
+        mask_dev = torch.from_numpy(pr.mask.astype(np.float32)).cuda()
+        evx = evy = None
+    else:
+        ev = b.evals
+        evx = ev[b.layout.evals_off[pr.x]:b.layout.evals_off[pr.x] + k].contiguous()
+        evy = ev[b.layout.evals_off[pr.y]:b.layout.evals_off[pr.y] + k].contiguous()
+        dm = orc.mask_from_evals(evx.double().cpu().numpy(), evy.double().cpu().numpy())
+        mask_dev = None
+    c_ref = orc.solve(ax.double().cpu().numpy(), ay.double().cpu().numpy(), dm, lam)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        c = torch.full((k, k), float("nan"), dtype=torch.float32, device="cuda")
+        rc = lib.fmap_solve_pair_noalloc(_ptr(ax), _ptr(ay), k, d,
+                                         None if evx is None else _ptr(evx), None if evy is None else _ptr(evy),
+                                         None if mask_dev is None else _ptr(mask_dev), ctypes.c_float(lam), 1,
+                                         _ptr(c), _ptr(status), stream)
+        assert rc == 0, _lib.error_string(rc)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        got = c.double().cpu().numpy()
+        err = float(np.linalg.norm(got - c_ref) / np.linalg.norm(c_ref))
+        assert err <= TOL, (k, with_mask, err)
