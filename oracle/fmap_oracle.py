@@ -30,6 +30,13 @@ The backward pass (not in the paper) is the adjoint of Eq. 5 derived by hand:
 gamma_i = S_i^{-1} dL/dc_i, dB = Gamma A, dA = Gamma^T B - (Gamma^T C + C^T Gamma) A,
 dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C), dF = M Phi dA.
 
+Spatial gradient features (Sec. "Learned Scaling and Rotation in DiffusionNet"): the
+complex per-vertex gradients z = G X of features X under a sparse complex gradient
+operator G, a learned complex D x D matrix A, and the real features g = Re(conj(z) o Az),
+in the paper's real decomposition; variant A (rotation and isotropic scaling) and
+variant B (the other indexing of the imaginary part: fixed +-45 degree rotations and
+anisotropic scaling).
+
 Overlap metrics (Sec. "Overlap Prediction Metrics"): confusion counts of a thresholded
 per-vertex overlap prediction against binary labels, and IoU, accuracy, precision,
 recall, specificity, F1 and balanced accuracy from them.
@@ -38,8 +45,11 @@ Parity pins: every function here is checked against something other than itself
 in tests/test_oracle_pins.py (Kronecker k^2 x k^2 solve, lambda = 0 closed form,
 identity case, energy minimality, exact rational solve, Moore-Penrose inverse,
 finite differences, LAPACK; for the overlap metrics the paper's closed forms for the
-Zeros / Ones / Random predictors and brute-force counting). No function is "parity
-unpinned".
+Zeros / Ones / Random predictors and brute-force counting; for the spatial gradient
+features the complex form Re(conj(z) o Az), the paper's per-channel 2 x 2 block sums by
+brute force, the diagonal closed form s |z|^2 cos(theta), invariance under a global
+rotation of the tangent frames (variant A only) and the dense operator product). No
+function is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -231,6 +241,42 @@ def backward_batch(shapes, pairs, fwd, d_c_list):
         extra.append(g)
     d_f = [project_backward(s["phi"], s["mass"], da) for s, da in zip(shapes, d_a)]
     return dict(dA=d_a, dF=d_f, pair=extra)
+
+
+# --------------------------------------------------------------------------
+# Spatial gradient features (Sec. "Learned Scaling and Rotation in DiffusionNet")
+# --------------------------------------------------------------------------
+def gradient_apply(row_ptr, col_idx, g_re, g_im, feat):
+    """z = G X for a sparse complex gradient operator G (CSR: row_ptr, col_idx, values
+    g_re + i g_im) and real features X (n x D). Returns (x, y) = (Re z, Im z), each n x D:
+    x_v = sum_u Re(G_vu) X_u, y_v = sum_u Im(G_vu) X_u."""
+    import scipy.sparse as sp
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    n = len(row_ptr) - 1
+    feat = np.asarray(feat, dtype=np.float64)
+    gx = sp.csr_matrix((np.asarray(g_re, np.float64), np.asarray(col_idx), row_ptr), shape=(n, feat.shape[0]))
+    gy = sp.csr_matrix((np.asarray(g_im, np.float64), np.asarray(col_idx), row_ptr), shape=(n, feat.shape[0]))
+    return np.asarray(gx @ feat), np.asarray(gy @ feat)
+
+
+def spatial_gradient_features(x, y, a_re, a_im, variant="A"):
+    """g (n x D) from the per-vertex tangent vectors z = x + i y (rows of x, y) and the
+    learned complex matrix A = a_re + i a_im (D x D, (Az)_i = sum_j A_ij z_j):
+      (Az)_re = A_re x - A_im y,
+      (Az)_im = A_re y + A_im x   (variant A)   or   A_re x + A_im y   (variant B),
+      g = x o (Az)_re + y o (Az)_im."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    a_re = np.asarray(a_re, dtype=np.float64)
+    a_im = np.asarray(a_im, dtype=np.float64)
+    az_re = x @ a_re.T - y @ a_im.T
+    if variant == "A":
+        az_im = y @ a_re.T + x @ a_im.T
+    elif variant == "B":
+        az_im = x @ a_re.T + y @ a_im.T
+    else:
+        raise ValueError("variant must be 'A' or 'B'")
+    return x * az_re + y * az_im
 
 
 # --------------------------------------------------------------------------

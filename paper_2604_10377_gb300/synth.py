@@ -211,3 +211,56 @@ def make_small(seed: int, npairs: int, n_range, ks, d: int, feat_dtype: str = "f
         gt = random_orthogonal(seed * 7919 + 100003 + p, k)
         pairs.append(Pair(x=len(shapes) - 2, y=len(shapes) - 1, lam=lam, mask=mask, c_gt=gt))
     return Workload(name=f"small{seed}", shapes=shapes, pairs=pairs, feat_dtype=feat_dtype)
+
+
+# ---------------------------------------------------------------- spatial gradient inputs
+@dataclasses.dataclass
+class GradientInput:
+    """Inputs of the spatial-gradient feature kernel for one shape: a sparse complex
+    gradient operator in CSR form (n x n, values g_re + i g_im), FP32 features X (n x D)
+    and a learned complex D x D matrix A = a_re + i a_im."""
+    n: int
+    dim: int
+    row_ptr: np.ndarray    # (n + 1,) int64
+    col_idx: np.ndarray    # (nnz,) int32, sorted within each row
+    g_re: np.ndarray       # (nnz,) float32
+    g_im: np.ndarray       # (nnz,) float32
+    feat: np.ndarray       # (n, D) float32
+    a_re: np.ndarray       # (D, D) float32
+    a_im: np.ndarray       # (D, D) float32
+
+
+def make_gradient_input(seed: int, n: int, dim: int, nbrs: int = 6, window: int = 64) -> GradientInput:
+    """A random stand-in for a mesh gradient operator: every vertex has itself and `nbrs`
+    distinct other vertices within +-`window` indices (the locality of a vertex ordering
+    along a mesh), off-diagonal complex values N(0, 1) / sqrt(nbrs), and a diagonal value
+    that makes every row sum to zero (the gradient of a constant field vanishes). X is
+    N(0, 1); A has N(0, 1 / D) entries."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows, cols = [], []
+    ptr = np.zeros(n + 1, np.int64)
+    for v in range(n):
+        lo, hi = max(0, v - window), min(n, v + window + 1)
+        cand = np.arange(lo, hi)
+        cand = cand[cand != v]
+        k = min(nbrs, len(cand))
+        nb = np.sort(rng.choice(cand, size=k, replace=False)) if k > 0 else np.zeros(0, np.int64)
+        c = np.sort(np.concatenate([nb, [v]]))
+        cols.append(c)
+        ptr[v + 1] = ptr[v] + len(c)
+    col = np.concatenate(cols).astype(np.int32)
+    nnz = len(col)
+    re = (rng.standard_normal(nnz) / np.sqrt(max(nbrs, 1))).astype(np.float64)
+    im = (rng.standard_normal(nnz) / np.sqrt(max(nbrs, 1))).astype(np.float64)
+    for v in range(n):
+        s, e = ptr[v], ptr[v + 1]
+        d = s + int(np.nonzero(col[s:e] == v)[0][0])
+        re[d] = 0.0
+        im[d] = 0.0
+        re[d] = -re[s:e].sum()
+        im[d] = -im[s:e].sum()
+    feat = rng.standard_normal((n, dim), dtype=np.float32)
+    a_re = (rng.standard_normal((dim, dim)) / np.sqrt(dim)).astype(np.float32)
+    a_im = (rng.standard_normal((dim, dim)) / np.sqrt(dim)).astype(np.float32)
+    return GradientInput(n=n, dim=dim, row_ptr=ptr, col_idx=col, g_re=re.astype(np.float32),
+                         g_im=im.astype(np.float32), feat=feat, a_re=a_re, a_im=a_im)

@@ -486,3 +486,89 @@ def test_overlap_undefined_ratios_are_nan():
     m = orc.overlap_metrics(0, 0, 0, 10)       # no positives predicted or present
     assert np.isnan(m[0]) and np.isnan(m[3]) and np.isnan(m[4]) and np.isnan(m[6])
     assert m[2] == 1.0 and m[5] == 1.0 and np.isnan(m[1])
+
+
+# ---------------------------------------------------------------- spatial gradient features
+def _grad_case(seed=3, n=9, dim=5):
+    from paper_2604_10377_gb300 import synth
+    gi = synth.make_gradient_input(seed, n, dim, nbrs=3, window=4)
+    x, y = orc.gradient_apply(gi.row_ptr, gi.col_idx, gi.g_re, gi.g_im, gi.feat)
+    return gi, x, y
+
+
+def test_gradient_apply_is_the_dense_operator_product():
+    """z = G X against the densified complex operator times X (numpy matmul)."""
+    gi, x, y = _grad_case()
+    g = np.zeros((gi.n, gi.n), complex)
+    for v in range(gi.n):
+        for e in range(gi.row_ptr[v], gi.row_ptr[v + 1]):
+            g[v, gi.col_idx[e]] += complex(float(gi.g_re[e]), float(gi.g_im[e]))
+    z = g @ gi.feat.astype(np.float64)
+    assert np.allclose(x, z.real, rtol=0, atol=1e-12) and np.allclose(y, z.imag, rtol=0, atol=1e-12)
+    # rows sum to zero: a constant field has no gradient
+    xc, yc = orc.gradient_apply(gi.row_ptr, gi.col_idx, gi.g_re, gi.g_im, np.ones((gi.n, 2)))
+    assert np.abs(xc).max() < 1e-6 and np.abs(yc).max() < 1e-6
+
+
+def test_variant_a_is_re_conj_z_times_az():
+    """Variant A written in the paper's real decomposition equals Re(conj(z) o Az) in
+    complex arithmetic."""
+    gi, x, y = _grad_case()
+    z = x + 1j * y
+    a = gi.a_re.astype(np.float64) + 1j * gi.a_im.astype(np.float64)
+    want = np.real(np.conj(z) * (z @ a.T))
+    got = orc.spatial_gradient_features(x, y, gi.a_re, gi.a_im, "A")
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("variant", ["A", "B"])
+def test_variants_are_the_per_channel_2x2_block_sums(variant):
+    """g_i = sum_j v_i^T M_ij v_j with v_j = (x_j, y_j) and M_ij = [[a, -b], [b, a]]
+    (variant A) or [[a, -b], [a, b]] (variant B), a = Re A_ij, b = Im A_ij: brute force."""
+    gi, x, y = _grad_case(seed=4, n=4, dim=3)
+    got = orc.spatial_gradient_features(x, y, gi.a_re, gi.a_im, variant)
+    for v in range(gi.n):
+        for i in range(gi.dim):
+            acc = 0.0
+            for j in range(gi.dim):
+                a, b = float(gi.a_re[i, j]), float(gi.a_im[i, j])
+                m = [[a, -b], [b, a]] if variant == "A" else [[a, -b], [a, b]]
+                vi, vj = (x[v, i], y[v, i]), (x[v, j], y[v, j])
+                acc += sum(vi[p] * m[p][q] * vj[q] for p in range(2) for q in range(2))
+            assert abs(got[v, i] - acc) <= 1e-12 * max(1.0, abs(acc))
+
+
+def test_diagonal_rotation_scaling_closed_form():
+    """A = diag(s e^{i theta}) (variant A): g = s |z|^2 cos(theta) per channel."""
+    gi, x, y = _grad_case(seed=5)
+    rng = np.random.default_rng(0)
+    s = rng.uniform(0.5, 2.0, gi.dim)
+    th = rng.uniform(-np.pi, np.pi, gi.dim)
+    g = orc.spatial_gradient_features(x, y, np.diag(s * np.cos(th)), np.diag(s * np.sin(th)), "A")
+    assert np.allclose(g, s * (x * x + y * y) * np.cos(th), rtol=1e-12, atol=1e-12)
+    # variant B with diagonal A: a x^2 + (a - b) x y + b y^2
+    a, b = s * np.cos(th), s * np.sin(th)
+    gb = orc.spatial_gradient_features(x, y, np.diag(a), np.diag(b), "B")
+    assert np.allclose(gb, a * x * x + (a - b) * x * y + b * y * y, rtol=1e-12, atol=1e-12)
+
+
+def test_tangent_frame_rotation_invariance_of_variant_a_only():
+    """Rotating every tangent frame by one angle (z -> e^{i phi} z) leaves variant A's
+    features unchanged and changes variant B's (fixed +-45 degree family)."""
+    gi, x, y = _grad_case(seed=6)
+    phi = 0.7
+    xr = np.cos(phi) * x - np.sin(phi) * y
+    yr = np.sin(phi) * x + np.cos(phi) * y
+    ga = orc.spatial_gradient_features(x, y, gi.a_re, gi.a_im, "A")
+    assert np.allclose(orc.spatial_gradient_features(xr, yr, gi.a_re, gi.a_im, "A"), ga, rtol=1e-11, atol=1e-11)
+    gb = orc.spatial_gradient_features(x, y, gi.a_re, gi.a_im, "B")
+    assert not np.allclose(orc.spatial_gradient_features(xr, yr, gi.a_re, gi.a_im, "B"), gb, rtol=1e-3, atol=1e-6)
+
+
+def test_planted_variant_mistakes_are_caught():
+    """Swapping the variants or flipping the sign of Im A breaks the 2 x 2 block form."""
+    gi, x, y = _grad_case(seed=7)
+    ga = orc.spatial_gradient_features(x, y, gi.a_re, gi.a_im, "A")
+    gb = orc.spatial_gradient_features(x, y, gi.a_re, gi.a_im, "B")
+    assert not np.allclose(ga, gb, rtol=1e-6)
+    assert not np.allclose(orc.spatial_gradient_features(x, y, gi.a_re, -gi.a_im, "A"), ga, rtol=1e-6)
