@@ -711,6 +711,85 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
     return out
 
 
+GRADFEAT_WORKLOAD = ("spatial gradient features (DiffusionNet, Sec. 'Learned Scaling and Rotation'): 64 shapes, "
+                     "n log-uniform 1k-100k, D=128 channels, one block-diagonal complex gradient operator "
+                     "(7 entries per row), BF16 features out")
+
+
+def bench_gradient_features(args, dev, peaks, measured, uuid):
+    """fmap_gradient_features over a batch of 64 shapes stored as one block-diagonal CSR
+    operator (n log-uniform in 1k..100k per shape, D = 128), variants A and B, BF16 output
+    rows of width D: vertices/s and the roofline of the kernel (HBM bytes: X read once, the
+    CSR read once, F written once; tensor flops: 2 n (2D)^2)."""
+    import numpy as np
+    import torch
+    from paper_2604_10377_gb300 import api, synth
+    rng = np.random.Generator(np.random.PCG64(synth.BASE_SEED + 7000))
+    dim = 128
+    ns = [int(round(np.exp(rng.uniform(np.log(1000), np.log(100000))))) for _ in range(64)]
+    t_gen = time.time()
+    parts = [synth.make_gradient_input(synth.BASE_SEED + 7001 + i, n, dim) for i, n in enumerate(ns)]
+    off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    row_ptr = [np.zeros(1, np.int64)]
+    eoff = 0
+    for p_, o in zip(parts, off[:-1]):
+        row_ptr.append(p_.row_ptr[1:] + eoff)
+        eoff += int(p_.row_ptr[-1])
+    row_ptr = torch.from_numpy(np.concatenate(row_ptr)).to(dev)
+    col = torch.from_numpy(np.concatenate([p_.col_idx + np.int32(o) for p_, o in zip(parts, off[:-1])])).to(dev)
+    vals = torch.from_numpy(np.concatenate([np.stack([p_.g_re, p_.g_im], 1) for p_ in parts])).to(dev)
+    x = torch.from_numpy(np.concatenate([p_.feat for p_ in parts])).to(dev)
+    a_re, a_im = torch.from_numpy(parts[0].a_re).to(dev), torch.from_numpy(parts[0].a_im).to(dev)
+    t_gen = time.time() - t_gen
+    n = int(off[-1])
+    nnz = int(col.numel())
+    out = torch.empty((n, dim), dtype=torch.bfloat16, device=dev)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    sampler = ClockSampler(uuid) if uuid else None
+    if sampler:
+        sampler.start()
+    for variant in ("A", "B"):
+        for _ in range(max(3, args.warmup)):
+            api.gradient_features(row_ptr, col, vals, x, a_re, a_im, variant=variant, out=out, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            _, status = api.gradient_features(row_ptr, col, vals, x, a_re, a_im, variant=variant, out=out, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[variant] = {"ms_per_call": ms, "vertices_per_s": n / (ms * 1e-3), "status": int(status.item())}
+    clocks = sampler.stop() if sampler else None
+    nbytes = n * dim * 4 + (n + 1) * 8 + nnz * 12 + n * dim * 2 + (2 * dim) ** 2 * 4
+    flops = 2.0 * n * (2 * dim) ** 2
+    ms = min(r["ms_per_call"] for r in res.values())
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    tfl = flops / (ms * 1e-3) / 1e12
+    tf32 = measured["tf32_mma"] if measured else None
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    ten_frac = tfl / tf32 if tf32 else None
+    bound = "tensor" if (ten_frac is not None and (flops / (tf32 * 1e12)) > nbytes / (peaks["hbm_gbs"] * 1e9)) else "hbm"
+    # accuracy: the first shape's rows against the FP64 oracle (variant B ran last)
+    from oracle import fmap_oracle as orc
+    p0 = parts[0]
+    gx, gy = orc.gradient_apply(p0.row_ptr, p0.col_idx, p0.g_re, p0.g_im, p0.feat)
+    ref = orc.spatial_gradient_features(gx, gy, p0.a_re, p0.a_im, "B")
+    got = out[:p0.n].float().cpu().numpy()
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"workload": GRADFEAT_WORKLOAD, "vertices": n, "nnz": nnz, "variants": res,
+            "roofline": {"bound": bound, "achieved": gbs if bound == "hbm" else tfl,
+                         "peak": peaks["hbm_gbs"] if bound == "hbm" else tf32,
+                         "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+                         "frac": hbm_frac if bound == "hbm" else ten_frac,
+                         "hbm": {"achieved_gbs": gbs, "frac": hbm_frac, "algorithmic_bytes": nbytes},
+                         "tensor": {"achieved_tflops": tfl, "frac": ten_frac, "algorithmic_flops": flops,
+                                    "peak": "measured tf32_mma"}},
+            "accuracy": {"rows": p0.n, "rel_fro": err, "tolerance": 3e-3, "reference": "FP64 oracle, BF16 output"},
+            "clocks": clocks, "gen_s": round(t_gen, 1)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -739,6 +818,9 @@ def run_ours(args):
                            "best of 3, CUDA events")
 
     main = bench_workload(args.workload, args, dev, peaks, measured, uuid, rank, world, full=True)
+    gradfeat = None
+    if world == 1 and not args.no_sub_workloads:
+        gradfeat = bench_gradient_features(args, dev, peaks, measured, uuid)
     subs = None
     if world == 1 and not args.no_sub_workloads:
         # the other workloads of the hot path, each timed the same way (one line, one key)
@@ -757,6 +839,7 @@ def run_ours(args):
         line.update({k: v for k, v in main.items() if k not in ("value", "ms_per_step")})
         line["peaks_measured"] = measured
         line["workloads"] = subs
+        line["gradient_features"] = gradfeat
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -254,6 +254,39 @@ enum fmap_peak_kind {
 FMAP_API int32_t fmap_peak_loop(int32_t kind, int32_t blocks, int64_t iters, void* sink, double* flops_per_launch,
                                 void* stream);
 
+/* ---- Spatial gradient features (Sec. "Learned Scaling and Rotation in DiffusionNet") --
+ * The upstream producer of the features F of a shape, fused in one kernel that writes F
+ * straight into the layout fmap_shape_desc.feat describes. For every vertex v:
+ *   z_v = sum_u G_vu X_u                     complex per-channel gradients, z = x + i y
+ *   (Az)_re = A_re x - A_im y
+ *   (Az)_im = A_re y + A_im x   (variant 0, "A": rotation and isotropic scaling)
+ *           = A_re x + A_im y   (variant 1, "B": fixed +-45 degree rotations, anisotropic scaling)
+ *   out[v, c] = x_c (Az)_re,c + y_c (Az)_im,c      (= Re(conj(z) o Az) for variant A)
+ * with (Az)_i = sum_j A_ij z_j. The D x D complex product runs on the tensor cores
+ * (tcgen05 kind::tf32: x, y truncated to TF32, A rounded to TF32, FP32 accumulation;
+ * relative error ~1e-3), the gather and the final products in FP32.
+ *   n           output vertices (rows of G), >= 0 (0: nothing is enqueued)
+ *   row_ptr     device int64[n + 1], CSR row offsets of G into col_idx / g_vals
+ *   col_idx     device int32[nnz], columns of G (vertices of X), each in [0, n_in)
+ *   g_vals      device float[2 nnz]: (Re G_vu, Im G_vu) pairs, 8-byte aligned
+ *   x_in        device FP32 n_in x ld_in (ld_in >= dim, multiple of 4; 16-byte aligned)
+ *   dim         D: multiple of 16, 16..128
+ *   a_re, a_im  device FP32 D x D row-major
+ *   out         device n x ld_out, FP32 or BF16 (out_dtype = enum fmap_precision); ld_out
+ *               >= dim, multiple of 8; 16-byte aligned. Columns past dim are not written.
+ *   status      device int32[1]: set to 0 by the call, then FMAP_ERR_INVALID_ARG if a CSR
+ *               offset or column index was out of range (that entry is skipped) or
+ *               FMAP_ERR_TIMEOUT if a bounded device wait gave up
+ *   ws          device workspace of >= fmap_gradient_features_ws_bytes(dim) bytes, 256-byte
+ *               aligned (the tensor-core image of A, rebuilt by every call)
+ * Enqueues on stream; no allocation. Calls sharing a workspace must not overlap. */
+FMAP_API size_t fmap_gradient_features_ws_bytes(int32_t dim);
+FMAP_API int32_t fmap_gradient_features(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                        const float* g_vals, int64_t nnz, int64_t n_in, const float* x_in,
+                                        int64_t ld_in, int32_t dim, const float* a_re, const float* a_im,
+                                        int32_t variant, void* out, int64_t ld_out, int32_t out_dtype,
+                                        int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- Overlap-prediction metrics (Sec. "Overlap Prediction Metrics") ---------------
  * For segments s = 0 .. n_segments-1 of flat per-vertex arrays (the vertices of one
  * shape, or of one pair's predicted overlap region): a vertex is predicted overlapping

@@ -86,6 +86,10 @@ _PROTOS = {
     "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),
     "fmap_solve_pair_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                           c_float, c_int32, c_void_p, c_void_p, c_void_p]),
+    "fmap_gradient_features_ws_bytes": (c_size_t, [c_int32]),
+    "fmap_gradient_features": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int64,
+                                         c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32, c_void_p,
+                                         c_void_p, c_size_t, c_void_p]),
     "fmap_peak_loop": (c_int32, [c_int32, c_int32, c_int64, c_void_p, POINTER(ctypes.c_double), c_void_p]),
     "fmap_overlap_metrics": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_float, c_void_p, c_void_p,
                                        c_void_p]),

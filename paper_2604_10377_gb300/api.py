@@ -427,6 +427,41 @@ def overlap_metrics(scores: torch.Tensor, labels: torch.Tensor, seg_offsets, thr
     return counts, (metrics[:n_seg] if metrics is not None else None)
 
 
+def gradient_features(row_ptr: torch.Tensor, col_idx: torch.Tensor, g_vals: torch.Tensor, x_in: torch.Tensor,
+                      a_re: torch.Tensor, a_im: torch.Tensor, variant: str = "A", out: Optional[torch.Tensor] = None,
+                      out_dtype=torch.float32, ws: Optional[torch.Tensor] = None):
+    """Spatial gradient features (fmap_gradient_features): F = Re(conj(z) o Az) (variant A)
+    or the variant-B form, z = G X, written into `out` (n x ld_out rows of out_dtype; a new
+    n x D tensor when None). row_ptr int64 (n+1,), col_idx int32 (nnz,), g_vals float32
+    (nnz, 2) = (Re, Im), x_in float32 (n_in, ld_in) with D = a_re.shape[0] used columns.
+    Returns (out, status int32 (1,) device tensor); the call only enqueues."""
+    dev = x_in.device
+    n = row_ptr.numel() - 1
+    dim = a_re.shape[0]
+    if out is None:
+        out = torch.empty((max(n, 0), dim), dtype=out_dtype, device=dev)
+    bf16 = out.dtype == torch.bfloat16
+    if out.dtype not in (torch.bfloat16, torch.float32):
+        raise TypeError("out must be float32 or bfloat16")
+    for t, dt in ((row_ptr, torch.int64), (col_idx, torch.int32), (g_vals, torch.float32), (x_in, torch.float32),
+                  (a_re, torch.float32), (a_im, torch.float32)):
+        if t.dtype != dt or t.device != dev or not t.is_contiguous():
+            raise ValueError("gradient_features: wrong dtype, device or layout of an input")
+    L = _lib.lib()
+    need = int(L.fmap_gradient_features_ws_bytes(int(dim)))
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ld_in = x_in.stride(0) if x_in.dim() == 2 else dim
+    ld_out = out.stride(0) if out.dim() == 2 else dim
+    check(L.fmap_gradient_features(int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(g_vals), int(col_idx.numel()),
+                                   int(x_in.shape[0]), _ptr(x_in), int(ld_in), int(dim), _ptr(a_re), _ptr(a_im),
+                                   0 if variant == "A" else 1, _ptr(out), int(ld_out),
+                                   _lib.FMAP_PREC_BF16 if bf16 else _lib.FMAP_PREC_FP32, _ptr(status), _ptr(ws),
+                                   ws.numel(), _stream(dev)), "fmap_gradient_features")
+    return out, status
+
+
 def batch_from_workload(wl, device="cuda:0", with_grad=True, **kw) -> FmapBatch:
     """Allocate a batch for a synth.Workload and upload its inputs."""
     lay = BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)

@@ -27,6 +27,7 @@ SOURCES = [
     "k_overlap.cu",
     "fmap_noalloc.cu",
     "k_peaks.cu",
+    "k_gradfeat.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

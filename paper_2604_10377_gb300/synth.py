@@ -231,34 +231,35 @@ class GradientInput:
 
 
 def make_gradient_input(seed: int, n: int, dim: int, nbrs: int = 6, window: int = 64) -> GradientInput:
-    """A random stand-in for a mesh gradient operator: every vertex has itself and `nbrs`
-    distinct other vertices within +-`window` indices (the locality of a vertex ordering
-    along a mesh), off-diagonal complex values N(0, 1) / sqrt(nbrs), and a diagonal value
-    that makes every row sum to zero (the gradient of a constant field vanishes). X is
-    N(0, 1); A has N(0, 1 / D) entries."""
+    """A random stand-in for a mesh gradient operator: every vertex has itself and up to
+    `nbrs` distinct other vertices within +-`window` indices (the locality of a vertex
+    ordering along a mesh; offsets that fall outside [0, n) are dropped), off-diagonal
+    complex values N(0, 1) / sqrt(nbrs), and a diagonal value that makes every row sum to
+    zero (the gradient of a constant field vanishes). X is N(0, 1); A has N(0, 1 / D)
+    entries."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    rows, cols = [], []
-    ptr = np.zeros(n + 1, np.int64)
-    for v in range(n):
-        lo, hi = max(0, v - window), min(n, v + window + 1)
-        cand = np.arange(lo, hi)
-        cand = cand[cand != v]
-        k = min(nbrs, len(cand))
-        nb = np.sort(rng.choice(cand, size=k, replace=False)) if k > 0 else np.zeros(0, np.int64)
-        c = np.sort(np.concatenate([nb, [v]]))
-        cols.append(c)
-        ptr[v + 1] = ptr[v] + len(c)
-    col = np.concatenate(cols).astype(np.int32)
+    pool = np.concatenate([np.arange(-window, 0), np.arange(1, window + 1)])
+    k = min(nbrs, len(pool))
+    pick = np.argsort(rng.random((n, len(pool))), axis=1)[:, :k]
+    cols = np.arange(n)[:, None] + pool[pick]
+    cols = np.concatenate([cols, np.arange(n)[:, None]], axis=1)          # the vertex itself last
+    valid = (cols >= 0) & (cols < n)
+    cols = np.where(valid, cols, n)                                       # invalid entries sort to the end
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    valid = np.take_along_axis(valid, order, axis=1)
+    counts = valid.sum(axis=1)
+    ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    col = cols[valid].astype(np.int32)
     nnz = len(col)
-    re = (rng.standard_normal(nnz) / np.sqrt(max(nbrs, 1))).astype(np.float64)
-    im = (rng.standard_normal(nnz) / np.sqrt(max(nbrs, 1))).astype(np.float64)
-    for v in range(n):
-        s, e = ptr[v], ptr[v + 1]
-        d = s + int(np.nonzero(col[s:e] == v)[0][0])
-        re[d] = 0.0
-        im[d] = 0.0
-        re[d] = -re[s:e].sum()
-        im[d] = -im[s:e].sum()
+    re = rng.standard_normal(nnz) / np.sqrt(max(nbrs, 1))
+    im = rng.standard_normal(nnz) / np.sqrt(max(nbrs, 1))
+    row = np.repeat(np.arange(n), counts)
+    diag = col == row
+    re[diag] = 0.0
+    im[diag] = 0.0
+    re[diag] = -np.bincount(row, weights=re, minlength=n)
+    im[diag] = -np.bincount(row, weights=im, minlength=n)
     feat = rng.standard_normal((n, dim), dtype=np.float32)
     a_re = (rng.standard_normal((dim, dim)) / np.sqrt(dim)).astype(np.float32)
     a_im = (rng.standard_normal((dim, dim)) / np.sqrt(dim)).astype(np.float32)
