@@ -6,17 +6,22 @@
 // row's 8-column tile segment is two aligned float4 and consecutive rows fall on
 // different banks). The Gram kernel leaves G in that layout too, so one bulk copy
 // loads it; then lambda D_i is added to the diagonal. The factorisation is a blocked
-// left-looking Cholesky in FP32 with column blocks of 8: block column J is formed once
-// from the finished columns of L (the rows of the diagonal block are broadcast reads,
-// the K range is split over threads when few rows remain), warp 0 forms and factors the
-// 8 x 8 diagonal block (storing its inverse) and applies it to the right-hand side
-// (forward substitution bordered into the factorisation), and every thread then finishes
-// one row below the block and solves it against L_JJ^T (TRSM). Two block barriers per
-// column block, and each entry of S is written once.
-// The back substitution and the refinement's triangular solves use every warp with the
-// inverses of 16-row diagonal blocks (one barrier per 16 rows); `ir_steps` steps of
-// iterative refinement take the residual rhs - S x in FP32, for hi_gram pairs with G as
-// the two FP32 halves (hi + lo) of its double-float accumulation.
+// right-looking Cholesky in FP32 with 8-column panels and one panel of lookahead:
+//   TRSM     every thread solves one row of panel J below its diagonal block,
+//            x = s L_JJ^-T, as a product with the stored inverse block; one warp
+//            applies L_JJ^-1 to the right-hand side (forward substitution bordered
+//            into the factorisation);
+//   (a)      every thread updates one row of the next column block J+1 and its
+//            right-hand side entry;
+//   (b)      warp 0 factors the diagonal block J+1 in registers and stores its
+//            inverse, while the other warps update the rest of the trailing matrix
+//            in 8x4 or 4x4 register tiles (whichever balances best),
+//            S_AB -= L_AJ L_BJ^T.
+// (a) and (b) touch disjoint blocks, so a panel costs two block barriers. The back
+// substitution and the refinement's triangular solves use every warp with the inverses
+// of 16-row diagonal blocks (one barrier per 16 rows); `ir_steps` steps of iterative refinement
+// take the residual rhs - S x in FP32, for hi_gram pairs with G as the two FP32
+// halves (hi + lo) of its double-float accumulation.
 #include <math.h>
 
 #include "fmap_internal.cuh"
@@ -95,6 +100,58 @@ __device__ __forceinline__ bool diag_block(float* S, float* linv, int J, int lan
   bad = __shfl_sync(0xffffffffu, bad ? 1 : 0, 0) != 0;
   __syncwarp();
   return !bad;
+}
+
+// Row index of entry t of a lower triangle enumerated row by row (t = a(a+1)/2 + b).
+__device__ __forceinline__ void tri_decode(int t, int& a, int& b) {
+  int ai = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((ai + 1) * (ai + 2) / 2 <= t) ++ai;
+  while (ai * (ai + 1) / 2 > t) --ai;
+  a = ai;
+  b = t - ai * (ai + 1) / 2;
+}
+
+// S[A.., B..] -= L[A.., J] L[B.., J]^T for one R x C tile (R, C in {4, 8}), with the
+// panel's 8 columns read from `pan` (column-major, leading dimension kp).
+template <int R, int C>
+__device__ __forceinline__ void trail_tile(float* S, const float* pan, int kp, int A, int B) {
+  float acc[R][C];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float4* sr = reinterpret_cast<const float4*>(S + rowoff(A + r) + B);
+#pragma unroll
+    for (int h = 0; h < C / 4; ++h) {
+      const float4 u = sr[h];
+      acc[r][4 * h] = u.x; acc[r][4 * h + 1] = u.y; acc[r][4 * h + 2] = u.z; acc[r][4 * h + 3] = u.w;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float la[R], lb[C];
+    const float4* pa = reinterpret_cast<const float4*>(pan + c * kp + A);
+    const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + B);
+#pragma unroll
+    for (int h = 0; h < R / 4; ++h) {
+      const float4 u = pa[h];
+      la[4 * h] = u.x; la[4 * h + 1] = u.y; la[4 * h + 2] = u.z; la[4 * h + 3] = u.w;
+    }
+#pragma unroll
+    for (int h = 0; h < C / 4; ++h) {
+      const float4 u = pb[h];
+      lb[4 * h] = u.x; lb[4 * h + 1] = u.y; lb[4 * h + 2] = u.z; lb[4 * h + 3] = u.w;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int q = 0; q < C; ++q) acc[r][q] = fmaf(-la[r], lb[q], acc[r][q]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float4* sr = reinterpret_cast<float4*>(S + rowoff(A + r) + B);
+#pragma unroll
+    for (int h = 0; h < C / 4; ++h)
+      sr[h] = make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+  }
 }
 
 // The triangular solves work on 16-row blocks p (rows 16p .. 16p+15; the last block has
@@ -362,108 +419,31 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
     for (int a = tid; a < k; a += NT) S[rowoff(a) + a] += dg[a];
     for (int a = tid; a < kp; a += NT) v[a] = rh[a];   // right-hand side, reduced during the factorisation
     __syncthreads();
-    // Left-looking blocked factorisation, column blocks of 8 (r0 = 8 J): block column J is
-    // formed once from the finished columns 0 .. r0-1 of L,
-    //   S[a, J] -= L[a, 0:r0] L[J, 0:r0]^T        (rows a >= r0),
-    // so every entry of S is written once (no read-modify-write of the trailing matrix per
-    // panel). Phase A: warp 0 forms the diagonal block's rows and the right-hand side's
-    // border v_J -= L[J, 0:r0] y, factors the 8 x 8 block (storing its inverse) and solves
-    // y_J = L_JJ^-1 v_J (forward substitution bordered into the factorisation), while the
-    // other warps form partial sums of the rows below over slices of the K range (rows x
-    // slices spread over the threads; the J rows' values are broadcast reads). Phase B: one
-    // thread per row adds its slices' partial sums in a fixed order and solves against
-    // L_JJ^T (TRSM). Two block barriers per column block.
-    float* red = pan;   // partial sums: 8 floats per (slice, row), at most kp (slice, row) pairs
-    for (int J = 0; J < Q; ++J) {
+    if (warp == 0 && !diag_block(S, linv, 0, lane) && lane == 0) s_bad = 1;
+    __syncthreads();
+    for (int J = 0; J < Q && !s_bad; ++J) {
       const int r0 = 8 * J;
-      const int m = kp - r0 - 8;   // rows below the diagonal block
-      // K slices of the rows below: a power of two, at most one (slice, row) per thread of
-      // warps 1.., at most kp pairs (the buffer), at least 8 columns per slice
-      int nsl = 1;
-      while (2 * nsl * m <= NT - 32 && 2 * nsl * m <= kp && r0 >= 16 * nsl) nsl *= 2;
-      const int chunk = ((r0 / nsl) + 3) & ~3;
-      if (warp == 0) {
-        // lane = (row i0 = lane / 8 and i0 + 4, column c = lane % 8) of the diagonal block,
-        // four partial sums per entry (one per float4 component)
-        const int i0 = lane >> 3, c = lane & 7;
-        const float* ra = S + rowoff(r0 + i0);
-        const float* rb = S + rowoff(r0 + i0 + 4);
-        const float* rc = S + rowoff(r0 + c);
-        float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int kk = 0; kk < r0; kk += 4) {
-          const float4 a4 = *reinterpret_cast<const float4*>(ra + kk);
-          const float4 b4 = *reinterpret_cast<const float4*>(rb + kk);
-          const float4 c4 = *reinterpret_cast<const float4*>(rc + kk);
-          s0[0] = fmaf(a4.x, c4.x, s0[0]); s0[1] = fmaf(a4.y, c4.y, s0[1]);
-          s0[2] = fmaf(a4.z, c4.z, s0[2]); s0[3] = fmaf(a4.w, c4.w, s0[3]);
-          s1[0] = fmaf(b4.x, c4.x, s1[0]); s1[1] = fmaf(b4.y, c4.y, s1[1]);
-          s1[2] = fmaf(b4.z, c4.z, s1[2]); s1[3] = fmaf(b4.w, c4.w, s1[3]);
-        }
-        // border of the right-hand side: v[r0 + c] -= L[r0 + c, 0:r0] y, the K range in four
-        // interleaved parts (lane / 8), summed by shuffles
-        float t = 0.f;
-        for (int kk = 4 * i0; kk < r0; kk += 16) {
-          const float4 l4 = *reinterpret_cast<const float4*>(rc + kk);
-          const float4 y4 = *reinterpret_cast<const float4*>(v + kk);
-          t = fmaf(l4.x, y4.x, t); t = fmaf(l4.y, y4.y, t); t = fmaf(l4.z, y4.z, t); t = fmaf(l4.w, y4.w, t);
-        }
-        t += __shfl_xor_sync(0xffffffffu, t, 8);
-        t += __shfl_xor_sync(0xffffffffu, t, 16);
-        if (r0 > 0) {
-          S[rowoff(r0 + i0) + r0 + c] -= (s0[0] + s0[1]) + (s0[2] + s0[3]);
-          S[rowoff(r0 + i0 + 4) + r0 + c] -= (s1[0] + s1[1]) + (s1[2] + s1[3]);
-          if (lane < 8) v[r0 + lane] -= t;
-        }
-        __syncwarp();
-        if (!diag_block(S, linv, J, lane) && lane == 0) s_bad = 1;
+      const float* li = linv + J * 64;
+      // forward substitution, bordered into the factorisation: y_J = L_JJ^-1 v_J, on the
+      // last warp when it has no panel rows (off the TRSM's critical path), else warp 0
+      const int yw = (r0 + 8 + (NW - 1) * 32 >= kp) ? NW - 1 : 0;
+      if (warp == yw) {
         float y = 0.f;
         if (lane < 8)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) y = fmaf(linv[J * 64 + lane * 8 + j], v[r0 + j], y);
+          for (int j = 0; j < 8; ++j) y = fmaf(li[lane * 8 + j], v[r0 + j], y);
         __syncwarp();
         if (lane < 8) v[r0 + lane] = y;
-      } else if (m > 0 && r0 > 0) {
-        const int nb = NT - 32;
-        for (int e = tid - 32; e < nsl * m; e += nb) {
-          const int row = e % m, sl = e / m;
-          const int k0 = sl * chunk, k1 = min(r0, k0 + chunk);
-          const float* ra = S + rowoff(r0 + 8 + row);
-          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int kk = k0; kk < k1; kk += 4) {
-            const float4 a4 = *reinterpret_cast<const float4*>(ra + kk);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const float4 l4 = *reinterpret_cast<const float4*>(S + rowoff(r0 + c) + kk);
-              acc[c] = fmaf(a4.x, l4.x, acc[c]);
-              acc[c] = fmaf(a4.y, l4.y, acc[c]);
-              acc[c] = fmaf(a4.z, l4.z, acc[c]);
-              acc[c] = fmaf(a4.w, l4.w, acc[c]);
-            }
-          }
-          float4* dst = reinterpret_cast<float4*>(red + 8 * e);
-          dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-          dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-        }
       }
-      __syncthreads();
-      if (s_bad || J + 1 == Q) break;
-      // phase B: thread t finishes row r0 + 8 + t (every launch has NT >= kp threads)
-      if (tid < m) {
-        const int a = r0 + 8 + tid;
-        float4* sa = reinterpret_cast<float4*>(S + rowoff(a) + r0);
-        const float4 u0 = sa[0], u1 = sa[1];
-        float sv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-        if (r0 > 0) {
-          for (int sl = 0; sl < nsl; ++sl) {
-            const float4* pr = reinterpret_cast<const float4*>(red + 8 * (sl * m + tid));
-            const float4 p0 = pr[0], p1 = pr[1];
-            sv[0] -= p0.x; sv[1] -= p0.y; sv[2] -= p0.z; sv[3] -= p0.w;
-            sv[4] -= p1.x; sv[5] -= p1.y; sv[6] -= p1.z; sv[7] -= p1.w;
-          }
-        }
-        // TRSM: x = s L_JJ^-T, a product with the stored inverse block
-        const float4* l4 = reinterpret_cast<const float4*>(linv + J * 64);
-        float x[8];
+      // TRSM: rows below the diagonal block, x = s L_JJ^-T. Thread t owns row r0 + 8 + t
+      // (every launch has NT >= kp threads) here and in (a), which reuses x.
+      const int ar = r0 + 8 + tid;
+      float x[8];
+      if (ar < kp) {
+        float4* ra = reinterpret_cast<float4*>(S + rowoff(ar) + r0);
+        const float4 s0 = ra[0], s1 = ra[1];
+        const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        const float4* l4 = reinterpret_cast<const float4*>(li);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const float4 q0 = l4[2 * c];
@@ -472,13 +452,71 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
             const float4 q1 = l4[2 * c + 1];
             lr[4] = q1.x; lr[5] = q1.y; lr[6] = q1.z; lr[7] = q1.w;
           }
-          float tt = 0.f;
+          float t = 0.f;
 #pragma unroll
-          for (int mm = 0; mm <= c; ++mm) tt = fmaf(sv[mm], lr[mm], tt);
-          x[c] = tt;
+          for (int m = 0; m <= c; ++m) t = fmaf(sv[m], lr[m], t);
+          x[c] = t;
         }
-        sa[0] = make_float4(x[0], x[1], x[2], x[3]);
-        sa[1] = make_float4(x[4], x[5], x[6], x[7]);
+        ra[0] = make_float4(x[0], x[1], x[2], x[3]);
+        ra[1] = make_float4(x[4], x[5], x[6], x[7]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) pan[c * kp + ar] = x[c];
+      }
+      __syncthreads();
+      if (J + 1 == Q) break;
+      // (a) the next column block, one row per thread; the row's right-hand side
+      // takes the panel's contribution, v_a -= L_aJ y_J
+      const int n0 = r0 + 8;
+      if (ar < kp) {
+        float4* ra = reinterpret_cast<float4*>(S + rowoff(ar) + n0);
+        const float4 u0 = ra[0], u1 = ra[1];
+        float acc[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        const float4 y0 = reinterpret_cast<const float4*>(v + r0)[0], y1 = reinterpret_cast<const float4*>(v + r0)[1];
+        const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+        float va = v[ar];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float la = x[c];
+          va = fmaf(-la, yv[c], va);
+          const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + n0);
+          const float4 b0 = pb[0], b1 = pb[1];
+          acc[0] = fmaf(-la, b0.x, acc[0]); acc[1] = fmaf(-la, b0.y, acc[1]);
+          acc[2] = fmaf(-la, b0.z, acc[2]); acc[3] = fmaf(-la, b0.w, acc[3]);
+          acc[4] = fmaf(-la, b1.x, acc[4]); acc[5] = fmaf(-la, b1.y, acc[5]);
+          acc[6] = fmaf(-la, b1.z, acc[6]); acc[7] = fmaf(-la, b1.w, acc[7]);
+        }
+        ra[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        ra[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        v[ar] = va;
+      }
+      // (a) writes column block J+1 and (b)'s tiles touch only blocks J+2.. (both read the
+      // panel), so no block barrier separates them: warp 0 updated the diagonal block's
+      // rows itself (threads 0-7) and factors it right away
+      __syncwarp();
+      // (b) warp 0: next diagonal block; warps 1..: trailing tiles (A, B), J+2 <= B <= A < Q
+      if (warp == 0) {
+        if (!diag_block(S, linv, J + 1, lane) && lane == 0) s_bad = 1;
+      } else {
+        // trailing blocks (A, B), J+2 <= B <= A < Q, as 8x4 or 4x4 register tiles: the
+        // size whose rounds over the NT - 32 threads cost the fewest instructions (8x8
+        // tiles fit the registers only with a partly rolled panel loop and ran slower)
+        const int m = Q - J - 2;
+        const int nb = NT - 32, t0 = tid - 32, base = 8 * (J + 2);
+        const int T84 = m * (m + 1), T44 = m * (2 * m + 1);
+        const int c84 = (T84 + nb - 1) / nb * 296, c44 = (T44 + nb - 1) / nb * 152;
+        if (c84 <= c44) {
+          for (int t = t0; t < T84; t += nb) {
+            int ai, bi;
+            tri_decode(t >> 1, ai, bi);
+            trail_tile<8, 4>(S, pan, kp, base + 8 * ai, base + 8 * bi + 4 * (t & 1));
+          }
+        } else {
+          for (int t = t0; t < T44; t += nb) {
+            int ai, bi;
+            tri_decode(t, ai, bi);
+            trail_tile<4, 4>(S, pan, kp, base + 4 * ai, base + 4 * bi);
+          }
+        }
       }
       __syncthreads();
     }
