@@ -16,7 +16,8 @@
 //   (b)      warp 0 factors the diagonal block J+1 in registers and stores its
 //            inverse, while the other warps update the rest of the trailing matrix
 //            in 8x4 or 4x4 register tiles (whichever balances best),
-//            S_AB -= L_AJ L_BJ^T.
+//            S_AB -= L_AJ L_BJ^T, two columns per packed FP32x2 FMA (each lane of the
+//            pair rounds like a scalar fmaf).
 // (a) and (b) touch disjoint blocks, so a panel costs two block barriers. The back
 // substitution and the refinement's triangular solves use every warp with the inverses
 // of 16-row diagonal blocks (one barrier per 16 rows); `ir_steps` steps of iterative refinement
@@ -111,46 +112,67 @@ __device__ __forceinline__ void tri_decode(int t, int& a, int& b) {
   b = t - ai * (ai + 1) / 2;
 }
 
+__device__ __forceinline__ uint64_t pk2(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // S[A.., B..] -= L[A.., J] L[B.., J]^T for one R x C tile (R, C in {4, 8}), with the
-// panel's 8 columns read from `pan` (column-major, leading dimension kp).
+// panel's 8 columns read from `pan` (column-major, leading dimension kp). Pairs of
+// columns are updated with packed FP32x2 FMAs.
 template <int R, int C>
 __device__ __forceinline__ void trail_tile(float* S, const float* pan, int kp, int A, int B) {
-  float acc[R][C];
+  uint64_t acc[R][C / 2];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const float4* sr = reinterpret_cast<const float4*>(S + rowoff(A + r) + B);
 #pragma unroll
     for (int h = 0; h < C / 4; ++h) {
       const float4 u = sr[h];
-      acc[r][4 * h] = u.x; acc[r][4 * h + 1] = u.y; acc[r][4 * h + 2] = u.z; acc[r][4 * h + 3] = u.w;
+      acc[r][2 * h] = pk2(u.x, u.y); acc[r][2 * h + 1] = pk2(u.z, u.w);
     }
   }
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    float la[R], lb[C];
+    float la[R];
+    uint64_t lb[C / 2];
     const float4* pa = reinterpret_cast<const float4*>(pan + c * kp + A);
     const float4* pb = reinterpret_cast<const float4*>(pan + c * kp + B);
 #pragma unroll
     for (int h = 0; h < R / 4; ++h) {
       const float4 u = pa[h];
-      la[4 * h] = u.x; la[4 * h + 1] = u.y; la[4 * h + 2] = u.z; la[4 * h + 3] = u.w;
+      la[4 * h] = -u.x; la[4 * h + 1] = -u.y; la[4 * h + 2] = -u.z; la[4 * h + 3] = -u.w;
     }
 #pragma unroll
     for (int h = 0; h < C / 4; ++h) {
       const float4 u = pb[h];
-      lb[4 * h] = u.x; lb[4 * h + 1] = u.y; lb[4 * h + 2] = u.z; lb[4 * h + 3] = u.w;
+      lb[2 * h] = pk2(u.x, u.y); lb[2 * h + 1] = pk2(u.z, u.w);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < R; ++r) {
+      const uint64_t l2 = pk2(la[r], la[r]);
 #pragma unroll
-      for (int q = 0; q < C; ++q) acc[r][q] = fmaf(-la[r], lb[q], acc[r][q]);
+      for (int q = 0; q < C / 2; ++q) acc[r][q] = fma2(l2, lb[q], acc[r][q]);
+    }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     float4* sr = reinterpret_cast<float4*>(S + rowoff(A + r) + B);
 #pragma unroll
-    for (int h = 0; h < C / 4; ++h)
-      sr[h] = make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
+    for (int h = 0; h < C / 4; ++h) {
+      float x0, x1, x2, x3;
+      upk2(acc[r][2 * h], x0, x1); upk2(acc[r][2 * h + 1], x2, x3);
+      sr[h] = make_float4(x0, x1, x2, x3);
+    }
   }
 }
 

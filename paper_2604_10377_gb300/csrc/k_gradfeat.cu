@@ -7,12 +7,15 @@
 //
 // with P = (Az)_re = A_re x - A_im y and Q = (Az)_im = A_re y + A_im x (variant A) or
 // A_re x + A_im y (variant B). One persistent CTA per SM walks 128-vertex tiles:
-//   all 8 warps   gather x and y of the tile's vertices (lanes over channels, float4
-//                 rows of X, the row's CSR entries broadcast by shuffles) into a K-major,
-//                 128-byte-swizzled FP32 tile in shared memory (K = the 2D channels x, y);
+//   all 16 warps  gather x and y of the tile's vertices (lanes over channels, float4
+//                 rows of X) into a K-major, 128-byte-swizzled FP32 tile in shared memory
+//                 (K = the 2D channels x, y); each warp pass keeps eight rows of X in
+//                 flight per lane and fetches the next pass's CSR offsets and first eight
+//                 entries while the current rows load;
 //   thread 0      streams the K-blocks of the W image (built once per call in the
-//                 workspace, rounded to TF32) through two shared-memory stages and issues
-//                 tcgen05.mma kind::tf32 (M = 128 vertices, N = 2D, K = 8) into TMEM;
+//                 workspace, rounded to TF32) through two shared-memory stages (the first
+//                 two issued before the gather) and issues tcgen05.mma kind::tf32
+//                 (M = 128 vertices, N = 2D, K = 8) into TMEM;
 //   warps 4-7     read P and Q from TMEM (one vertex per lane), x and y from the tile,
 //                 and store g in FP32 or BF16 rows of the output.
 // The x, y tile is the MMA operand and the epilogue's input, so a tile's gather starts
@@ -24,7 +27,7 @@
 namespace fmap {
 namespace {
 
-constexpr int kGfThreads = 256;
+constexpr int kGfThreads = 512;
 constexpr int kGfTileV = 128;
 constexpr int kGfMaxDim = 128;
 
@@ -135,73 +138,120 @@ __global__ void __launch_bounds__(kGfThreads, 1) gradfeat_kernel(GfParams P) {
   const uint32_t idesc = idesc_tf32(128, (uint32_t)n2);
 
   // gather mapping: `lpv` lanes per vertex (4 channels each), `vpw` vertices per warp pass
+  constexpr int kWarps = kGfThreads / 32;
   const int lpv = dim / 4, vpw = 32 / lpv;
   const int sub = lane / lpv, cl = lane % lpv;
   const bool lane_on = sub < vpw;
+  const int npass = (kGfTileV + kWarps * vpw - 1) / (kWarps * vpw);
   const int64_t ntiles = (P.n + kGfTileV - 1) / kGfTileV;
+  const uint8_t* wsrc = reinterpret_cast<const uint8_t*>(P.w_img);
+  auto load_stage = [&](int kb) {
+    const int s = kb & 1;
+    tc::mbar_arrive_expect_tx(&w_full[s], w_stage);
+    for (uint32_t off = 0; off < w_stage; off += 16384u)
+      tc::bulk_g2s(sW + (size_t)s * w_stage + off, wsrc + (size_t)kb * w_stage + off,
+                   (w_stage - off) < 16384u ? (w_stage - off) : 16384u, &w_full[s]);
+  };
+  // CSR offsets of the vertex of pass `ps` (length 0 outside the tile or the operator)
+  auto meta = [&](int64_t v0, int ps, int64_t& e0, int& len) {
+    const int r = (ps * kWarps + warp) * vpw + sub;
+    const int64_t v = v0 + r;
+    e0 = 0;
+    len = 0;
+    if (lane_on && r < kGfTileV && v < P.n) {
+      const int64_t a = __ldg(P.row_ptr + v), b = __ldg(P.row_ptr + v + 1);
+      if (a < 0 || b < a || b > P.nnz) {
+        *bad_index = 1;
+      } else {
+        e0 = a;
+        len = (b - a) < (int64_t)(1 << 30) ? (int)(b - a) : (1 << 30);
+      }
+    }
+  };
+  // entries q .. q+7 of a row (column -1: none); a column outside X is reported and skipped
+  auto entries = [&](int64_t e0, int len, int q, int32_t (&c)[8], float2 (&g)[8]) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      c[u] = -1;
+      g[u] = make_float2(0.f, 0.f);
+      if (q + u < len) {
+        const int32_t cc = __ldg(P.col_idx + e0 + q + u);
+        if (cc >= 0 && cc < P.n_in) {
+          c[u] = cc;
+          g[u] = __ldg(P.vals + e0 + q + u);
+        } else {
+          *bad_index = 1;
+        }
+      }
+    }
+  };
+  auto accumulate = [&](const int32_t (&c)[8], const float2 (&g)[8], float4& ax, float4& ay) {
+    float4 xr[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      xr[u] = c[u] >= 0 ? __ldg(reinterpret_cast<const float4*>(P.x_in + (int64_t)c[u] * P.ld_in) + cl)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ax.x = fmaf(g[u].x, xr[u].x, ax.x); ax.y = fmaf(g[u].x, xr[u].y, ax.y);
+      ax.z = fmaf(g[u].x, xr[u].z, ax.z); ax.w = fmaf(g[u].x, xr[u].w, ax.w);
+      ay.x = fmaf(g[u].y, xr[u].x, ay.x); ay.y = fmaf(g[u].y, xr[u].y, ay.y);
+      ay.z = fmaf(g[u].y, xr[u].z, ay.z); ay.w = fmaf(g[u].y, xr[u].w, ay.w);
+    }
+  };
   uint32_t wphase[2] = {0, 0}, ephase[2] = {0, 0}, aphase = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t v0 = tile * kGfTileV;
+    // the first two K-blocks of W stream in while the tile gathers (the previous tile's
+    // MMAs have completed: their stages were drained)
+    if (tid == 0) {
+      load_stage(0);
+      if (nkb > 1) load_stage(1);
+    }
     // ---------------------------------------------------------------- gather x, y
-    for (int r0 = warp * vpw; r0 < kGfTileV; r0 += 8 * vpw) {
-      const int r = r0 + sub;
-      const int64_t v = v0 + r;
+    int64_t e0;
+    int len;
+    meta(v0, 0, e0, len);
+    int32_t c_cur[8];
+    float2 g_cur[8];
+    entries(e0, len, 0, c_cur, g_cur);
+    for (int ps = 0; ps < npass; ++ps) {
+      const int r = (ps * kWarps + warp) * vpw + sub;
+      int64_t e0n = 0;
+      int lenn = 0;
+      if (ps + 1 < npass) meta(v0, ps + 1, e0n, lenn);
       float4 ax = make_float4(0.f, 0.f, 0.f, 0.f), ay = ax;
-      int64_t e0 = 0, e1 = 0;
-      if (lane_on && v < P.n) {
-        e0 = __ldg(P.row_ptr + v);
-        e1 = __ldg(P.row_ptr + v + 1);
-        if (e0 < 0 || e1 < e0 || e1 > P.nnz) { *bad_index = 1; e1 = e0 = 0; }
-      }
-      // every lane walks the longest row of its warp pass; entries past a row are skipped
-      int64_t len = e1 - e0, mx = len;
+      int mx = len;
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      for (int64_t q = 0; q < mx; q += 4) {
-        float4 xr[4];
-        float2 gv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          xr[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          gv[u] = make_float2(0.f, 0.f);
-          if (q + u < len) {
-            const int64_t e = e0 + q + u;
-            const int32_t c = __ldg(P.col_idx + e);
-            if (c >= 0 && c < P.n_in) {
-              gv[u] = __ldg(P.vals + e);
-              xr[u] = __ldg(reinterpret_cast<const float4*>(P.x_in + (int64_t)c * P.ld_in) + cl);
-            } else {
-              *bad_index = 1;
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          ax.x = fmaf(gv[u].x, xr[u].x, ax.x); ax.y = fmaf(gv[u].x, xr[u].y, ax.y);
-          ax.z = fmaf(gv[u].x, xr[u].z, ax.z); ax.w = fmaf(gv[u].x, xr[u].w, ax.w);
-          ay.x = fmaf(gv[u].y, xr[u].x, ay.x); ay.y = fmaf(gv[u].y, xr[u].y, ay.y);
-          ay.z = fmaf(gv[u].y, xr[u].z, ay.z); ay.w = fmaf(gv[u].y, xr[u].w, ay.w);
-        }
+      // rows longer than eight entries: the rest first, one chunk of eight at a time
+      for (int q = 8; q < mx; q += 8) {
+        int32_t c_more[8];
+        float2 g_more[8];
+        entries(e0, len, q, c_more, g_more);
+        accumulate(c_more, g_more, ax, ay);
       }
-      if (lane_on) {
+      // the next pass's first entries load while this pass's first eight rows of X do
+      int32_t c_nxt[8];
+      float2 g_nxt[8];
+      entries(e0n, lenn, 0, c_nxt, g_nxt);
+      accumulate(c_cur, g_cur, ax, ay);
+      if (lane_on && r < kGfTileV) {
         *reinterpret_cast<float4*>(sA + sw_off(r, 4 * cl, kGfTileV)) = ax;
         *reinterpret_cast<float4*>(sA + sw_off(r, dim + 4 * cl, kGfTileV)) = ay;
+      }
+      e0 = e0n;
+      len = lenn;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c_cur[u] = c_nxt[u];
+        g_cur[u] = g_nxt[u];
       }
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
     // ---------------------------------------------------------------- MMAs
     if (tid == 0) {
-      const uint8_t* wsrc = reinterpret_cast<const uint8_t*>(P.w_img);
-      auto load_stage = [&](int kb) {
-        const int s = kb & 1;
-        tc::mbar_arrive_expect_tx(&w_full[s], w_stage);
-        for (uint32_t off = 0; off < w_stage; off += 16384u)
-          tc::bulk_g2s(sW + (size_t)s * w_stage + off, wsrc + (size_t)kb * w_stage + off,
-                       (w_stage - off) < 16384u ? (w_stage - off) : 16384u, &w_full[s]);
-      };
       bool ok = true;
-      load_stage(0);
-      if (nkb > 1) load_stage(1);
       const uint32_t a_base = tc::smem_u32(sA);
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb & 1;
@@ -234,7 +284,7 @@ __global__ void __launch_bounds__(kGfThreads, 1) gradfeat_kernel(GfParams P) {
       }
     }
     // ---------------------------------------------------------------- epilogue
-    if (warp >= 4) {
+    if (warp >= 4 && warp < 8) {
       const int quarter = warp & 3;
       const int r = quarter * 32 + lane;
       const int64_t v = v0 + r;
