@@ -992,6 +992,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of one CUDA graph per step")
     ap.add_argument("--k-sweep", action="store_true", help="spectral-resolution sweep (Fig. 1) instead of the step")
     ap.add_argument("--overlap", action="store_true", help="overlap-prediction metrics instead of the step")
+    ap.add_argument("--gradfeat", action="store_true",
+                    help="spatial gradient features (DiffusionNet variants A and B) instead of the step")
     ap.add_argument("--copy-streams", type=int, default=4, help="side streams of the end-to-end host-to-device copies")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's built-in tiling choices")
     ap.add_argument("--no-peaks", action="store_true", help="derive the FP32 peak instead of measuring it")
@@ -1003,6 +1005,13 @@ def main():
         args.warmup = 3
     if args.overlap:
         run_overlap(args)
+        return
+    if args.gradfeat:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        measured = None if args.no_peaks else measure_peaks(dev)
+        print(json.dumps(bench_gradient_features(args, dev, load_peaks(), measured, None)), flush=True)
         return
     if args.k_sweep:
         run_ksweep(args)
