@@ -406,13 +406,16 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
       tc::bulk_g2s(S, fac, (uint32_t)fsz * 4u, &s_bar);
       if (use_gs) tc::bulk_g2s(Gs, G, gs_bytes, &s_bar);
     }
-    if (!tc::mbar_wait(&s_bar, 0, &s_abort)) {
+    tc::mbar_wait(&s_bar, 0, &s_abort);
+    __syncthreads();
+    if (s_abort) {
+      // a copy that never completed: report, give it a bounded time to land, leave (every
+      // thread of the block takes this branch together)
       if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
       const uint64_t t0 = tc::globaltimer();
       while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}
       return;
     }
-    __syncthreads();
   } else {
     // S = G + lambda diag(D_i). The Gram kernel left rows 0 .. k-1 of G in this packed
     // layout (each row up to the end of its diagonal block; the entries above the
@@ -430,14 +433,14 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
       float* row = S + rowoff(a);
       for (int c = 0; c < (a & ~7) + 8; ++c) row[c] = (c == a) ? 1.f : 0.f;
     }
-    if (!tc::mbar_wait(&s_bar, 0, &s_abort)) {
-      // a copy that never completed: report, give it a bounded time to land, leave
+    tc::mbar_wait(&s_bar, 0, &s_abort);
+    __syncthreads();   // every thread's copies are visible
+    if (s_abort) {
       if (tid == 0) set_status(status, p, FMAP_ERR_TIMEOUT);
       const uint64_t t0 = tc::globaltimer();
       while (!tc::mbar_try_wait(&s_bar, 0) && tc::globaltimer() - t0 < tc::kWaitTimeoutNs) {}
       return;
     }
-    __syncthreads();   // every thread's copies are visible
     for (int a = tid; a < k; a += NT) S[rowoff(a) + a] += dg[a];
     for (int a = tid; a < kp; a += NT) v[a] = rh[a];   // right-hand side, reduced during the factorisation
     __syncthreads();

@@ -31,26 +31,6 @@ constexpr int kGfThreads = 512;
 constexpr int kGfTileV = 128;
 constexpr int kGfMaxDim = 128;
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 // Byte offset of (row r, K index kk) in a K-major tile of 128-byte rows with the 128-byte
 // swizzle: K-block kk / 32 of `rows` rows, 16-byte chunk (kk % 32) / 4 of row r stored at
 // chunk ((kk % 32) / 4) ^ (r % 8).
@@ -81,7 +61,7 @@ __global__ void gradfeat_w_image_kernel(const float* a_re, const float* a_im, in
       w = kx ? aim : are;                                   // Q_i = A_re y + A_im x
     else
       w = kx ? are : aim;                                   // Q_i = A_re x + A_im y
-    img[(int64_t)(kb * n2 + n) * 32 + (((kk >> 2) ^ (n & 7)) << 2) + (kk & 3)] = tf32_rna(w);
+    img[(int64_t)(kb * n2 + n) * 32 + (((kk >> 2) ^ (n & 7)) << 2) + (kk & 3)] = tc::tf32_rna(w);
   }
 }
 
@@ -135,7 +115,7 @@ __global__ void __launch_bounds__(kGfThreads, 1) gradfeat_kernel(GfParams P) {
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const uint32_t idesc = idesc_tf32(128, (uint32_t)n2);
+  const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)n2);
 
   // gather mapping: `lpv` lanes per vertex (4 channels each), `vpw` vertices per warp pass
   constexpr int kWarps = kGfThreads / 32;
@@ -264,7 +244,7 @@ __global__ void __launch_bounds__(kGfThreads, 1) gradfeat_kernel(GfParams P) {
           const uint64_t ad = tc::smem_desc(a_base + (uint32_t)kb * (kGfTileV * 128u) + ks * 32, 16, 1024,
                                             tc::kLayoutSW128);
           const uint64_t bd = tc::smem_desc(b_base + ks * 32, 16, 1024, tc::kLayoutSW128);
-          mma_tf32(tmem_base, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
+          tc::mma_tf32(tmem_base, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
         }
         tc::mma_commit(&w_empty[s]);
         if (kb + 2 < nkb) {

@@ -80,20 +80,6 @@ __global__ void fma64_loop_kernel(int64_t iters, double mul, double add, float* 
   if (s == 12345.678) sink[blockIdx.x] = (float)s;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
-}
-
 // bf16 = 0: kind::tf32 (K = 8 per MMA); 1: kind::f16 with BF16 operands (K = 16).
 __global__ void __launch_bounds__(kMmaThreads, 1) mma_loop_kernel(int64_t iters, int bf16, int* err) {
   extern __shared__ uint8_t smem_raw[];
@@ -122,7 +108,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) mma_loop_kernel(int64_t iters,
   const uint32_t d = *tmem_slot;
   if (threadIdx.x == 0) {
     const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-    const uint32_t idesc = bf16 ? tc::idesc_bf16_f32(128, kMmaN, 0, 0) : idesc_tf32(128, kMmaN);
+    const uint32_t idesc = bf16 ? tc::idesc_bf16_f32(128, kMmaN, 0, 0) : tc::idesc_tf32(128, kMmaN);
     for (int64_t i = 0; i < iters; ++i) {
       const uint32_t ks = (uint32_t)(i & 3) * 32u;   // four K-steps of 32 bytes per 128-byte row
       const uint64_t ad = tc::smem_desc(a0 + ks, 16, 1024, tc::kLayoutSW128);
@@ -130,7 +116,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) mma_loop_kernel(int64_t iters,
       if (bf16)
         tc::mma_bf16(d, ad, bd, idesc, i != 0 ? 1u : 0u);
       else
-        mma_tf32(d, ad, bd, idesc, i != 0 ? 1u : 0u);
+        tc::mma_tf32(d, ad, bd, idesc, i != 0 ? 1u : 0u);
     }
     tc::mma_commit(done);
     if (!tc::mbar_wait(done, 0, &s_abort)) atomicExch(err, (int)FMAP_ERR_TIMEOUT);

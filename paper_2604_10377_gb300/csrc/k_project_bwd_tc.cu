@@ -31,21 +31,6 @@ constexpr uint32_t kAStageBytes = kTileV * 128;   // 128 rows x 32 fp32
 constexpr uint32_t kOutChunkBytes = 32 * 32;      // 32 rows x 16 BF16: one TMA store box
 constexpr uint32_t kOutWarpBytes = 4 * kOutChunkBytes;   // <= 4 chunks of 16 features per warp and tile
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// kind::tf32, FP32 accumulation, both operands K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
-}
-
 __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -147,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
         if (!tc::mbar_wait(b_full, bphase, abort_flag)) break;
         bphase ^= 1;
         tc::tc_fence_after();
-        const uint32_t idesc = idesc_tf32(128, (uint32_t)(item.nf > 0 ? item.nf : 16));
+        const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)(item.nf > 0 ? item.nf : 16));
         const uint32_t b_base = tc::smem_u32(sB);
         const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
         for (int t = 0; t < ntiles && ok; ++t) {
@@ -164,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc_kernel(TcBwdParams
                 const uint64_t ad = tc::smem_desc(a_base + ks * 32, 16, 1024, tc::kLayoutSW128);
                 const uint64_t bd = tc::smem_desc(b_base + (uint32_t)(kb * item.nf * 128) + ks * 32, 16, 1024,
                                                   tc::kLayoutSW128);
-                mma_tf32(d, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
+                tc::mma_tf32(d, ad, bd, idesc, (kb | ks) != 0 ? 1u : 0u);
               }
             }
             tc::mma_commit(&a_empty[stage]);

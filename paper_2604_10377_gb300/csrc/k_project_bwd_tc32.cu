@@ -33,26 +33,6 @@ constexpr uint32_t kAStageBytes = kTileV * 128;      // 128 rows x 32 FP32
 constexpr uint32_t kOutChunkBytes = 32 * 16 * 4;     // 32 rows x 16 FP32: one TMA store box
 constexpr uint32_t kOutWarpBytes = 2 * kOutChunkBytes;   // <= 32 features per warp and tile
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 // x minus the TF32 value the tensor core reads for it (the low 13 bits dropped): exact.
 __device__ __forceinline__ float tf32_trunc_rest(float x) {
   return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
@@ -153,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc32_kernel(TcBwdPara
         if (!tc::mbar_wait(b_full, bphase, abort_flag)) break;
         bphase ^= 1;
         tc::tc_fence_after();
-        const uint32_t idesc = idesc_tf32(128, (uint32_t)item.nf);
+        const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)item.nf);
         const uint32_t bh_base = tc::smem_u32(sB);
         const uint32_t bl_base = bh_base + P.b_bytes_max;
         const int ntiles = (int)((item.v1 - item.v0 + kTileV - 1) / kTileV);
@@ -172,9 +152,9 @@ __global__ void __launch_bounds__(kThreads, 1) project_bwd_tc32_kernel(TcBwdPara
               const uint32_t boff = (uint32_t)(kb * item.nf * 128) + ks * 32;
               const uint64_t bh = tc::smem_desc(bh_base + boff, 16, 1024, tc::kLayoutSW128);
               const uint64_t bl = tc::smem_desc(bl_base + boff, 16, 1024, tc::kLayoutSW128);
-              mma_tf32(d, at, bh, idesc, (kb | ks) != 0 ? 1u : 0u);
-              mma_tf32(d, at, bl, idesc, 1u);
-              mma_tf32(d, ar, bh, idesc, 1u);
+              tc::mma_tf32(d, at, bh, idesc, (kb | ks) != 0 ? 1u : 0u);
+              tc::mma_tf32(d, at, bl, idesc, 1u);
+              tc::mma_tf32(d, ar, bh, idesc, 1u);
             }
             tc::mma_commit(&a_empty[stage]);
             if (++stage == (uint32_t)S) { stage = 0; phase ^= 1; }
@@ -282,7 +262,7 @@ __global__ void build_dat_image32_kernel(const ShapeDev* shapes, const TcBwdGrou
     const float val = (n < s.k && fg < s.d) ? d_a[s.a_off + (int64_t)n * s.d + fg] : 0.f;
     const int chunk = nl >> 2;
     const int64_t at = (int64_t)kb * g.nf * 32 + f * 32 + ((chunk ^ (f & 7)) << 2) + (nl & 3);
-    const float h = tf32_rna(val);
+    const float h = tc::tf32_rna(val);
     img[at] = h;
     img[at + total] = val - h;
   }

@@ -34,10 +34,6 @@ constexpr int kStageV = 64;            // vertices per pipeline stage (= one 128
 constexpr uint32_t kBoxBytes = 64 * 64 * 2;   // one TMA box: 64 vertices x 64 features bf16
 constexpr uint32_t kPhiBoxBytes = 64 * 128;    // one TMA box: 64 vertices x 32 basis functions fp32
 
-__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
   return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
@@ -191,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P)
             }
           }
         }
-        named_barrier_sync(1, 32 * kConvWarps);
+        tc::named_barrier_sync(1, 32 * kConvWarps);
         // write phase: P hi at [0, npad*128), lo at [npad*128, 2*npad*128), K-major, 128-byte swizzle
         uint8_t* th = tile;
         uint8_t* tl = tile + (size_t)item.npad * 128;

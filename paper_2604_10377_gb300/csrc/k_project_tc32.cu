@@ -35,32 +35,6 @@ constexpr int kStageV = 32;                  // vertices per pipeline stage (one
 constexpr uint32_t kBoxBytes = 32 * 128;     // one TMA box: 32 vertices x 32 FP32 (features or basis)
 constexpr uint32_t kGroupBytes = 4 * kBoxBytes;   // 128 features of one stage
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// kind::tf32, FP32 accumulation, both operands K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t m, uint32_t n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
-}
-
-__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// x rounded to TF32 (nearest, ties away), as an FP32 value with the low 13 bits clear.
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 constexpr int kMaxFg = 2;   // feature groups of 128 per CTA (the planner caps FP32 units at 2)
 
 __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams P) {
@@ -151,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
         const TcItem item = P.items[it];
         if (!tc::mbar_wait(&acc_empty[buf], acc_phase[buf] ^ 1, abort_flag)) break;
         tc::tc_fence_after();
-        const uint32_t idesc = idesc_tf32(128, (uint32_t)item.npad);
+        const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)item.npad);
         const int nst = (int)((item.v1 - item.v0 + kStageV - 1) / kStageV);
         const int kb = (item.npad + 31) / 32;
         bool ok = true;
@@ -171,9 +145,9 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
               const uint64_t af = tc::smem_desc(f_base + m * kGroupBytes + kk * 32, 16, 1024, tc::kLayoutSW128);
               const uint64_t al = tc::smem_desc(fl_base + m * kGroupBytes + kk * 32, 16, 1024, tc::kLayoutSW128);
               const uint32_t d = tmem_base + (uint32_t)buf * half_cols + (uint32_t)(m * item.npad);
-              mma_tf32(d, af, bh, idesc, (st | kk) != 0 ? 1u : 0u);
-              mma_tf32(d, af, bl, idesc, 1u);
-              mma_tf32(d, al, bh, idesc, 1u);
+              tc::mma_tf32(d, af, bh, idesc, (st | kk) != 0 ? 1u : 0u);
+              tc::mma_tf32(d, af, bl, idesc, 1u);
+              tc::mma_tf32(d, al, bh, idesc, 1u);
             }
           }
           tc::mma_commit(&empty[stage]);
@@ -227,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
             }
           }
         }
-        named_barrier_sync(1, 32 * kConvWarps);
+        tc::named_barrier_sync(1, 32 * kConvWarps);
 #pragma unroll
         for (int r = 0; r < kMaxFg * 4; ++r) {
           const int q = ct + 32 * kConvWarps * r;
@@ -236,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
             float h[4], l[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              h[j] = tf32_rna(fx[r][j]);
+              h[j] = tc::tf32_rna(fx[r][j]);
               l[j] = fx[r][j] - h[j];
             }
             const uint32_t off = (uint32_t)f * 128u + ((uint32_t)(c ^ (f & 7)) << 4);
@@ -257,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) project_tc32_kernel(TcProjParams 
             const float ph = *reinterpret_cast<const float*>(phi + b * kBoxBytes + v * 128 +
                                                              ((((nn >> 2) ^ (v & 7)) << 4) | ((nn & 3) << 2)));
             const float p = (vbase + v < item.v1) ? ph * mst[v] : 0.f;
-            hv[j] = tf32_rna(p);
+            hv[j] = tc::tf32_rna(p);
             lv[j] = p - hv[j];
           }
           const uint32_t off = (uint32_t)n * 128u + ((uint32_t)(c ^ (n & 7)) << 4);

@@ -152,6 +152,21 @@ def test_refinement_with_fp32_gram_from_global(ks, hi_min, ir):
     _check_forward(wl, ir_steps=ir, hi_gram_min_k=hi_min)
 
 
+@pytest.mark.parametrize("feat_dtype,hi_min", [("fp32", 1000), ("fp32", 150), ("bf16", 200)])
+def test_row_solve_sizes_129_to_200(feat_dtype, hi_min):
+    """Row systems of the 256-thread launches (128 < k <= 200) at sizes where the trailing
+    update's tile counts change shape (k = 129: one padded row past a block; 144, 152, 184,
+    200), with the FP32 and the double-float Gram, forward against the oracle at the
+    mode's tolerance (d = 448, well-conditioned systems)."""
+    rng = np.random.default_rng(23)
+    shapes, pairs = [], []
+    for i, k in enumerate((129, 144, 152, 184, 200)):
+        shapes += [_shape(rng, 2600 + 9 * i, k, 448, feat_dtype), _shape(rng, 2400 + 7 * i, k, 448, feat_dtype)]
+        pairs.append(synth.Pair(x=2 * i, y=2 * i + 1, lam=1e-3))
+    wl = synth.Workload("tc_trailing", shapes, pairs, feat_dtype)
+    _check_forward(wl, hi_gram_min_k=hi_min)
+
+
 def test_bitwise_reproducible():
     wl = synth.make_small(7, 3, (3000, 20000), [30, 64, 100], 64)
     from paper_2604_10377_gb300 import api
