@@ -83,6 +83,11 @@ typedef struct fmap_options {
                                    item, multiple of 128 in 1024..65536 (default 8192) */
     int32_t solve_threads_k64;  /* row-solve block for k <= 64: 64 or 128 threads (default 64) */
     int32_t solve_threads_k128; /* row-solve block for 64 < k <= 128: 128 or 256 (default 128) */
+    /* Persistent CTAs of the tensor-core projections, 1..152 (0 = one per SM, 152). A batch
+     * whose projection runs beside another batch's row solves (two streams) can keep it on
+     * part of the SMs, so that the solves' blocks hold the rest. */
+    int32_t proj_ctas;          /* forward projection */
+    int32_t bwd_ctas;           /* backward projection, even (two CTAs share each vertex tile) */
 } fmap_options;
 
 typedef struct fmap_shape_desc {
@@ -199,6 +204,22 @@ FMAP_API int32_t fmap_solve(fmap_batch* batch, const float* a, float* c_out, voi
 FMAP_API int32_t fmap_solve_backward(fmap_batch* batch, const float* d_c, const float* a, const float* c,
                             const void* saved, float* d_a, float* d_mask, float* d_lambda,
                             int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* The two halves of fmap_solve_backward, for callers that put them on different streams
+ * (the adjoint solves are bound by the SMs' arithmetic latency, the backward projection by
+ * HBM, so one batch's projection can run beside another batch's adjoint):
+ *   fmap_adjoint           everything up to dL/dA (same arguments; d_a is required), and
+ *                          dL/dD, dL/dlambda; no dL/dF
+ *   fmap_project_backward  dL/dF_s = diag(M_s) Phi_s dL/dA_s for every shape with a dfeat
+ *                          buffer (the chain rule of Eq. 1), from d_a as fmap_adjoint wrote it
+ * Both use the batch workspace (>= sizes.ws_bwd_bytes): calls on one batch must be ordered
+ * (fmap_project_backward after the fmap_adjoint whose d_a it reads). Together they do
+ * exactly what fmap_solve_backward does, in the same arithmetic. */
+FMAP_API int32_t fmap_adjoint(fmap_batch* batch, const float* d_c, const float* a, const float* c,
+                              const void* saved, float* d_a, float* d_mask, float* d_lambda,
+                              int32_t* status, void* ws, size_t ws_bytes, void* stream);
+FMAP_API int32_t fmap_project_backward(fmap_batch* batch, const float* d_a, void* ws, size_t ws_bytes,
+                                       void* stream);
 
 /* The training loss of the differentiable workloads, per pair:
  *   L_p = ||C C^T - I||_F^2 + ||C - C_gt||_F^2,  dL/dC = 4 (C C^T - I) C + 2 (C - C_gt).

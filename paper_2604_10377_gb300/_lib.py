@@ -29,10 +29,11 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("ir_steps", c_int32), ("hi_gram_min_k", c_int32),
                 ("store_factors_max_k", c_int32), ("adjoint_ir_steps", c_int32),
                 ("proj_max_stages", c_int32), ("proj_seg_max_v", c_int32), ("bwd_group_features", c_int32),
-                ("bwd_chunk_v", c_int32), ("solve_threads_k64", c_int32), ("solve_threads_k128", c_int32)]
+                ("bwd_chunk_v", c_int32), ("solve_threads_k64", c_int32), ("solve_threads_k128", c_int32),
+                ("proj_ctas", c_int32), ("bwd_ctas", c_int32)]
 
 
-TUNING_FIELDS = ("proj_max_stages", "proj_seg_max_v", "bwd_group_features", "bwd_chunk_v",
+TUNING_FIELDS = ("proj_max_stages", "proj_seg_max_v", "bwd_group_features", "bwd_chunk_v", "proj_ctas", "bwd_ctas",
                  "solve_threads_k64", "solve_threads_k128")
 
 
@@ -81,6 +82,9 @@ _PROTOS = {
     "fmap_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_solve_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "fmap_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "fmap_project_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_loss_orth": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_batch_set_timing": (c_int32, [c_void_p, c_int32]),
     "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),

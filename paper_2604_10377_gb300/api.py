@@ -307,6 +307,25 @@ class FmapBatch:
                                              self.ws.numel(), _stream(self.device)), "fmap_solve_backward")
         return d_a
 
+    def adjoint(self, d_c: torch.Tensor, a: Optional[torch.Tensor] = None, c: Optional[torch.Tensor] = None,
+                use_saved: bool = True, d_a: Optional[torch.Tensor] = None, d_mask: Optional[torch.Tensor] = None,
+                d_lambda: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The first half of solve_backward: dL/dA (and dL/dD, dL/dlambda), no dL/dF."""
+        a = self.A if a is None else a
+        c = self.C if c is None else c
+        d_a = self.dA if d_a is None else d_a
+        saved = self.saved if use_saved else None
+        check(_lib.lib().fmap_adjoint(self._batch, _ptr(d_c), _ptr(a), _ptr(c), _ptr(saved), _ptr(d_a),
+                                      _ptr(d_mask), _ptr(d_lambda), _ptr(self.status), _ptr(self.ws),
+                                      self.ws.numel(), _stream(self.device)), "fmap_adjoint")
+        return d_a
+
+    def project_backward(self, d_a: Optional[torch.Tensor] = None):
+        """The second half of solve_backward: dL/dF of every shape from dL/dA."""
+        d_a = self.dA if d_a is None else d_a
+        check(_lib.lib().fmap_project_backward(self._batch, _ptr(d_a), _ptr(self.ws), self.ws.numel(),
+                                               _stream(self.device)), "fmap_project_backward")
+
     def loss_orth(self, c: torch.Tensor, c_gt: torch.Tensor, loss: Optional[torch.Tensor] = None,
                   d_c: Optional[torch.Tensor] = None):
         if loss is None:

@@ -64,7 +64,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // One launch of the forward projection: the segments of one spectral-size class.
 struct TcLaunch {
-  int32_t cta_off;     // offset of its kTcCtas + 1 CTA boundaries in tc_cta_first
+  int32_t cta_off;     // offset of its proj_ctas + 1 CTA boundaries in tc_cta_first
   int32_t stages;
   uint32_t f_stage, p_stage, tmem_cols;
   int32_t smem;
@@ -86,14 +86,16 @@ struct Plan {
   bool tc_bwd = false;    // backward projection on the tensor cores (BF16 features: CTA pairs)
   bool tc_bwd32 = false;  // backward projection on the tensor cores (FP32 features: three TF32 passes)
   std::vector<TcItem> tc_items;
-  std::vector<int32_t> tc_cta_first;   // kTcCtas + 1 entries per launch
+  int proj_ctas = kTcCtas;             // persistent CTAs of the forward projection
+  int bwd_ctas = kTcCtas;              // and of the backward projection
+  std::vector<int32_t> tc_cta_first;   // proj_ctas + 1 entries per launch
   std::vector<TcLaunch> tc_launches;
   std::vector<TcRedGroup> tc_groups;
   int64_t tc_max_group_elems = 0;
   int tc_smem = 0;                     // the largest dynamic shared memory of the launches
   // tensor-core backward projection
   std::vector<TcBwdItem> bw_items;
-  std::vector<int32_t> bw_cta_first;   // kTcCtas + 1 segment boundaries
+  std::vector<int32_t> bw_cta_first;   // bwd_ctas + 1 (FP32) or bwd_ctas / 2 + 1 (BF16) boundaries
   std::vector<TcBwdGroup> bw_groups;
   int bw_max_img = 0, bw_stages = 0, bw_smem = 0;
   uint32_t bw_b_bytes = 0;
@@ -115,6 +117,8 @@ int32_t validate_options(const fmap_options& o) {
   if (o.solve_threads_k64 != 0 && o.solve_threads_k64 != 64 && o.solve_threads_k64 != 128) return FMAP_ERR_INVALID_ARG;
   if (o.solve_threads_k128 != 0 && o.solve_threads_k128 != 128 && o.solve_threads_k128 != 256)
     return FMAP_ERR_INVALID_ARG;
+  if (o.proj_ctas < 0 || o.proj_ctas > kTcCtas) return FMAP_ERR_INVALID_ARG;
+  if (o.bwd_ctas < 0 || o.bwd_ctas > kTcCtas || (o.bwd_ctas & 1)) return FMAP_ERR_INVALID_ARG;
   return FMAP_OK;
 }
 
@@ -125,6 +129,8 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   if (n_shapes < 0 || n_pairs < 0 || n_shapes > 65535 || n_pairs > 65535) return FMAP_ERR_INVALID_ARG;
   if ((n_shapes > 0 && !shapes) || (n_pairs > 0 && !pairs)) return FMAP_ERR_INVALID_ARG;
   P.opt = opt;
+  P.proj_ctas = opt.proj_ctas ? opt.proj_ctas : kTcCtas;
+  P.bwd_ctas = opt.bwd_ctas ? opt.bwd_ctas : kTcCtas;
   const size_t fsz = opt.precision == FMAP_PREC_BF16 ? 2 : 4;
 
   P.shapes.resize(n_shapes);
@@ -183,7 +189,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
   {
     // (shape, feature group) units, grouped by spectral-size class (k padded to 32, 64,
     // 128, 256); every class is one launch with its own pipeline depth, and within a
-    // class a stream-K split of the vertex ranges into kTcCtas ranges of equal cost
+    // class a stream-K split of the vertex ranges into proj_ctas ranges of equal cost
     // (64-vertex granularity)
     // A spectral size above the widest basis range of one unit (256, the MMA's largest
     // N, for BF16 features; 128 for FP32 features, whose stages are larger) is split
@@ -247,10 +253,11 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       }
       TcLaunch L{};
       L.cta_off = (int32_t)P.tc_cta_first.size();
-      P.tc_cta_first.resize(P.tc_cta_first.size() + kTcCtas + 1, 0);
+      const int nctas = P.proj_ctas;
+      P.tc_cta_first.resize(P.tc_cta_first.size() + nctas + 1, 0);
       int32_t* first = P.tc_cta_first.data() + L.cta_off;
       first[0] = (int32_t)P.tc_items.size();
-      const double per_cta = total / kTcCtas;
+      const double per_cta = total / nctas;
       int cta = 0;
       double budget = per_cta;
       for (const Unit& u : units) {
@@ -263,7 +270,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         while (v < sd.n) {
           int64_t take = (int64_t)std::ceil(std::max(budget, 0.0) / u.cpv);
           take = std::max<int64_t>(stage_v, (take + stage_v - 1) / stage_v * stage_v);
-          if (cta == kTcCtas - 1) take = sd.n - v;
+          if (cta == nctas - 1) take = sd.n - v;
           // a segment accumulates in TMEM; bounding its length bounds the accumulated
           // rounding of the tensor-core FP32 sums (partials are added in IEEE FP32)
           take = std::min<int64_t>(std::min<int64_t>(take, seg_max), sd.n - v);
@@ -276,7 +283,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
           P.tc_items.push_back(it);
           v += take;
           budget -= u.cpv * (double)take;
-          if (budget <= 1e-9 * per_cta && cta < kTcCtas - 1) {
+          if (budget <= 1e-9 * per_cta && cta < nctas - 1) {
             ++cta;
             first[cta] = (int32_t)P.tc_items.size();
             budget += per_cta;
@@ -286,7 +293,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         P.tc_groups.push_back(rg);
         P.tc_max_group_elems = std::max<int64_t>(P.tc_max_group_elems, (int64_t)u.nk * rg.dspan);
       }
-      for (int c = cta + 1; c <= kTcCtas; ++c) first[c] = (int32_t)P.tc_items.size();
+      for (int c = cta + 1; c <= nctas; ++c) first[c] = (int32_t)P.tc_items.size();
       L.f_stage = std::max<uint32_t>(fmax, 16384u);
       L.p_stage = (std::max<uint32_t>(pmax, 8192u) + 1023u) / 1024u * 1024u;
       uint32_t cols = 32;
@@ -333,7 +340,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     // into an even number of groups of <= 128, and a work item is (shape, vertex chunk,
     // pair of groups), one group per CTA of the pair. Items are sorted by cost and dealt
     // to the CTA pairs round-robin.
-    const int n_ctapairs = kTcCtas / 2;
+    const int n_ctapairs = P.bwd_ctas / 2;
     int64_t bw_work = 0;
     for (int s = 0; s < n_shapes; ++s)
       if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + 255) / 256);
@@ -415,7 +422,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
       if (P.shapes[s].dfeat) bw_work += P.shapes[s].n * (int64_t)((P.shapes[s].d + nf_g - 1) / nf_g);
     const int64_t bw_chunk = opt.bwd_chunk_v ? (int64_t)opt.bwd_chunk_v
                                              : std::min<int64_t>(kTcChunkV, std::max<int64_t>(
-                                                   1024, (bw_work / (4 * kTcCtas) + 127) / 128 * 128));
+                                                   1024, (bw_work / (4 * P.bwd_ctas) + 127) / 128 * 128));
     std::vector<TcBwdItem> items;
     for (int s = 0; s < n_shapes; ++s) {
       const ShapeDev& sd = P.shapes[s];
@@ -449,12 +456,13 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
         if (cx != cy) return cx > cy;
         return a < b;
       });
-      P.bw_cta_first.assign(kTcCtas + 1, 0);
-      for (int c = 0; c < kTcCtas; ++c) {
+      const int nctas = P.bwd_ctas;
+      P.bw_cta_first.assign(nctas + 1, 0);
+      for (int c = 0; c < nctas; ++c) {
         P.bw_cta_first[c] = (int32_t)P.bw_items.size();
-        for (size_t j = c; j < order.size(); j += kTcCtas) P.bw_items.push_back(items[order[j]]);
+        for (size_t j = c; j < order.size(); j += nctas) P.bw_items.push_back(items[order[j]]);
       }
-      P.bw_cta_first[kTcCtas] = (int32_t)P.bw_items.size();
+      P.bw_cta_first[nctas] = (int32_t)P.bw_items.size();
     }
     const int fixed = 1024 + 512;
     const int out_staging = 8 * 4096;   // FP32 dF staging of the eight epilogue warps
@@ -920,7 +928,7 @@ int32_t fmap_project(fmap_batch* b, float* a_out, void* ws, size_t ws_bytes, voi
     tp.err = static_cast<int*>(ws);
     {
       TimedScope ts(b, FMAP_KIND_PROJECT, st);
-      e = P.tc32 ? launch_project_tc32(tp, kTcCtas, L.smem, st) : launch_project_tc(tp, kTcCtas, L.smem, st);
+      e = P.tc32 ? launch_project_tc32(tp, P.proj_ctas, L.smem, st) : launch_project_tc(tp, P.proj_ctas, L.smem, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "project (tensor cores)");
   }
@@ -963,18 +971,14 @@ int32_t fmap_solve(fmap_batch* b, const float* a, float* c_out, void* saved, int
   return FMAP_OK;
 }
 
-int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved,
-                            float* d_a, float* d_mask, float* d_lambda, int32_t* status, void* ws,
-                            size_t ws_bytes, void* stream) {
-  if (!b) return FMAP_ERR_INVALID_ARG;
-  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
-  if (!d_c || !a || !c) return FMAP_ERR_INVALID_ARG;
-  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bwd_bytes);
-  if (rc) return rc;
-  if (saved && !aligned(saved, 256)) return FMAP_ERR_WORKSPACE;
-  DeviceGuard dg(b->ctx->device);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  float* w = static_cast<float*>(ws);
+}  // extern "C"
+
+namespace {
+
+// The adjoint part of the backward pass: dC -> Gamma (adjoint row solves) -> dA (and dD,
+// dlambda), written to da.
+int32_t adjoint_impl(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved, float* da,
+                     float* d_mask, float* d_lambda, int32_t* status, float* w, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (status) {
     TimedScope ts(b, FMAP_KIND_STATUS, st);
@@ -1001,37 +1005,90 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
     e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint gemms");
-  float* da = d_a ? d_a : w + b->plan.da_int_off;
   {
     TimedScope ts(b, FMAP_KIND_GATHER, st);
     e = launch_gather_da(b->dev, (int)b->plan.max_kd, da, w, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "gather dA");
-  if (!b->plan.bw_items.empty()) {
-    const Plan& P = b->plan;
-    {
-      TimedScope ts(b, FMAP_KIND_GATHER, st);
-      e = P.tc_bwd32
-              ? launch_build_dat_image32(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st)
-              : launch_build_dat_image(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "dA image");
-    TcBwdParams bp{};
-    bp.shapes = b->dev.shapes;
-    bp.phimaps = b->d_phimaps_bwd;
-    bp.dfmaps = b->d_dfmaps;
-    bp.items = b->d_bw_items;
-    bp.cta_first = b->d_bw_cta_first;
-    bp.stages = P.bw_stages;
-    bp.b_bytes_max = P.bw_b_bytes;
-    bp.tmem_cols = P.tc_bwd32 ? 128 : 256;   // two accumulators of <= 64 or <= 128 columns
-    bp.ws = w;
-    bp.err = static_cast<int*>(ws);
+  return FMAP_OK;
+}
+
+// dF = diag(M) Phi dA for every shape with a dF buffer: the dA^T images, then the
+// tensor-core backward projection.
+int32_t project_backward_impl(fmap_batch* b, const float* da, float* w, void* ws, cudaStream_t st) {
+  if (b->plan.bw_items.empty()) return FMAP_OK;
+  const Plan& P = b->plan;
+  cudaError_t e;
+  {
+    TimedScope ts(b, FMAP_KIND_GATHER, st);
+    e = P.tc_bwd32
+            ? launch_build_dat_image32(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st)
+            : launch_build_dat_image(b->dev.shapes, b->d_bw_groups, (int)P.bw_groups.size(), P.bw_max_img, da, w, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dA image");
+  TcBwdParams bp{};
+  bp.shapes = b->dev.shapes;
+  bp.phimaps = b->d_phimaps_bwd;
+  bp.dfmaps = b->d_dfmaps;
+  bp.items = b->d_bw_items;
+  bp.cta_first = b->d_bw_cta_first;
+  bp.stages = P.bw_stages;
+  bp.b_bytes_max = P.bw_b_bytes;
+  bp.tmem_cols = P.tc_bwd32 ? 128 : 256;   // two accumulators of <= 64 or <= 128 columns
+  bp.ws = w;
+  bp.err = static_cast<int*>(ws);
+  {
     TimedScope ts(b, FMAP_KIND_PROJECT_BWD, st);
-    e = P.tc_bwd32 ? launch_project_bwd_tc32(bp, kTcCtas, P.bw_smem, st) : launch_project_bwd_tc(bp, kTcCtas, P.bw_smem, st);
+    e = P.tc_bwd32 ? launch_project_bwd_tc32(bp, P.bwd_ctas, P.bw_smem, st)
+                   : launch_project_bwd_tc(bp, P.bwd_ctas, P.bw_smem, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "project backward");
   return FMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved,
+                            float* d_a, float* d_mask, float* d_lambda, int32_t* status, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
+  if (!d_c || !a || !c) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bwd_bytes);
+  if (rc) return rc;
+  if (saved && !aligned(saved, 256)) return FMAP_ERR_WORKSPACE;
+  DeviceGuard dg(b->ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* w = static_cast<float*>(ws);
+  float* da = d_a ? d_a : w + b->plan.da_int_off;
+  rc = adjoint_impl(b, d_c, a, c, saved, da, d_mask, d_lambda, status, w, st);
+  if (rc) return rc;
+  return project_backward_impl(b, da, w, ws, st);
+}
+
+int32_t fmap_adjoint(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved, float* d_a,
+                     float* d_mask, float* d_lambda, int32_t* status, void* ws, size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
+  if (!d_c || !a || !c || !d_a) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bwd_bytes);
+  if (rc) return rc;
+  if (saved && !aligned(saved, 256)) return FMAP_ERR_WORKSPACE;
+  DeviceGuard dg(b->ctx->device);
+  return adjoint_impl(b, d_c, a, c, saved, d_a, d_mask, d_lambda, status, static_cast<float*>(ws),
+                      static_cast<cudaStream_t>(stream));
+}
+
+int32_t fmap_project_backward(fmap_batch* b, const float* d_a, void* ws, size_t ws_bytes, void* stream) {
+  if (!b) return FMAP_ERR_INVALID_ARG;
+  if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
+  if (!d_a) return FMAP_ERR_INVALID_ARG;
+  int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bwd_bytes);
+  if (rc) return rc;
+  DeviceGuard dg(b->ctx->device);
+  return project_backward_impl(b, d_a, static_cast<float*>(ws), ws, static_cast<cudaStream_t>(stream));
 }
 
 int32_t fmap_loss_orth(fmap_batch* b, const float* c, const float* c_gt, float* loss, float* d_c, void* ws,

@@ -34,15 +34,14 @@ constexpr int kStageV = 64;            // vertices per pipeline stage (= one 128
 constexpr uint32_t kBoxBytes = 64 * 64 * 2;   // one TMA box: 64 vertices x 64 features bf16
 constexpr uint32_t kPhiBoxBytes = 64 * 128;    // one TMA box: 64 vertices x 32 basis functions fp32
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-}
-
+// (a, b) -> BF16 heads RN(a), RN(b) and remainders RN(a - head), RN(b - head), each pair
+// packed low = a, high = b (one packed conversion per pair).
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-  lo = pack_bf16(a - __bfloat162float(ha), b - __bfloat162float(hb));
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) project_tc_kernel(TcProjParams P) {

@@ -165,6 +165,8 @@ def test_options_validation(lib):
     ("bwd_chunk_v", (0, 1024, 65536), (512, 1000, 131072)),
     ("solve_threads_k64", (0, 64, 128), (32, 256)),
     ("solve_threads_k128", (0, 128, 256), (64, 320)),
+    ("proj_ctas", (0, 1, 48, 152), (-1, 153)),
+    ("bwd_ctas", (0, 2, 64, 152), (-2, 1, 63, 154)),
 ])
 def test_tuning_knob_validation(lib, knob, good, bad):
     """Every tuning knob defaults to 0 (built-in choice); values outside its documented set
@@ -206,6 +208,8 @@ def test_store_factor_threshold(lib):
 def test_calls_without_batch_are_rejected(lib):
     assert lib.fmap_project(None, None, None, 0, None) == 1
     assert lib.fmap_solve(None, None, None, None, None, None, 0, None) == 1
+    assert lib.fmap_adjoint(None, None, None, None, None, None, None, None, None, None, 0, None) == 1
+    assert lib.fmap_project_backward(None, None, None, 0, None) == 1
 
 
 # ------------------------------------------------------------ independence of oracle and CUDA path

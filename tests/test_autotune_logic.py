@@ -50,8 +50,9 @@ def test_coordinate_descent_and_cache(tmp_path, monkeypatch):
     assert res["baseline_ms"] == 10.0 and abs(res["ms"] - 8.4) < 1e-9
     n_trials = sum(len([v for v in vals if v != 0]) for vals in autotune.CANDIDATES.values())
     assert len(res["trials"]) == 1 + n_trials
-    for knob, v in res["tuning"].items():
-        assert v in autotune.CANDIDATES[knob]
+    for knob in autotune.CANDIDATES:
+        assert res["tuning"][knob] in autotune.CANDIDATES[knob]
+    assert res["tuning"]["proj_ctas"] == 0 and res["tuning"]["bwd_ctas"] == 0   # not searched here
     with open(cache) as fh:
         assert autotune.batch_signature(b) in json.load(fh)
 

@@ -335,6 +335,41 @@ def test_backward_bf16_fp32_copy(d, ks, n_range):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["bf16"]
 
 
+@pytest.mark.parametrize("feat_dtype", ["fp32", "bf16"])
+def test_split_backward_and_projection_cta_counts(feat_dtype):
+    """fmap_adjoint followed by fmap_project_backward writes the same dL/dA and dL/dF as
+    fmap_solve_backward, bit for bit; with the projections on fewer persistent CTAs
+    (proj_ctas = 48, bwd_ctas = 38) A, C and dL/dF still match the oracle."""
+    import torch
+    from paper_2604_10377_gb300 import api
+    wl = synth.make_small(33, 4, (700, 9000), [30, 64, 100, 200], 256, feat_dtype=feat_dtype)
+    b = api.batch_from_workload(wl, with_grad=True)
+    a = b.project(); c = b.solve(a)
+    gt = api.flat_c(b, [p.c_gt for p in wl.pairs])
+    _, dc = b.loss_orth(c, gt)
+    da1 = b.solve_backward(dc, a, c).clone(); df1 = b.dfeat.clone()
+    b.dfeat.zero_()
+    da2 = b.adjoint(dc, a, c, d_a=torch.empty_like(da1))
+    b.project_backward(da2)
+    torch.cuda.synchronize()
+    assert torch.equal(da1, da2) and torch.equal(df1, b.dfeat)
+
+    b2 = api.batch_from_workload(wl, with_grad=True, tuning={"proj_ctas": 48, "bwd_ctas": 38})
+    a2 = b2.project(); c2 = b2.solve(a2)
+    _, dc2 = b2.loss_orth(c2, api.flat_c(b2, [p.c_gt for p in wl.pairs]))
+    b2.solve_backward(dc2, a2, c2)
+    torch.cuda.synchronize()
+    shapes, pairs, fwd, losses, dcs, g = _oracle_backward(wl)
+    tol, gtol = TOL[feat_dtype], GTOL[feat_dtype]
+    assert np.all(b2.status[:len(wl.pairs)].cpu().numpy() == 0)
+    for s in range(len(wl.shapes)):
+        assert rel_fro(b2.a_view(a2, s).cpu().numpy(), fwd["A"][s]) <= tol
+        dfs = b2.layout.feat_view(b2.dfeat, s).float().cpu().numpy()
+        assert rel_fro(dfs, g["dF"][s]) <= gtol
+    for p in range(len(wl.pairs)):
+        assert rel_fro(b2.c_view(c2, p).cpu().numpy(), fwd["C"][p]) <= tol
+
+
 @pytest.mark.parametrize("feat_dtype,use_saved", [("fp32", True), ("bf16", True), ("bf16", False)])
 def test_large_spectral_sizes(feat_dtype, use_saved):
     """k above 256 up to the 304 limit: the tensor-core projection splits the basis into
