@@ -433,7 +433,7 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
     # backward pass, none stored
     store_max_k = 0 if wid == 3 else args.store_factors_max_k
     t_gen = time.time()
-    wl = synth.make_config(wid, replica=rank)
+    wl = synth.make_config(wid, replica=rank, pairs=range(args.pairs) if args.pairs else None)
     t_gen = time.time() - t_gen
     lay = api.BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)
     host = lay.pack_host(wl.shapes)
@@ -683,7 +683,8 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
 
     out = {
         "value": rate_step, "ms_per_step": ms_step,
-        "config": {"workload": WORKLOADS[wid], "pairs_per_gpu": npairs, "global_batch": world * npairs,
+        "config": {"workload": WORKLOADS[wid] + (f" (first {npairs} pairs only)" if args.pairs else ""),
+                   "pairs_per_gpu": npairs, "global_batch": world * npairs,
                    "parallelism": f"pairs sharded over {world} GPU(s), no collective",
                    "l2": "inputs larger than L2 (%.2f GB streamed per step)" % (work["project"]["bytes"] / 1e9)
                    if work["project"]["bytes"] > 129e6 else
@@ -1000,6 +1001,8 @@ def main():
     ap.add_argument("--no-sub-workloads", action="store_true",
                     help="time only the main workload (not the other four as sub-results)")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle check of sampled pairs")
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="first N pairs of the workload only (small cases for ncu captures; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
