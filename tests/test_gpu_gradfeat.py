@@ -93,6 +93,31 @@ def test_gradient_features_long_and_empty_rows_and_wide_layouts():
     assert rel_fro(got[:, :dim], ref) <= TOL["fp32"]
 
 
+def test_tiles_of_long_rows_beside_short_ones():
+    """Whole 128-vertex tiles of long rows (24 entries per row: three rounds of eight loads
+    per lane; 16 per row: two) beside tiles of short rows, in one call, against the oracle."""
+    from paper_2604_10377_gb300 import api
+    rng = np.random.default_rng(6)
+    n, dim = 600, 32
+    lens = rng.integers(0, 9, n)
+    lens[:128] = 24
+    lens[300:428] = 16   # 2048 entries: exactly the slice
+    ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = np.concatenate([np.sort(rng.choice(n, size=l, replace=False)) for l in lens]).astype(np.int32)
+    gi = synth.GradientInput(n=n, dim=dim, row_ptr=ptr, col_idx=col,
+                             g_re=rng.standard_normal(len(col)).astype(np.float32),
+                             g_im=rng.standard_normal(len(col)).astype(np.float32),
+                             feat=rng.standard_normal((n, dim)).astype(np.float32),
+                             a_re=(rng.standard_normal((dim, dim)) / 6).astype(np.float32),
+                             a_im=(rng.standard_normal((dim, dim)) / 6).astype(np.float32))
+    row_ptr, col_idx, vals, x, are, aim = _dev(gi)
+    for variant in ("A", "B"):
+        out, status = api.gradient_features(row_ptr, col_idx, vals, x, are, aim, variant=variant)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert rel_fro(out.cpu().numpy(), _oracle(gi, variant)) <= TOL["fp32"], variant
+
+
 def test_out_of_range_column_is_reported_and_skipped():
     """A column index past the input rows sets the status word to INVALID_ARG and the entry
     is skipped (the kernel checks every index before it loads)."""
