@@ -88,6 +88,9 @@ typedef struct fmap_options {
      * part of the SMs, so that the solves' blocks hold the rest. */
     int32_t proj_ctas;          /* forward projection */
     int32_t bwd_ctas;           /* backward projection, even (two CTAs share each vertex tile) */
+    int32_t solve_no_g_copy;    /* row solves of k <= 128: 0 keeps a copy of G in shared memory for the
+                                   refinement residual (default), 1 reads G from L2 instead (less shared
+                                   memory per block, more blocks per SM) */
 } fmap_options;
 
 typedef struct fmap_shape_desc {

@@ -31,6 +31,7 @@ CANDIDATES: Dict[str, tuple] = {
     "proj_seg_max_v": (0, 4096, 16384),
     "solve_threads_k64": (0, 128),
     "solve_threads_k128": (0, 256),
+    "solve_no_g_copy": (0, 1),
 }
 
 

@@ -117,6 +117,7 @@ int32_t validate_options(const fmap_options& o) {
   if (o.solve_threads_k64 != 0 && o.solve_threads_k64 != 64 && o.solve_threads_k64 != 128) return FMAP_ERR_INVALID_ARG;
   if (o.solve_threads_k128 != 0 && o.solve_threads_k128 != 128 && o.solve_threads_k128 != 256)
     return FMAP_ERR_INVALID_ARG;
+  if (o.solve_no_g_copy != 0 && o.solve_no_g_copy != 1) return FMAP_ERR_INVALID_ARG;
   if (o.proj_ctas < 0 || o.proj_ctas > kTcCtas) return FMAP_ERR_INVALID_ARG;
   if (o.bwd_ctas < 0 || o.bwd_ctas > kTcCtas || (o.bwd_ctas & 1)) return FMAP_ERR_INVALID_ARG;
   return FMAP_OK;
@@ -503,6 +504,7 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     SolveGroup g{};
     g.first = (int32_t)P.systems.size();
     g.threads = threads[gi];
+    g.no_g_copy = opt.solve_no_g_copy;
     std::vector<int> members;
     for (int p = 0; p < n_pairs; ++p) {
       const int k = P.pairs[p].k;

@@ -182,6 +182,8 @@ struct SolveGroup {
   int32_t count;     // systems in this group
   int32_t kmax;      // largest k in the group
   int32_t threads;
+  int32_t no_g_copy; // 1: no shared-memory copy of G for the refinement residual (the residual
+                     // then reads G from L2); 0: the built-in rule, a copy for k <= 128
 };
 
 enum SolveMode { kSolveForward = 0, kSolveAdjoint = 1 };

@@ -712,9 +712,9 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
 // Launches for k <= kGsMaxK reserve a copy of G (k x gram_ld(k) floats) after the vectors.
 constexpr int kGsMaxK = 128;
 
-size_t chol_smem_bytes(int kmax) {
+size_t chol_smem_bytes(int kmax, bool g_copy = true) {
   const int Q = (kmax + 7) / 8, kp = 8 * Q;
-  const int64_t gs = kmax <= kGsMaxK ? (int64_t)kmax * gram_ld(kmax) : 0;
+  const int64_t gs = (g_copy && kmax <= kGsMaxK) ? (int64_t)kmax * gram_ld(kmax) : 0;
   return (size_t)(factor_floats(Q) + 8 * kp + 4 * kp + gs) * sizeof(float);
 }
 
@@ -742,8 +742,9 @@ cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* sys
   // one thread per row: the substitutions, the TRSM and the (a) update assume NT >= kp
   const int nt = (g.threads == 64 || g.threads == 128 || g.threads == 256) ? g.threads : 320;
   if (8 * ((g.kmax + 7) / 8) > nt) return cudaErrorInvalidValue;
-  const size_t smem = chol_smem_bytes(g.kmax);
-  const int gs = g.kmax <= kGsMaxK ? 1 : 0;
+  const bool g_copy = g.no_g_copy == 0 && g.kmax <= kGsMaxK;
+  const size_t smem = chol_smem_bytes(g.kmax, g_copy);
+  const int gs = g_copy ? 1 : 0;
   switch (g.threads) {
     case 64:
       chol_solve_kernel<64><<<g.count, 64, smem, st>>>(b, systems, g.first, g.count, mode, rhs_flat, out_flat, saved,

@@ -167,6 +167,7 @@ def test_options_validation(lib):
     ("solve_threads_k128", (0, 128, 256), (64, 320)),
     ("proj_ctas", (0, 1, 48, 152), (-1, 153)),
     ("bwd_ctas", (0, 2, 64, 152), (-2, 1, 63, 154)),
+    ("solve_no_g_copy", (0, 1), (-1, 2)),
 ])
 def test_tuning_knob_validation(lib, knob, good, bad):
     """Every tuning knob defaults to 0 (built-in choice); values outside its documented set

@@ -167,6 +167,14 @@ def test_row_solve_sizes_129_to_200(feat_dtype, hi_min):
     _check_forward(wl, hi_gram_min_k=hi_min)
 
 
+@pytest.mark.parametrize("ir", [1, 2])
+def test_refinement_residual_without_the_shared_memory_copy_of_g(ir):
+    """Row systems of k <= 128 with solve_no_g_copy = 1: the refinement residual reads G from
+    L2 instead of a shared-memory copy; forward against the oracle at the FP32 tolerance."""
+    wl = synth.make_small(19, 4, (1000, 6000), [20, 60, 100, 128], 320)
+    _check_forward(wl, ir_steps=ir, tuning={"solve_no_g_copy": 1})
+
+
 def test_bitwise_reproducible():
     wl = synth.make_small(7, 3, (3000, 20000), [30, 64, 100], 64)
     from paper_2604_10377_gb300 import api
