@@ -91,6 +91,14 @@ typedef struct fmap_options {
     int32_t solve_no_g_copy;    /* row solves of k <= 128: 0 keeps a copy of G in shared memory for the
                                    refinement residual (default), 1 reads G from L2 instead (less shared
                                    memory per block, more blocks per SM) */
+    int32_t adjoint_kernel;     /* W = Gamma^T C + C^T Gamma, dA_x = Gamma^T A_y - W A_x, dA_y = Gamma A_x:
+                                   1 tensor cores (three TF32 passes), 2 CUDA cores (FP32 FMA tiles);
+                                   0 the built-in choice: tensor cores when dA_x has at least two
+                                   128-column tiles per SM, else CUDA cores */
+    int32_t adjoint_features;   /* tensor-core adjoint GEMMs: output columns per CTA, 64, 128 or 256
+                                   (default 128, or 64 below two dA_x tiles per SM) */
+    int32_t adjoint_stages;     /* tensor-core adjoint GEMMs: shared-memory stages per CTA, 1 or 2
+                                   (default 1) */
 } fmap_options;
 
 typedef struct fmap_shape_desc {

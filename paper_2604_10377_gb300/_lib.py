@@ -30,11 +30,14 @@ class Options(ctypes.Structure):
                 ("store_factors_max_k", c_int32), ("adjoint_ir_steps", c_int32),
                 ("proj_max_stages", c_int32), ("proj_seg_max_v", c_int32), ("bwd_group_features", c_int32),
                 ("bwd_chunk_v", c_int32), ("solve_threads_k64", c_int32), ("solve_threads_k128", c_int32),
-                ("proj_ctas", c_int32), ("bwd_ctas", c_int32), ("solve_no_g_copy", c_int32)]
+                ("proj_ctas", c_int32), ("bwd_ctas", c_int32), ("solve_no_g_copy", c_int32),
+                ("adjoint_kernel", c_int32),
+                ("adjoint_features", c_int32), ("adjoint_stages", c_int32)]
 
 
 TUNING_FIELDS = ("proj_max_stages", "proj_seg_max_v", "bwd_group_features", "bwd_chunk_v", "proj_ctas", "bwd_ctas",
-                 "solve_threads_k64", "solve_threads_k128", "solve_no_g_copy")
+                 "solve_threads_k64", "solve_threads_k128", "solve_no_g_copy", "adjoint_kernel",
+                 "adjoint_features", "adjoint_stages")
 
 
 class ShapeDesc(ctypes.Structure):

@@ -32,6 +32,9 @@ CANDIDATES: Dict[str, tuple] = {
     "solve_threads_k64": (0, 128),
     "solve_threads_k128": (0, 256),
     "solve_no_g_copy": (0, 1),
+    "adjoint_kernel": (0, 1, 2),
+    "adjoint_features": (0, 64, 128, 256),
+    "adjoint_stages": (0, 1, 2),
 }
 
 

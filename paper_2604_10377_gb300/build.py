@@ -28,6 +28,7 @@ SOURCES = [
     "fmap_noalloc.cu",
     "k_peaks.cu",
     "k_gradfeat.cu",
+    "k_adjoint_tc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

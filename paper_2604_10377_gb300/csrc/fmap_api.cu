@@ -99,6 +99,8 @@ struct Plan {
   std::vector<TcBwdGroup> bw_groups;
   int bw_max_img = 0, bw_stages = 0, bw_smem = 0;
   uint32_t bw_b_bytes = 0;
+  // tensor-core adjoint GEMMs (built when the batch is created: the SM count sets the tiles)
+  AdjTcPlan adj;
   fmap_sizes sizes{};
 };
 
@@ -118,6 +120,10 @@ int32_t validate_options(const fmap_options& o) {
   if (o.solve_threads_k128 != 0 && o.solve_threads_k128 != 128 && o.solve_threads_k128 != 256)
     return FMAP_ERR_INVALID_ARG;
   if (o.solve_no_g_copy != 0 && o.solve_no_g_copy != 1) return FMAP_ERR_INVALID_ARG;
+  if (o.adjoint_kernel < 0 || o.adjoint_kernel > 2) return FMAP_ERR_INVALID_ARG;
+  if (o.adjoint_features != 0 && o.adjoint_features != 64 && o.adjoint_features != 128 && o.adjoint_features != 256)
+    return FMAP_ERR_INVALID_ARG;
+  if (o.adjoint_stages < 0 || o.adjoint_stages > 2) return FMAP_ERR_INVALID_ARG;
   if (o.proj_ctas < 0 || o.proj_ctas > kTcCtas) return FMAP_ERR_INVALID_ARG;
   if (o.bwd_ctas < 0 || o.bwd_ctas > kTcCtas || (o.bwd_ctas & 1)) return FMAP_ERR_INVALID_ARG;
   return FMAP_OK;
@@ -564,7 +570,8 @@ struct fmap_batch {
   const TcBwdItem* d_bw_items = nullptr;
   const int32_t* d_bw_cta_first = nullptr;
   const TcBwdGroup* d_bw_groups = nullptr;
-  int sm_count = 148;
+  const AdjItem* d_adj_items = nullptr;
+  int sm_count = 152;
 };
 
 namespace {
@@ -693,6 +700,19 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   if (!dg.ok) { delete b; return cuda_fail(cudaErrorInvalidDevice, "cudaSetDevice"); }
   cudaError_t e = solve_set_smem_limits();
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaFuncSetAttribute"); }
+  {
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    b->sm_count = dev_sms > 0 ? dev_sms : kTcCtas;
+  }
+  if (ctx->opt.adjoint_kernel != 2 && n_pairs > 0) {
+    std::vector<int3> pk(P.pairs.size());
+    for (size_t p = 0; p < P.pairs.size(); ++p)
+      pk[p] = make_int3(P.pairs[p].k, P.shapes[P.pairs[p].y].k, P.pairs[p].d);
+    P.adj.stages = ctx->opt.adjoint_stages;
+    P.adj.features = ctx->opt.adjoint_features;
+    adjoint_tc_plan(pk, b->sm_count, P.adj);
+  }
 
   // one allocation for every table
   auto bytes_of = [](size_t n, size_t sz) { return (int64_t)align_up((int64_t)(n * sz), 256); };
@@ -711,7 +731,8 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_bi = o_pb + bytes_of(P.shapes.size(), sizeof(CUtensorMap));
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
   const int64_t o_bg = o_bo + bytes_of(P.bw_cta_first.size(), sizeof(int32_t));
-  const int64_t total = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup)) + 256;
+  const int64_t o_ai = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup));
+  const int64_t total = o_ai + bytes_of(P.adj.items.size(), sizeof(AdjItem)) + 256;
   e = cudaMalloc(&b->dev_mem, (size_t)total);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch tables)"); }
   char* base = static_cast<char*>(b->dev_mem);
@@ -721,6 +742,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   put(o_pr, P.pairs.data(), P.pairs.size() * sizeof(PairDev));
   put(o_sl, P.slot_list.data(), P.slot_list.size() * sizeof(int64_t));
   put(o_sy, P.systems.data(), P.systems.size() * sizeof(int2));
+  put(o_ai, P.adj.items.data(), P.adj.items.size() * sizeof(AdjItem));
   if (n_shapes > 0) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) { cudaFree(b->dev_mem); delete b; return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
@@ -816,9 +838,6 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
     put(o_tg, P.tc_groups.data(), P.tc_groups.size() * sizeof(TcRedGroup));
     e = P.tc32 ? project_tc32_set_smem(P.tc_smem) : project_tc_set_smem(P.tc_smem);
     if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaFuncSetAttribute(project)"); }
-    int dev_sms = 0;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    b->sm_count = dev_sms > 0 ? dev_sms : 148;
   }
   e = cudaMemcpy(b->dev_mem, host.data(), (size_t)total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(b->dev_mem); delete b; return cuda_fail(e, "cudaMemcpy(batch tables)"); }
@@ -842,6 +861,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_bw_items = reinterpret_cast<const TcBwdItem*>(base + o_bi);
   b->d_bw_cta_first = reinterpret_cast<const int32_t*>(base + o_bo);
   b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
+  b->d_adj_items = reinterpret_cast<const AdjItem*>(base + o_ai);
   *out = b;
   return FMAP_OK;
 }
@@ -1004,7 +1024,10 @@ int32_t adjoint_impl(fmap_batch* b, const float* d_c, const float* a, const floa
   }
   {
     TimedScope ts(b, FMAP_KIND_ADJ_GEMM, st);
-    e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, st);
+    const int ak = b->plan.opt.adjoint_kernel;
+    const bool simt = ak == 2 || (ak == 0 && !b->plan.adj.fills_sms);
+    e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, simt, st);
+    if (e == cudaSuccess && !simt) e = launch_adjoint_tc(b->dev, b->d_adj_items, b->plan.adj, a, c, w, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint gemms");
   {

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/fmap.h"
 
@@ -191,8 +192,28 @@ enum SolveMode { kSolveForward = 0, kSolveAdjoint = 1 };
 cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode,
                          const float* rhs_flat, float* out_flat, float* saved_rw, int32_t* status,
                          float* ws, cudaStream_t st);
+// The mask and lambda gradients (when d_mask / d_lambda are given) and, with simt, W and the
+// dA contributions on the CUDA cores (FP32 FMA tiles)
 cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
-                                 float* d_mask, float* d_lambda, float* ws, cudaStream_t st);
+                                 float* d_mask, float* d_lambda, float* ws, bool simt, cudaStream_t st);
+
+// One CTA of the tensor-core adjoint GEMMs: output rows r0 .. r0+127 and columns f0 .. f0+NT-1
+// of W (kind 2), dA_y (kind 1) or dA_x (kind 0) of one pair.
+struct AdjItem {
+  int32_t pair, kind, r0, f0;
+};
+struct AdjTcPlan {
+  std::vector<AdjItem> items;   // the first launch's n_first items (kinds 2, 1), then kind 0
+  int n_first = 0;
+  int stages = 0;               // shared-memory stages, 1 or 2 (0 on input: the built-in choice)
+  int features = 0;             // output columns per CTA, 64, 128 or 256 (0 on input: built-in)
+  bool fills_sms = false;       // at least two dA_x tiles of 128 columns per SM
+};
+// shapes[p] = (k_X, k_Y, d) of pair p; fills the work list, longest reduction first
+void adjoint_tc_plan(const std::vector<int3>& shapes, int sms, AdjTcPlan& P);
+cudaError_t launch_adjoint_tc(const BatchDev& b, const AdjItem* items, const AdjTcPlan& P, const float* a,
+                              const float* c, float* ws, cudaStream_t st);
+cudaError_t adjoint_tc_set_smem();
 cudaError_t launch_gather_da(const BatchDev& b, int max_kd, float* d_a, const float* ws, cudaStream_t st);
 cudaError_t launch_loss_orth(const BatchDev& b, int max_k, const float* c, const float* c_gt, float* loss,
                              float* d_c, float* ws, float* partial, cudaStream_t st);

@@ -733,7 +733,8 @@ cudaError_t solve_set_smem_limits() {
   if ((e = set_limit<64>()) != cudaSuccess) return e;
   if ((e = set_limit<128>()) != cudaSuccess) return e;
   if ((e = set_limit<256>()) != cudaSuccess) return e;
-  return set_limit<320>();
+  if ((e = set_limit<320>()) != cudaSuccess) return e;
+  return adjoint_tc_set_smem();
 }
 
 cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode, const float* rhs_flat,

@@ -422,16 +422,19 @@ __global__ void status_clear_kernel(int32_t* status, int n) {
 }  // namespace
 
 cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
-                                 float* d_mask, float* d_lambda, float* ws, cudaStream_t st) {
+                                 float* d_mask, float* d_lambda, float* ws, bool simt, cudaStream_t st) {
   if (b.n_pairs <= 0) return cudaSuccess;
   const int ntk = (max_k + kTile - 1) / kTile, ntd = (max_d + kTile - 1) / kTile;
-  adjoint_w_kernel<<<dim3(ntk * ntk, 1, b.n_pairs), 256, 0, st>>>(b, c, ws);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (simt) {
+    adjoint_w_kernel<<<dim3(ntk * ntk, 1, b.n_pairs), 256, 0, st>>>(b, c, ws);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (d_lambda || d_mask) {
     adjoint_dlambda_kernel<<<b.n_pairs, 256, 0, st>>>(b, c, d_mask, d_lambda, ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (!simt) return cudaSuccess;
   adjoint_da_kernel<<<dim3(ntk * ntd, 2, b.n_pairs), 256, 0, st>>>(b, a, ws);
   return cudaGetLastError();
 }

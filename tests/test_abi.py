@@ -168,6 +168,9 @@ def test_options_validation(lib):
     ("proj_ctas", (0, 1, 48, 152), (-1, 153)),
     ("bwd_ctas", (0, 2, 64, 152), (-2, 1, 63, 154)),
     ("solve_no_g_copy", (0, 1), (-1, 2)),
+    ("adjoint_kernel", (0, 1, 2), (-1, 3)),
+    ("adjoint_features", (0, 64, 128, 256), (-1, 32, 96, 512)),
+    ("adjoint_stages", (0, 1, 2), (-1, 3)),
 ])
 def test_tuning_knob_validation(lib, knob, good, bad):
     """Every tuning knob defaults to 0 (built-in choice); values outside its documented set

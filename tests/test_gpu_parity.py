@@ -396,6 +396,45 @@ def test_large_spectral_sizes(feat_dtype, use_saved):
         assert rel_fro(out["dF"][s], g["dF"][s]) <= gtol
 
 
+@pytest.mark.parametrize("tuning", [{"adjoint_kernel": 1, "adjoint_stages": 1, "adjoint_features": 256},
+                                    {"adjoint_kernel": 1, "adjoint_stages": 2, "adjoint_features": 256},
+                                    {"adjoint_kernel": 1, "adjoint_stages": 1, "adjoint_features": 128},
+                                    {"adjoint_kernel": 1, "adjoint_stages": 2, "adjoint_features": 64},
+                                    {"adjoint_kernel": 1}, {"adjoint_kernel": 2}])
+@pytest.mark.parametrize("d", [16, 272, 448])
+def test_adjoint_gemm_kernels(tuning, d):
+    """dA_x = Gamma^T A_y - W A_x and dA_y = Gamma A_x on the tensor cores (one or two
+    shared-memory stages, 64 to 256 columns per CTA) and on the CUDA cores, W = Gamma^T C +
+    C^T Gamma with them (the tensor-core kernel's first launch): square and
+    rectangular pairs with k from 3 to 304 (one to three 128-row tiles, reductions
+    k_Y + k_X up to 608 with ragged 32-wide tails), d of one partial feature tile (16), a
+    full and a 16-wide one (272) and a full and a 192-wide one (448); dA against the
+    oracle, and each tensor-core variant against the CUDA-core kernel at the FP32
+    accumulation level. k stays at or below d so that every Gram matrix has full rank."""
+    rng = np.random.default_rng(41)
+    ks = {16: [5, 8, 12, 16, 3, 10, 7, 14], 272: [5, 33, 129, 260, 270, 96, 200, 257],
+          448: [5, 33, 129, 300, 304, 96, 200, 257]}[d]
+    shapes = [_shape(rng, 500 + 41 * i, k, d) for i, k in enumerate(ks)]
+    pairs = [synth.Pair(x=0, y=1, lam=1e-2), synth.Pair(x=3, y=4, lam=1e-3), synth.Pair(x=2, y=5, lam=1e-2),
+             synth.Pair(x=6, y=7, lam=1e-3), synth.Pair(x=7, y=2, lam=1e-2), synth.Pair(x=4, y=4, lam=1e-2)]
+    mrng = np.random.default_rng(5)
+    for p in pairs:
+        p.c_gt = (mrng.standard_normal((ks[p.y], ks[p.x])) / np.sqrt(ks[p.x])).astype(np.float32)
+    wl = synth.Workload("adjoint_gemm", shapes, pairs, "fp32")
+    out = _gpu_backward(wl, tuning=tuning)
+    shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["fp32"]
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
+    if tuning.get("adjoint_kernel") != 2:
+        # two FP32-class accumulations of sums of length up to k_Y + k_X = 608 differ by a few
+        # 2^-24 sqrt(K) ~ 1.5e-6 relative per element, more where Gamma^T A_y and W A_x cancel
+        ref = _gpu_backward(wl, tuning={"adjoint_kernel": 2})
+        for s in range(len(wl.shapes)):
+            assert rel_fro(out["dA"][s], ref["dA"][s]) <= 1e-5
+
+
 def _tuning_cases():
     from paper_2604_10377_gb300.autotune import CANDIDATES
     return [(knob, v) for knob, vals in CANDIDATES.items() for v in vals if v != 0]
