@@ -192,6 +192,7 @@ class FmapBatch:
         dev = self.device
         if self.ws is None or self.ws.numel() < sz.ws_bwd_bytes:
             self.ws = torch.empty(max(256, sz.ws_bwd_bytes), dtype=torch.uint8, device=dev)
+            self.ws[:256].zero_()   # control words (fmap_project clears them again each step)
         if sz.saved_bytes and (self.saved is None or self.saved.numel() < sz.saved_bytes):
             self.saved = torch.empty(max(256, sz.saved_bytes), dtype=torch.uint8, device=dev)
 

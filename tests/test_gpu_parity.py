@@ -123,6 +123,22 @@ def test_not_spd_reports_row_and_nan():
     assert rel_fro(c_gpu[0], ref["C"][0]) < 1e-5
 
 
+def test_not_spd_in_a_256_thread_system():
+    """A row system of the 256-thread class (k = 150) meets an indefinite pivot in a late
+    panel (mask entry 140 of row system 5 of pair 1): status NOT_SPD | 5 << 8, that row of
+    C is NaN, the other rows and pair 0 match the oracle."""
+    wl = synth.make_small(5, 2, (3000, 3500), [150], 448, with_mask=True)
+    shapes, pairs = oracle_inputs(wl)
+    ref = orc.forward_batch(shapes, pairs)   # row systems other than 5 do not see its mask entry
+    wl.pairs[1].mask[5, 140] = -1e12
+    b, a_gpu, c_gpu, status = gpu_forward(wl)
+    assert status[0] == 0
+    assert status[1] == (4 | (5 << 8)), hex(int(status[1]))
+    assert np.all(np.isnan(c_gpu[1][5]))
+    assert rel_fro(c_gpu[0], ref["C"][0]) < 1e-5
+    assert rel_fro(np.delete(c_gpu[1], 5, axis=0), np.delete(ref["C"][1], 5, axis=0)) < 1e-5
+
+
 def test_empty_batch():
     from paper_2604_10377_gb300 import api
     lay = api.BatchLayout([100], [10], [16], "fp32")
@@ -138,18 +154,19 @@ def test_ir_steps_and_hi_gram():
         _check_forward(wl, ir_steps=ir, hi_gram_min_k=50)
 
 
-@pytest.mark.parametrize("ks,hi_min,ir", [((129, 150, 199), 200, 1), ((150, 256), 1000, 2)])
+@pytest.mark.parametrize("ks,hi_min,ir", [((129, 150, 199), 200, 1), ((150, 256), 1000, 2), ((136, 256), 1000, 0)])
 def test_refinement_with_fp32_gram_from_global(ks, hi_min, ir):
     """Row systems above the shared-memory copy of G (k > 128) with the FP32 Gram: the
     refinement residual reads the lower triangle of G from global memory, for one and two
-    refinement steps (d >= 2k, well-conditioned FP32 systems)."""
+    refinement steps (d >= 2k, well-conditioned FP32 systems); forward only (no saved
+    factors)."""
     rng = np.random.default_rng(17)
     shapes, pairs = [], []
     for i, k in enumerate(ks):
         shapes += [_shape(rng, 3000 + 7 * i, k, 512), _shape(rng, 2500 + 5 * i, k, 512)]
         pairs.append(synth.Pair(x=2 * i, y=2 * i + 1, lam=1e-2))
     wl = synth.Workload("gram_global", shapes, pairs, "fp32")
-    _check_forward(wl, ir_steps=ir, hi_gram_min_k=hi_min)
+    _check_forward(wl, ir_steps=ir, hi_gram_min_k=hi_min, with_grad=False)
 
 
 @pytest.mark.parametrize("feat_dtype,hi_min", [("fp32", 1000), ("fp32", 150), ("bf16", 200)])
@@ -256,6 +273,29 @@ def test_rectangular_maps(feat_dtype, use_saved):
     for s_ in range(len(wl.shapes)):
         assert rel_fro(out["dA"][s_], g["dA"][s_]) <= gtol
         assert rel_fro(out["dF"][s_], g["dF"][s_]) <= gtol
+
+
+@pytest.mark.parametrize("use_saved,adj_ir", [(True, 0), (False, 0), (True, 1), (False, 1)])
+@pytest.mark.parametrize("ks", [(129, 136), (160, 200), (231, 256)])
+def test_backward_256_thread_class(ks, use_saved, adj_ir):
+    """Backward through row systems of 128 < k <= 256: the adjoint solves on saved factors,
+    or refactoring in the adjoint pass, with and without adjoint refinement; FP32 and
+    double-float Gram sizes; dA, dF, dD against the oracle."""
+    rng = np.random.default_rng(31)
+    shapes, pairs = [], []
+    for i, k in enumerate(ks):
+        shapes += [_shape(rng, 1800 + 13 * i, k, 512), _shape(rng, 1700 + 11 * i, k, 512)]
+        pairs.append(synth.Pair(x=2 * i, y=2 * i + 1, lam=1e-2, c_gt=synth.random_orthogonal(60 + i, k)))
+    wl = synth.Workload("bwd_256", shapes, pairs, "fp32")
+    out = _gpu_backward(wl, use_saved=use_saved, adjoint_ir_steps=adj_ir)
+    shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert rel_fro(out["C"][p], fwd["C"][p]) <= TOL["fp32"]
+        assert rel_fro(out["dD"][p], g["pair"][p]["dD"]) <= GTOL["fp32"]
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["fp32"]
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
 
 
 @pytest.mark.parametrize("use_saved,adj_ir", [(True, 1), (False, 1), (True, 2)])
