@@ -198,8 +198,9 @@ def algorithmic_work(wl, ir_steps, saved_k_max):
     proj_bytes = sum(s.n * (4 * s.k + 4 + fsz * s.d) + 4 * s.k * s.d for s in wl.shapes)
     proj_flops = sum(2.0 * s.n * s.k * s.d for s in wl.shapes)
     bwd_bytes = sum(s.n * (4 * s.k + 4 + fsz * s.d) + 4 * s.k * s.d for s in wl.shapes)
-    solve_flops, adj_flops, loss_flops = 0.0, 0.0, 0.0
+    solve_flops, adj_flops, loss_flops, gemm_flops = 0.0, 0.0, 0.0, 0.0
     solve_bytes, adj_bytes = 0, 0
+    da_tiles = 0
     for p in wl.pairs:
         # C is ky x k: ky row systems of size k (square maps: ky == k)
         k, ky = wl.shapes[p.x].k, wl.shapes[p.y].k
@@ -209,12 +210,16 @@ def algorithmic_work(wl, ir_steps, saved_k_max):
         solve_flops += ky * k ** 3 / 3.0 + (2.0 + 4.0 * ir_steps) * ky * k ** 2
         adj_flops += (0.0 if k <= saved_k_max else ky * k ** 3 / 3.0) + 2.0 * ky * k ** 2
         loss_flops += 2.0 * ky * ky * k + 2.0 * ky * ky * k
+        # adjoint GEMMs: W = Gamma^T C + C^T Gamma, dA_y = Gamma A_x, dA_x = Gamma^T A_y - W A_x
+        d = wl.shapes[p.x].d
+        gemm_flops += 4.0 * k * k * ky + 2.0 * ky * k * d + 2.0 * k * (ky + k) * d
+        da_tiles += -(-k // 128) * -(-d // 128)
         # G, R and C move once each, saved factors written (forward) / read (adjoint)
         solve_bytes += 4 * (k * k + 2 * ky * k) + fac
         adj_bytes += 4 * 2 * ky * k + fac
     return dict(project=dict(bytes=proj_bytes, flops=proj_flops), project_bwd=dict(bytes=bwd_bytes, flops=proj_flops),
                 solve=dict(flops=solve_flops, bytes=solve_bytes), adj_solve=dict(flops=adj_flops, bytes=adj_bytes),
-                loss=dict(flops=loss_flops))
+                loss=dict(flops=loss_flops), adj_gemm=dict(flops=gemm_flops, da_tiles=da_tiles))
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -622,6 +627,17 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
                 r["tensor"] = {"achieved_tflops": tflops, "peak_tflops": measured[mma], "peak": mma,
                                "frac": tflops / measured[mma]}
             return r
+        if kind == "adj_gemm" and measured:
+            # the library's built-in choice (fmap_options.adjoint_kernel = 0): tensor cores when
+            # dA_x has at least two 128-column tiles per SM, else FP32 FMA tiles
+            ach = work[kind]["flops"] / (per_step_ms / 1000.0) / 1e12
+            if work[kind]["da_tiles"] >= 2 * SM_COUNT:
+                pk = measured["tf32_mma"] / 3.0
+                return {"kernel": kind, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                        "frac": ach / pk, "traffic": None,
+                        "peak_source": "measured TF32 MMA peak / 3 (three TF32 passes per FP32-class product)"}
+            return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak_tflops, "traffic": None, "peak_source": fp32_peak_source}
         flops = work.get(kind, {}).get("flops")
         if flops is None:
             return {"kernel": kind, "bound": "alu", "achieved": None, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
@@ -633,7 +649,8 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
                 "peak_source": fp32_peak_source}
 
     roofline = roof_for(dom)
-    others = {k: roof_for(k) for k in ("project", "project_bwd", "solve", "adj_solve") if k in kernels and k != dom}
+    others = {k: roof_for(k) for k in ("project", "project_bwd", "solve", "adj_solve", "adj_gemm")
+              if k in kernels and k != dom}
 
     # ---- accuracy against the FP64 oracle on sampled pairs (two of every k), last timed step
     accuracy = None

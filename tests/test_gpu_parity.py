@@ -475,6 +475,22 @@ def test_adjoint_gemm_kernels(tuning, d):
             assert rel_fro(out["dA"][s], ref["dA"][s]) <= 1e-5
 
 
+def test_adjoint_default_on_a_batch_that_fills_the_sms():
+    """160 pairs (k = 30, d = 256: 320 dA_x tiles of 128 columns, two per SM on 152 SMs):
+    the built-in choice runs the adjoint GEMMs on the tensor cores; dA and dF of every shape
+    against the oracle, and dA against the FP32 FMA tiles."""
+    wl = synth.make_small(43, 160, (300, 600), [30], 256)
+    out = _gpu_backward(wl)
+    shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
+    assert np.all(out["status"] == 0)
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["fp32"]
+        assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
+    ref = _gpu_backward(wl, tuning={"adjoint_kernel": 2})
+    for s in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s], ref["dA"][s]) <= 1e-5
+
+
 def _tuning_cases():
     from paper_2604_10377_gb300.autotune import CANDIDATES
     return [(knob, v) for knob, vals in CANDIDATES.items() for v in vals if v != 0]
