@@ -442,9 +442,10 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
     t_gen = time.time() - t_gen
     lay = api.BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)
     host = lay.pack_host(wl.shapes)
+    fixed_tuning = json.loads(args.tuning) if args.tuning else {}
     b = api.FmapBatch(lay, [(p.x, p.y, p.lam) for p in wl.pairs], device=dev, precision=wl.feat_dtype,
                       with_grad=True, masks=[p.mask for p in wl.pairs], ir_steps=args.ir_steps,
-                      store_factors_max_k=store_max_k)
+                      store_factors_max_k=store_max_k, tuning=fixed_tuning)
     b.upload(host)
     gt_host = np.zeros(int(b.c_off[-1]), np.float32)
     for p, pr in enumerate(wl.pairs):
@@ -492,7 +493,7 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
     # tile shapes / launch plans picked by the project's autotuner on this batch (outside
     # every timed region)
     tune = None
-    if full and not args.no_autotune:
+    if full and not args.no_autotune and not fixed_tuning:
         from paper_2604_10377_gb300 import autotune as at
         res = at.autotune(b, step)
         tune = {"tuning": res["tuning"], "tuned_ms": res["ms"], "default_ms": res["baseline_ms"],
@@ -627,15 +628,17 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
                 r["tensor"] = {"achieved_tflops": tflops, "peak_tflops": measured[mma], "peak": mma,
                                "frac": tflops / measured[mma]}
             return r
-        if kind == "adj_gemm" and measured:
-            # the library's built-in choice (fmap_options.adjoint_kernel = 0): tensor cores when
-            # dA_x has at least two 128-column tiles per SM, else FP32 FMA tiles
+        if kind == "adj_gemm":
+            # tensor cores when the knob says so, or by the library's built-in choice
+            # (fmap_options.adjoint_kernel = 0): at least two 128-column dA_x tiles per SM
             ach = work[kind]["flops"] / (per_step_ms / 1000.0) / 1e12
-            if work[kind]["da_tiles"] >= 2 * SM_COUNT:
-                pk = measured["tf32_mma"] / 3.0
+            ak = fixed_tuning.get("adjoint_kernel", 0)
+            if ak == 1 or (ak == 0 and work[kind]["da_tiles"] >= 2 * SM_COUNT):
+                pk = measured["tf32_mma"] / 3.0 if measured else None
                 return {"kernel": kind, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                        "frac": ach / pk, "traffic": None,
-                        "peak_source": "measured TF32 MMA peak / 3 (three TF32 passes per FP32-class product)"}
+                        "frac": ach / pk if pk else None, "traffic": None,
+                        "peak_source": "measured TF32 MMA peak / 3 (three TF32 passes per FP32-class product)"
+                        if pk else "TF32 peak not measured (--no-peaks)"}
             return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak_tflops, "traffic": None, "peak_source": fp32_peak_source}
         flops = work.get(kind, {}).get("flops")
@@ -708,6 +711,7 @@ def bench_workload(wid, args, dev, peaks, measured, uuid, rank, world, full):
                    "inputs smaller than L2 (%.3f GB per step): steps replay from a warm L2"
                    % (work["project"]["bytes"] / 1e9)},
         "fwd_only": {"value": rate_fwd, "unit": "pairs/s", "ms_per_step": ms_fwd},
+        "tuning": fixed_tuning or None,
         "launch": "eager" if args.no_graph else "one CUDA graph per step",
         "eager": {"value": rate_eager, "unit": "pairs/s", "ms_per_step": ms_eager},
         "roofline": roofline,
@@ -1014,6 +1018,8 @@ def main():
                     help="spatial gradient features (DiffusionNet variants A and B) instead of the step")
     ap.add_argument("--copy-streams", type=int, default=4, help="side streams of the end-to-end host-to-device copies")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's built-in tiling choices")
+    ap.add_argument("--tuning", default="",
+                    help='fixed tuning knobs as JSON (fmap_options names, e.g. {"adjoint_kernel": 1}); no autotuner')
     ap.add_argument("--no-peaks", action="store_true", help="derive the FP32 peak instead of measuring it")
     ap.add_argument("--no-sub-workloads", action="store_true",
                     help="time only the main workload (not the other four as sub-results)")
