@@ -21,6 +21,10 @@ arXiv 2604.10377, Sec. 3.1 "Batched Functional Map Solver"):
   k_X coefficients of shape X to the k_Y of shape Y (k_Y x k_X); the paper's shapes share
   k, and with k_X != k_Y the same equations give k_Y row systems of size k_X.
 * Eq. 8-9: the rows are independent, so all of them are solved as one batch.
+* The paper's lambda is one scalar. A weight per row of C (lambda_i, the regulariser
+  sum_i lambda_i sum_j D_ij C_ij^2) keeps every row system separate: row i solves
+  (A A^T + lambda_i diag(D_i)) c_i = (B A^T)_i; a scalar lambda is the case of equal
+  weights.
 
 The solve uses a Cholesky factorisation written out below (the row systems are
 symmetric positive definite when A A^T or every lambda D_ij is positive). If a
@@ -28,7 +32,8 @@ pivot is not positive the oracle raises ``NotSPD``.
 
 The backward pass (not in the paper) is the adjoint of Eq. 5 derived by hand:
 gamma_i = S_i^{-1} dL/dc_i, dB = Gamma A, dA = Gamma^T B - (Gamma^T C + C^T Gamma) A,
-dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C), dF = M Phi dA.
+dD = -lambda Gamma o C, dlambda = -sum(D o Gamma o C), dF = M Phi dA (with row weights,
+dD_ij = -lambda_i Gamma_ij C_ij and dlambda_i = -sum_j D_ij Gamma_ij C_ij).
 
 Spatial gradient features (Sec. "Learned Scaling and Rotation in DiffusionNet"): the
 complex per-vertex gradients z = G X of features X under a sparse complex gradient
@@ -151,10 +156,22 @@ def cholesky_solve(l, rhs):
 # --------------------------------------------------------------------------
 # Eq. 4-9 — the row-wise (batched) regularised solve
 # --------------------------------------------------------------------------
+def _row_weights(lam, ky):
+    """lambda as a column of k_Y row weights: a scalar (the paper's single weight) or one
+    weight per row of C (the regulariser sum_i lambda_i sum_j D_ij C_ij^2)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    if lam.ndim == 0:
+        return lam
+    if lam.shape != (ky,):
+        raise ValueError("per-row lambda needs one weight per row of C")
+    return lam.reshape((ky, 1))
+
+
 def row_systems(a, d_mask, lam):
-    """S_i = A A^T + lambda diag(D_i) for every row i of C, stacked as (k_Y, k_X, k_X)
-    (Eq. 5, Eq. 8). A is k_X x d; D is k_Y x k_X, one row per row of C, so a map between
-    bases of different sizes (C of k_Y x k_X) has k_Y systems of size k_X."""
+    """S_i = A A^T + lambda_i diag(D_i) for every row i of C, stacked as (k_Y, k_X, k_X)
+    (Eq. 5, Eq. 8; lambda_i = lambda for the paper's single weight). A is k_X x d; D is
+    k_Y x k_X, one row per row of C, so a map between bases of different sizes (C of
+    k_Y x k_X) has k_Y systems of size k_X."""
     a = np.asarray(a, dtype=np.float64)
     d_mask = np.asarray(d_mask, dtype=np.float64)
     g = a @ a.T
@@ -162,7 +179,7 @@ def row_systems(a, d_mask, lam):
     ky = d_mask.shape[0]
     s = np.broadcast_to(g, (ky, kx, kx)).copy()
     idx = np.arange(kx)
-    s[:, idx, idx] += lam * d_mask
+    s[:, idx, idx] += _row_weights(lam, ky) * d_mask
     return s
 
 
@@ -178,7 +195,9 @@ def solve(a, b, d_mask, lam, return_factors=False):
 
 
 def solve_backward(a, b, c, d_mask, lam, d_c, factors=None):
-    """Adjoint of the row-wise solve. Returns dict(gamma, dA, dB, dD, dlam)."""
+    """Adjoint of the row-wise solve. Returns dict(gamma, dA, dB, dD, dlam); with one
+    lambda per row of C, dD = -lambda_i Gamma_ij C_ij and dlam is the vector of
+    dL/dlambda_i = -sum_j D_ij Gamma_ij C_ij."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
@@ -189,8 +208,12 @@ def solve_backward(a, b, c, d_mask, lam, d_c, factors=None):
     w = gamma.T @ c + c.T @ gamma
     d_a = gamma.T @ b - w @ a
     d_b = gamma @ a
-    d_d = -lam * gamma * c
-    d_lam = float(-np.sum(d_mask * gamma * c))
+    wts = _row_weights(lam, c.shape[0])
+    d_d = -wts * gamma * c
+    if np.ndim(wts) == 0:
+        d_lam = float(-np.sum(d_mask * gamma * c))
+    else:
+        d_lam = -np.sum(d_mask * gamma * c, axis=1)
     return dict(gamma=gamma, dA=d_a, dB=d_b, dD=d_d, dlam=d_lam)
 
 
@@ -215,8 +238,14 @@ def pair_mask(shape_x, shape_y, explicit_mask=None):
     return mask_from_evals(shape_x["evals"], shape_y["evals"])
 
 
+def pair_lambda(p):
+    """The pair's weight: its per-row vector when given (lam_rows), else the scalar lam."""
+    return p["lam_rows"] if p.get("lam_rows") is not None else p["lam"]
+
+
 def forward_batch(shapes, pairs):
-    """shapes: list of dict(phi, mass, feat, evals); pairs: list of dict(x, y, lam, mask).
+    """shapes: list of dict(phi, mass, feat, evals); pairs: list of dict(x, y, lam, mask)
+    (optionally lam_rows: one weight per row of C, used instead of lam).
 
     Returns dict(A=[per shape], C=[per pair])."""
     a_list = [project(s["phi"], s["mass"], s["feat"]) for s in shapes]
@@ -224,7 +253,7 @@ def forward_batch(shapes, pairs):
     for p in pairs:
         sx, sy = shapes[p["x"]], shapes[p["y"]]
         dm = pair_mask(sx, sy, p.get("mask"))
-        c_list.append(solve(a_list[p["x"]], a_list[p["y"]], dm, p["lam"]))
+        c_list.append(solve(a_list[p["x"]], a_list[p["y"]], dm, pair_lambda(p)))
     return dict(A=a_list, C=c_list)
 
 
@@ -235,7 +264,7 @@ def backward_batch(shapes, pairs, fwd, d_c_list):
     for p, dc in zip(pairs, d_c_list):
         sx, sy = shapes[p["x"]], shapes[p["y"]]
         dm = pair_mask(sx, sy, p.get("mask"))
-        g = solve_backward(fwd["A"][p["x"]], fwd["A"][p["y"]], fwd["C"][len(extra)], dm, p["lam"], dc)
+        g = solve_backward(fwd["A"][p["x"]], fwd["A"][p["y"]], fwd["C"][len(extra)], dm, pair_lambda(p), dc)
         d_a[p["x"]] += g["dA"]
         d_a[p["y"]] += g["dB"]
         extra.append(g)

@@ -356,6 +356,69 @@ def test_mask_and_lambda_gradients():
         assert abs(fd - g["dD"][i, j]) < 1e-6 * max(1, abs(fd))
 
 
+@pytest.mark.parametrize("kx,ky,d", [(3, 3, 5), (2, 5, 3), (5, 2, 7), (4, 6, 6)])
+def test_row_weights_vectorised_least_squares(kx, ky, d):
+    """A weight per row of C (lambda_i): the Kronecker form of Eq. 2 with penalty rows
+    sqrt(lambda_i D_ij), solved by LAPACK lstsq, equals the row systems with lambda_i."""
+    a, b, ex, ey, _ = _rand_rect(500 + kx * 10 + ky, kx, ky, d)
+    lam = np.random.default_rng(kx + 7 * ky).uniform(0.01, 3.0, ky)
+    dm = orc.mask_from_evals(ex, ey)
+    top = np.kron(a.T, np.eye(ky))
+    pen = np.diag(np.sqrt((lam[:, None] * dm).flatten(order="F")))
+    rhs = np.concatenate([b.flatten(order="F"), np.zeros(ky * kx)])
+    vec_c, *_ = np.linalg.lstsq(np.vstack([top, pen]), rhs, rcond=None)
+    c_ref = vec_c.reshape((ky, kx), order="F")
+    np.testing.assert_allclose(orc.solve(a, b, dm, lam), c_ref, rtol=1e-9, atol=1e-11)
+
+
+def test_row_weights_reduce_to_the_scalar_and_to_a_scaled_mask():
+    """Equal row weights give the scalar-lambda solve and gradients (dlambda summed over
+    rows); row weights lambda_i equal lambda = 1 with the mask rows scaled by lambda_i."""
+    kx, ky, d = 5, 4, 8
+    a, b, ex, ey, lam = _rand_rect(91, kx, ky, d)
+    dm = orc.mask_from_evals(ex, ey)
+    gt = np.random.default_rng(2).standard_normal((ky, kx))
+    c0 = orc.solve(a, b, dm, lam)
+    c1 = orc.solve(a, b, dm, np.full(ky, lam))
+    np.testing.assert_allclose(c1, c0, rtol=1e-12, atol=1e-14)
+    _, dc = orc.loss_orth_gt(c0, gt)
+    g0 = orc.solve_backward(a, b, c0, dm, lam, dc)
+    g1 = orc.solve_backward(a, b, c1, dm, np.full(ky, lam), dc)
+    np.testing.assert_allclose(g1["dD"], g0["dD"], rtol=1e-12, atol=1e-14)
+    assert abs(float(np.sum(g1["dlam"])) - g0["dlam"]) <= 1e-12 * max(1.0, abs(g0["dlam"]))
+    w = np.random.default_rng(3).uniform(0.1, 2.0, ky)
+    c2 = orc.solve(a, b, dm, w)
+    c3 = orc.solve(a, b, w[:, None] * dm, 1.0)
+    np.testing.assert_allclose(c2, c3, rtol=1e-12, atol=1e-14)
+
+
+def test_row_weight_gradients_fd():
+    """dL/dlambda_i and dL/dD_ij with a weight per row of C against central differences of
+    the training loss through the solve."""
+    kx, ky, d = 5, 6, 9
+    a, b, ex, ey, _ = _rand_rect(123, kx, ky, d)
+    lam = np.random.default_rng(5).uniform(0.05, 1.5, ky)
+    dm = orc.mask_from_evals(ex, ey)
+    gt = np.random.default_rng(6).standard_normal((ky, kx))
+
+    def loss(dmask, lm):
+        return orc.loss_orth_gt(orc.solve(a, b, dmask, lm), gt)[0]
+
+    c = orc.solve(a, b, dm, lam)
+    _, dc = orc.loss_orth_gt(c, gt)
+    g = orc.solve_backward(a, b, c, dm, lam, dc)
+    assert np.shape(g["dlam"]) == (ky,)
+    h = 1e-5
+    for i in range(ky):
+        e = np.zeros(ky); e[i] = h
+        fd = (loss(dm, lam + e) - loss(dm, lam - e)) / (2 * h)
+        assert abs(fd - g["dlam"][i]) < 1e-6 * max(1, abs(fd)), (i, fd, g["dlam"][i])
+    for (i, j) in [(0, 0), (2, 4), (5, 1)]:
+        e = np.zeros_like(dm); e[i, j] = h
+        fd = (loss(dm + e, lam) - loss(dm - e, lam)) / (2 * h)
+        assert abs(fd - g["dD"][i, j]) < 1e-6 * max(1, abs(fd)), (i, j)
+
+
 def test_loss_gradient_fd():
     rng = np.random.default_rng(8)
     c = rng.standard_normal((5, 5)); gt = rng.standard_normal((5, 5))
