@@ -129,6 +129,12 @@ typedef struct fmap_pair_desc {
     float lambda;          /* regularisation weight, >= 0 */
     const float* mask;     /* device k_y x k_x FP32 mask D (row i = target basis index), or
                               NULL: D_ij = (evals_y[i] - evals_x[j])^2 */
+    const float* lambda_rows;  /* device, k_y FP32 weights >= 0, or NULL: row i of C then solves
+                              (G + lambda_rows[i] diag(D_i)) c_i = R_i in place of lambda (the
+                              regulariser sum_i lambda_i sum_j D_ij C_ij^2); read by the row solves
+                              of fmap_solve and fmap_solve_backward, not checked for sign */
+    float* d_lambda_rows;  /* device, k_y FP32, or NULL: with lambda_rows, fmap_solve_backward writes
+                              dL/dlambda_i = -sum_j D_ij Gamma_ij C_ij here */
 } fmap_pair_desc;
 
 /* Sizes of a batch's buffers. Offsets: A of shape s starts at float a_offset(s) of
@@ -203,8 +209,11 @@ FMAP_API int32_t fmap_solve(fmap_batch* batch, const float* a, float* c_out, voi
  *   gamma_i = S_i^{-1} G_i                    (S_i the row system of Eq. 5)
  *   dL/dA_y += Gamma A_x
  *   dL/dA_x += Gamma^T A_y - (Gamma^T C + C^T Gamma) A_x
- *   dL/dD    = -lambda Gamma o C              (d_mask, optional, c_offsets layout)
- *   dL/dlambda = -sum(D o Gamma o C)         (d_lambda[n_pairs], optional)
+ *   dL/dD    = -lambda Gamma o C              (d_mask, optional, c_offsets layout; with row
+ *                                              weights row i is scaled by lambda_rows[i])
+ *   dL/dlambda = -sum(D o Gamma o C)         (d_lambda[n_pairs], optional; with row weights
+ *                                              the sum of the per-row gradients, which go to
+ *                                              the pair's d_lambda_rows)
  *   dL/dF_s  = diag(M_s) Phi_s dL/dA_s        written to shapes[s].dfeat when non-NULL
  * Contributions of a shape used by several pairs add up (fixed order).
  *   d_c, a, c  device, as in fmap_solve (c = its output)

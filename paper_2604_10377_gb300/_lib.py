@@ -47,7 +47,8 @@ class ShapeDesc(ctypes.Structure):
 
 
 class PairDesc(ctypes.Structure):
-    _fields_ = [("shape_x", c_int32), ("shape_y", c_int32), ("lam", c_float), ("mask", c_void_p)]
+    _fields_ = [("shape_x", c_int32), ("shape_y", c_int32), ("lam", c_float), ("mask", c_void_p),
+                ("lambda_rows", c_void_p), ("d_lambda_rows", c_void_p)]
 
 
 class Sizes(ctypes.Structure):

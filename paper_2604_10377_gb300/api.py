@@ -94,7 +94,7 @@ class FmapBatch:
     def __init__(self, layout: BatchLayout, pairs, device="cuda:0", precision: str = "fp32",
                  with_grad: bool = True, masks=None, ir_steps: int = 1, hi_gram_min_k: int = 200,
                  store_factors_max_k: int = 304, adjoint_ir_steps: int = 0, tuning: Optional[dict] = None,
-                 grad_f32_copy: bool = False):
+                 grad_f32_copy: bool = False, lambda_rows=None):
         self.layout = layout
         self.device = torch.device(device)
         self.precision = precision
@@ -121,6 +121,26 @@ class FmapBatch:
                     host[self.c_off_host[p]:self.c_off_host[p + 1]] = np.asarray(m, np.float32).reshape(-1)
             self.mask = torch.from_numpy(host).to(dev)
         self._masks_present = [m is not None for m in masks] if masks is not None else [False] * len(self.pairs)
+        # optional weight per row of C (k_Y floats per pair, in place of lam) and, with
+        # gradients, dL/dlambda_i per row; each pair's segment starts on a 16-byte boundary
+        self.lam_rows = self.dlam_rows = None
+        self._lr_off = None
+        if lambda_rows is not None and any(v is not None for v in lambda_rows):
+            offs, cur = [], 0
+            for p, v in enumerate(lambda_rows):
+                offs.append(cur if v is not None else -1)
+                if v is not None:
+                    if np.shape(v) != (self.kys[p],):
+                        raise ValueError(f"pair {p}: lambda_rows needs {self.kys[p]} weights (one per row of C)")
+                    cur += (self.kys[p] + 3) // 4 * 4
+            host = np.zeros(max(cur, 4), np.float32)
+            for p, v in enumerate(lambda_rows):
+                if v is not None:
+                    host[offs[p]:offs[p] + self.kys[p]] = np.asarray(v, np.float32)
+            self._lr_off = offs
+            self.lam_rows = torch.from_numpy(host).to(dev)
+            if with_grad:
+                self.dlam_rows = torch.zeros_like(self.lam_rows)
 
         L = _lib.lib()
         opt = _lib.default_options()
@@ -158,6 +178,9 @@ class FmapBatch:
         for p, (x, y, lam) in enumerate(self.pairs):
             pd[p].shape_x, pd[p].shape_y, pd[p].lam = x, y, lam
             pd[p].mask = (self.mask.data_ptr() + 4 * int(self.c_off_host[p])) if self._masks_present[p] else None
+            lr = self._lr_off[p] if self._lr_off is not None else -1
+            pd[p].lambda_rows = (self.lam_rows.data_ptr() + 4 * lr) if lr >= 0 else None
+            pd[p].d_lambda_rows = (self.dlam_rows.data_ptr() + 4 * lr) if (lr >= 0 and self.dlam_rows is not None) else None
         return sd, pd
 
     def _apply_tuning(self, tuning: dict):
@@ -271,6 +294,12 @@ class FmapBatch:
                 i += 1
         for st in self._copy_streams:
             cur.wait_stream(st)
+
+    def dlam_rows_view(self, p: int) -> Optional[torch.Tensor]:
+        """dL/dlambda_i of pair p's row weights (written by solve_backward), or None."""
+        if self.dlam_rows is None or self._lr_off[p] < 0:
+            return None
+        return self.dlam_rows[self._lr_off[p]:self._lr_off[p] + self.kys[p]]
 
     def a_view(self, flat: torch.Tensor, s: int) -> torch.Tensor:
         k, d = self.layout.ks[s], self.layout.ds[s]
@@ -486,6 +515,9 @@ def batch_from_workload(wl, device="cuda:0", with_grad=True, **kw) -> FmapBatch:
     """Allocate a batch for a synth.Workload and upload its inputs."""
     lay = BatchLayout([s.n for s in wl.shapes], [s.k for s in wl.shapes], [s.d for s in wl.shapes], wl.feat_dtype)
     masks = [p.mask for p in wl.pairs]
+    lam_rows = [getattr(p, "lam_rows", None) for p in wl.pairs]
+    if "lambda_rows" not in kw and any(v is not None for v in lam_rows):
+        kw["lambda_rows"] = lam_rows
     b = FmapBatch(lay, [(p.x, p.y, p.lam) for p in wl.pairs], device=device, precision=wl.feat_dtype,
                   with_grad=with_grad, masks=masks, **kw)
     b.upload(lay.pack_host(wl.shapes))

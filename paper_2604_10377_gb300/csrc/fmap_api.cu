@@ -101,6 +101,7 @@ struct Plan {
   uint32_t bw_b_bytes = 0;
   // tensor-core adjoint GEMMs (built when the batch is created: the SM count sets the tiles)
   AdjTcPlan adj;
+  bool row_grads = false;   // some pair has per-row lambda gradients to write
   fmap_sizes sizes{};
 };
 
@@ -182,6 +183,11 @@ int32_t make_plan(const fmap_options& opt, const fmap_shape_desc* shapes, int32_
     std::memset(&pd, 0, sizeof(pd));
     pd.x = q.shape_x; pd.y = q.shape_y; pd.k = sx.k; pd.d = sx.d;   // C is sy.k x sx.k
     pd.lam = q.lambda; pd.mask = q.mask;
+    if (q.lambda_rows && !aligned(q.lambda_rows, 4)) return FMAP_ERR_UNSUPPORTED;
+    if (q.d_lambda_rows && !aligned(q.d_lambda_rows, 4)) return FMAP_ERR_UNSUPPORTED;
+    pd.lam_rows = q.lambda_rows;
+    pd.dlam_rows = q.lambda_rows ? q.d_lambda_rows : nullptr;
+    if (pd.dlam_rows) P.row_grads = true;
     pd.hi_gram = sx.k >= opt.hi_gram_min_k ? 1 : 0;
     pd.c_off = P.c_off[p];
     P.c_off[p + 1] = P.c_off[p] + (int64_t)sy.k * sx.k;
@@ -1026,7 +1032,8 @@ int32_t adjoint_impl(fmap_batch* b, const float* d_c, const float* a, const floa
     TimedScope ts(b, FMAP_KIND_ADJ_GEMM, st);
     const int ak = b->plan.opt.adjoint_kernel;
     const bool simt = ak == 2 || (ak == 0 && !b->plan.adj.fills_sms);
-    e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, w, simt, st);
+    e = launch_adjoint_gemms(b->dev, b->plan.max_k, b->plan.max_d, a, c, d_mask, d_lambda, b->plan.row_grads, w,
+                             simt, st);
     if (e == cudaSuccess && !simt) e = launch_adjoint_tc(b->dev, b->d_adj_items, b->plan.adj, a, c, w, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint gemms");

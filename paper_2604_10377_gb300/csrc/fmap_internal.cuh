@@ -70,6 +70,8 @@ struct PairDev {
   float lam;
   int32_t hi_gram;     // 1: Gram matrix accumulated in FP64
   const float* mask;   // k x k or nullptr (use eigenvalues)
+  const float* lam_rows;   // k_Y weights, one per row system (in place of lam), or nullptr
+  float* dlam_rows;        // k_Y outputs dL/dlambda_i (with lam_rows), or nullptr
   int64_t c_off;       // float offset of C_p / dC_p in the flat k x k buffers
   int64_t g_off;       // float offset (workspace) of G = A_x A_x^T  (k x k, row stride gram_ld(k))
   int64_t r_off;       // float offset (workspace) of R = A_y A_x^T  (k x k)
@@ -192,10 +194,12 @@ enum SolveMode { kSolveForward = 0, kSolveAdjoint = 1 };
 cudaError_t launch_solve(const BatchDev& b, const SolveGroup& g, const int2* systems, int mode,
                          const float* rhs_flat, float* out_flat, float* saved_rw, int32_t* status,
                          float* ws, cudaStream_t st);
-// The mask and lambda gradients (when d_mask / d_lambda are given) and, with simt, W and the
-// dA contributions on the CUDA cores (FP32 FMA tiles)
+// The mask and lambda gradients (when d_mask / d_lambda are given, or a pair has per-row
+// lambda outputs: row_grads) and, with simt, W and the dA contributions on the CUDA cores
+// (FP32 FMA tiles)
 cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
-                                 float* d_mask, float* d_lambda, float* ws, bool simt, cudaStream_t st);
+                                 float* d_mask, float* d_lambda, bool row_grads, float* ws, bool simt,
+                                 cudaStream_t st);
 
 // One CTA of the tensor-core adjoint GEMMs: output rows r0 .. r0+127 and columns f0 .. f0+NT-1
 // of W (kind 2), dA_y (kind 1) or dA_x (kind 0) of one pair.

@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(NT, (NT > 256 ? 1 : (NT >= 256 ? 2 : (NT >= 12
   float* out = (mode == kSolveForward) ? out_flat + pd.c_off + (int64_t)i * k : ws + pd.gam_off + (int64_t)i * k;
   const int fsz = factor_floats(Q);
   float* fac = (saved != nullptr && pd.fac_off >= 0) ? saved + pd.fac_off + (int64_t)i * fsz : nullptr;
-  const float lam = pd.lam;
+  const float lam = pd.lam_rows ? pd.lam_rows[i] : pd.lam;   // row weight of this system
   const int n_ir = mode == kSolveForward ? b.ir_steps : b.ir_steps_adj;
   // small FP32-Gram systems keep G in shared memory for the refinement residual
   const bool use_gs = gs_ok != 0 && Ghl == nullptr && n_ir > 0;

@@ -93,21 +93,39 @@ __global__ void __launch_bounds__(256, 3) adjoint_w_kernel(BatchDev b, const flo
   }
 }
 
-// The mask gradient dD = -lambda Gamma o C (when d_mask is given) and
-// dlambda_p = -sum_ij D_ij Gamma_ij C_ij (when d_lambda is given), over the k_Y x k_X
-// entries; fixed-order block reduction (one block per pair).
+// The mask gradient dD = -lambda_i Gamma o C (when d_mask is given; lambda_i = lambda
+// without row weights), dlambda_p = -sum_ij D_ij Gamma_ij C_ij (when d_lambda is given;
+// with row weights the sum of the per-row gradients) and, for pairs with row weights and an
+// output for them, dlambda_i = -sum_j D_ij Gamma_ij C_ij (one warp per row, lanes in a fixed
+// order); over the k_Y x k_X entries, fixed-order block reductions (one block per pair).
 __global__ void __launch_bounds__(256) adjoint_dlambda_kernel(BatchDev b, const float* c_flat, float* d_mask,
                                                               float* d_lambda, const float* ws) {
   __shared__ float red[256];
   const int p = blockIdx.x;
   const PairDev pd = b.pairs[p];
-  const int k = pd.k, n = b.shapes[pd.y].k * pd.k;   // the ky x k entries
+  const int k = pd.k, ky = b.shapes[pd.y].k, n = ky * pd.k;   // the ky x k entries
   const float* gam = ws + pd.gam_off;
   const float* cm = c_flat + pd.c_off;
   const float* evx = b.shapes[pd.x].evals;
   const float* evy = b.shapes[pd.y].evals;
   if (d_mask)
-    for (int e = threadIdx.x; e < n; e += 256) d_mask[pd.c_off + e] = -pd.lam * gam[e] * cm[e];
+    for (int e = threadIdx.x; e < n; e += 256) {
+      const float lam = pd.lam_rows ? pd.lam_rows[e / k] : pd.lam;
+      d_mask[pd.c_off + e] = -lam * gam[e] * cm[e];
+    }
+  if (pd.dlam_rows) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < ky; i += 8) {
+      float acc = 0.f;
+      for (int j = lane; j < k; j += 32) {
+        const int e = i * k + j;
+        acc = fmaf(mask_entry(pd, evx, evy, i, j) * gam[e], cm[e], acc);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) pd.dlam_rows[i] = -acc;
+    }
+  }
   if (!d_lambda) return;
   float acc = 0.f;
   for (int e = threadIdx.x; e < n; e += 256) {
@@ -422,7 +440,8 @@ __global__ void status_clear_kernel(int32_t* status, int n) {
 }  // namespace
 
 cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const float* a, const float* c,
-                                 float* d_mask, float* d_lambda, float* ws, bool simt, cudaStream_t st) {
+                                 float* d_mask, float* d_lambda, bool row_grads, float* ws, bool simt,
+                                 cudaStream_t st) {
   if (b.n_pairs <= 0) return cudaSuccess;
   const int ntk = (max_k + kTile - 1) / kTile, ntd = (max_d + kTile - 1) / kTile;
   cudaError_t e;
@@ -430,7 +449,7 @@ cudaError_t launch_adjoint_gemms(const BatchDev& b, int max_k, int max_d, const 
     adjoint_w_kernel<<<dim3(ntk * ntk, 1, b.n_pairs), 256, 0, st>>>(b, c, ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (d_lambda || d_mask) {
+  if (d_lambda || d_mask || row_grads) {
     adjoint_dlambda_kernel<<<b.n_pairs, 256, 0, st>>>(b, c, d_mask, d_lambda, ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -82,6 +82,7 @@ class Pair:
     lam: float              # stored as FP32 on both sides
     mask: Optional[np.ndarray] = None   # (k, k) float32 or None: use eigenvalues
     c_gt: Optional[np.ndarray] = None   # (k, k) float32 target map for the training loss
+    lam_rows: Optional[np.ndarray] = None   # (k_Y,) float32 weight per row of C, or None: lam
 
 
 @dataclasses.dataclass

@@ -8,7 +8,9 @@ def oracle_inputs(wl: "synth.Workload"):
     shapes = [dict(phi=s.phi.astype(np.float64), mass=s.mass.astype(np.float64),
                    feat=s.feat_f64(), evals=s.evals.astype(np.float64)) for s in wl.shapes]
     pairs = [dict(x=p.x, y=p.y, lam=float(np.float32(p.lam)),
-                  mask=None if p.mask is None else p.mask.astype(np.float64)) for p in wl.pairs]
+                  mask=None if p.mask is None else p.mask.astype(np.float64),
+                  lam_rows=None if getattr(p, "lam_rows", None) is None
+                  else np.asarray(p.lam_rows, np.float32).astype(np.float64)) for p in wl.pairs]
     return shapes, pairs
 
 

@@ -107,6 +107,23 @@ def test_plan_accepts_k_up_to_304(lib, precision):
     assert fac <= sz.saved_bytes < fac + 3 * 256
 
 
+def test_row_weight_pointers_must_be_aligned(lib):
+    """Per-row lambda weights and their gradient outputs are FP32 device arrays: a pointer
+    that is not 4-byte aligned is refused when the batch is planned (no device needed)."""
+    from paper_2604_10377_gb300 import _lib
+    specs = [dict(n=500, k=20, d=64), dict(n=600, k=30, d=64)]
+    for field in ("lambda_rows", "d_lambda_rows"):
+        sd, pd = _descs(specs, [(0, 1, 1e-3)])
+        pd[0].lambda_rows = 0x50000
+        setattr(pd[0], field, 0x50002)
+        sz = _lib.Sizes()
+        assert lib.fmap_plan_sizes(None, sd, 2, pd, 1, ctypes.byref(sz)) == _lib.FMAP_ERR_UNSUPPORTED
+    sd, pd = _descs(specs, [(0, 1, 1e-3)])
+    pd[0].lambda_rows, pd[0].d_lambda_rows = 0x50000, 0x60000
+    sz = _lib.Sizes()
+    assert lib.fmap_plan_sizes(None, sd, 2, pd, 1, ctypes.byref(sz)) == 0
+
+
 def test_plan_sizes_empty(lib):
     rc, sz = _plan(lib, [dict(n=10, k=4, d=16)], [])
     assert rc == 0 and sz.c_floats == 0 and sz.n_pairs == 0

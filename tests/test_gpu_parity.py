@@ -223,6 +223,8 @@ def _gpu_backward(wl, use_saved=True, **kw):
         dlam=d_lam.cpu().numpy(),
         C=[b.c_view(c, p).cpu().numpy() for p in range(len(wl.pairs))],
         status=b.status[:len(wl.pairs)].cpu().numpy(),
+        dlam_rows=[None if b.dlam_rows_view(p) is None else b.dlam_rows_view(p).cpu().numpy()
+                   for p in range(len(wl.pairs))],
     )
     if b.dfeat32 is not None:
         out["dF32"] = [b.layout.feat_view(b.dfeat32, s).cpu().numpy() for s in range(len(wl.shapes))]
@@ -270,6 +272,45 @@ def test_rectangular_maps(feat_dtype, use_saved):
         assert abs(out["loss"][p] - losses[p]) <= tol * max(1.0, abs(losses[p]))
         assert rel_fro(out["dD"][p], g["pair"][p]["dD"]) <= gtol
         assert abs(out["dlam"][p] - g["pair"][p]["dlam"]) <= gtol * max(1.0, abs(g["pair"][p]["dlam"]))
+    for s_ in range(len(wl.shapes)):
+        assert rel_fro(out["dA"][s_], g["dA"][s_]) <= gtol
+        assert rel_fro(out["dF"][s_], g["dF"][s_]) <= gtol
+
+
+@pytest.mark.parametrize("feat_dtype,use_saved", [("fp32", True), ("fp32", False), ("bf16", True)])
+def test_row_weights(feat_dtype, use_saved):
+    """A weight per row of C (lambda_rows: row i solves (G + lambda_i diag(D_i)) c_i = R_i):
+    square and rectangular pairs with row weights beside pairs with a scalar lambda, one
+    with an explicit mask, k across the 64 / 128 / 256-thread row-solve classes; C, dA, dF,
+    dD, the per-pair dlambda (the sum over rows) and dL/dlambda_i per row against the
+    oracle."""
+    rng = np.random.default_rng(47)
+    ks = [40, 40, 90, 60, 150, 150, 20, 30]
+    shapes = [_shape(rng, 900 + 31 * i, k, 320, feat_dtype) for i, k in enumerate(ks)]
+    wr = np.random.default_rng(9)
+    pairs = [synth.Pair(x=0, y=1, lam=1e-2, lam_rows=wr.uniform(1e-3, 5e-2, ks[1]).astype(np.float32)),
+             synth.Pair(x=2, y=3, lam=1e-3, lam_rows=wr.uniform(1e-4, 1e-2, ks[3]).astype(np.float32)),
+             synth.Pair(x=4, y=5, lam=1e-2),
+             synth.Pair(x=4, y=5, lam=1e-2, lam_rows=wr.uniform(1e-3, 3e-2, ks[5]).astype(np.float32)),
+             synth.Pair(x=6, y=7, lam=1e-2, lam_rows=wr.uniform(1e-3, 3e-2, ks[7]).astype(np.float32))]
+    pairs[4].mask = wr.uniform(0.0, 40.0, (ks[7], ks[6])).astype(np.float32)
+    for p in pairs:
+        p.c_gt = (wr.standard_normal((ks[p.y], ks[p.x])) / np.sqrt(ks[p.x])).astype(np.float32)
+    wl = synth.Workload("row_weights", shapes, pairs, feat_dtype)
+    out = _gpu_backward(wl, use_saved=use_saved)
+    shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
+    tol, gtol = TOL[feat_dtype], GTOL[feat_dtype]
+    assert np.all(out["status"] == 0)
+    for p, pr in enumerate(wl.pairs):
+        assert rel_fro(out["C"][p], fwd["C"][p]) <= tol
+        assert rel_fro(out["dD"][p], g["pair"][p]["dD"]) <= gtol
+        dl = g["pair"][p]["dlam"]
+        if pr.lam_rows is None:
+            assert out["dlam_rows"][p] is None
+            assert abs(out["dlam"][p] - dl) <= gtol * max(1.0, abs(dl))
+        else:
+            assert rel_fro(out["dlam_rows"][p], dl) <= gtol
+            assert abs(out["dlam"][p] - np.sum(dl)) <= gtol * max(1.0, np.sum(np.abs(dl)))
     for s_ in range(len(wl.shapes)):
         assert rel_fro(out["dA"][s_], g["dA"][s_]) <= gtol
         assert rel_fro(out["dF"][s_], g["dF"][s_]) <= gtol
