@@ -234,12 +234,15 @@ FMAP_API int32_t fmap_solve_backward(fmap_batch* batch, const float* d_c, const 
  *                          buffer (the chain rule of Eq. 1), from d_a as fmap_adjoint wrote it
  * Both use the batch workspace (>= sizes.ws_bwd_bytes): calls on one batch must be ordered
  * (fmap_project_backward after the fmap_adjoint whose d_a it reads). Together they do
- * exactly what fmap_solve_backward does, in the same arithmetic. */
+ * exactly what fmap_solve_backward does, in the same arithmetic. status (device
+ * int32[n_pairs], or NULL for fmap_project_backward) is not cleared by
+ * fmap_project_backward: a bounded wait that gave up sets FMAP_ERR_TIMEOUT in every pair
+ * that holds no error yet, as fmap_solve_backward and fmap_adjoint do at their end. */
 FMAP_API int32_t fmap_adjoint(fmap_batch* batch, const float* d_c, const float* a, const float* c,
                               const void* saved, float* d_a, float* d_mask, float* d_lambda,
                               int32_t* status, void* ws, size_t ws_bytes, void* stream);
-FMAP_API int32_t fmap_project_backward(fmap_batch* batch, const float* d_a, void* ws, size_t ws_bytes,
-                                       void* stream);
+FMAP_API int32_t fmap_project_backward(fmap_batch* batch, const float* d_a, int32_t* status, void* ws,
+                                       size_t ws_bytes, void* stream);
 
 /* The training loss of the differentiable workloads, per pair:
  *   L_p = ||C C^T - I||_F^2 + ||C - C_gt||_F^2,  dL/dC = 4 (C C^T - I) C + 2 (C - C_gt).

@@ -88,7 +88,7 @@ _PROTOS = {
                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
-    "fmap_project_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "fmap_project_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_loss_orth": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "fmap_batch_set_timing": (c_int32, [c_void_p, c_int32]),
     "fmap_batch_read_timing": (c_int32, [c_void_p, POINTER(c_float), POINTER(c_int32), c_int32]),

@@ -353,8 +353,8 @@ class FmapBatch:
     def project_backward(self, d_a: Optional[torch.Tensor] = None):
         """The second half of solve_backward: dL/dF of every shape from dL/dA."""
         d_a = self.dA if d_a is None else d_a
-        check(_lib.lib().fmap_project_backward(self._batch, _ptr(d_a), _ptr(self.ws), self.ws.numel(),
-                                               _stream(self.device)), "fmap_project_backward")
+        check(_lib.lib().fmap_project_backward(self._batch, _ptr(d_a), _ptr(self.status), _ptr(self.ws),
+                                               self.ws.numel(), _stream(self.device)), "fmap_project_backward")
 
     def loss_orth(self, c: torch.Tensor, c_gt: torch.Tensor, loss: Optional[torch.Tensor] = None,
                   d_c: Optional[torch.Tensor] = None):

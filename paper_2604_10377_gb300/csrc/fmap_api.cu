@@ -1005,6 +1005,22 @@ namespace {
 
 // The adjoint part of the backward pass: dC -> Gamma (adjoint row solves) -> dA (and dD,
 // dlambda), written to da.
+// A bounded device wait that gave up in a kernel after the row solves (the adjoint GEMMs,
+// the backward projection) leaves FMAP_ERR_TIMEOUT in the workspace's control word; this
+// turns it into every pair's status (pairs that already hold an error keep it).
+__global__ void status_from_control_kernel(const int* ctrl, int32_t* status, int n) {
+  const int code = ctrl[0];
+  if (code == 0) return;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    atomicCAS(status + p, 0, code);
+}
+
+cudaError_t launch_status_from_control(const void* ws, int32_t* status, int n, cudaStream_t st) {
+  if (!status || n <= 0) return cudaSuccess;
+  status_from_control_kernel<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const int*>(ws), status, n);
+  return cudaGetLastError();
+}
+
 int32_t adjoint_impl(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved, float* da,
                      float* d_mask, float* d_lambda, int32_t* status, float* w, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
@@ -1097,7 +1113,14 @@ int32_t fmap_solve_backward(fmap_batch* b, const float* d_c, const float* a, con
   float* da = d_a ? d_a : w + b->plan.da_int_off;
   rc = adjoint_impl(b, d_c, a, c, saved, da, d_mask, d_lambda, status, w, st);
   if (rc) return rc;
-  return project_backward_impl(b, da, w, ws, st);
+  rc = project_backward_impl(b, da, w, ws, st);
+  if (rc) return rc;
+  cudaError_t e;
+  {
+    TimedScope ts(b, FMAP_KIND_STATUS, st);
+    e = launch_status_from_control(ws, status, b->plan.sizes.n_pairs, st);
+  }
+  return e == cudaSuccess ? FMAP_OK : cuda_fail(e, "status");
 }
 
 int32_t fmap_adjoint(fmap_batch* b, const float* d_c, const float* a, const float* c, const void* saved, float* d_a,
@@ -1109,18 +1132,34 @@ int32_t fmap_adjoint(fmap_batch* b, const float* d_c, const float* a, const floa
   if (rc) return rc;
   if (saved && !aligned(saved, 256)) return FMAP_ERR_WORKSPACE;
   DeviceGuard dg(b->ctx->device);
-  return adjoint_impl(b, d_c, a, c, saved, d_a, d_mask, d_lambda, status, static_cast<float*>(ws),
-                      static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = adjoint_impl(b, d_c, a, c, saved, d_a, d_mask, d_lambda, status, static_cast<float*>(ws), st);
+  if (rc) return rc;
+  cudaError_t e;
+  {
+    TimedScope ts(b, FMAP_KIND_STATUS, st);
+    e = launch_status_from_control(ws, status, b->plan.sizes.n_pairs, st);
+  }
+  return e == cudaSuccess ? FMAP_OK : cuda_fail(e, "status");
 }
 
-int32_t fmap_project_backward(fmap_batch* b, const float* d_a, void* ws, size_t ws_bytes, void* stream) {
+int32_t fmap_project_backward(fmap_batch* b, const float* d_a, int32_t* status, void* ws, size_t ws_bytes,
+                              void* stream) {
   if (!b) return FMAP_ERR_INVALID_ARG;
   if (b->plan.sizes.n_pairs == 0) return FMAP_OK;
   if (!d_a) return FMAP_ERR_INVALID_ARG;
   int32_t rc = check_ws(ws, ws_bytes, b->plan.sizes.ws_bwd_bytes);
   if (rc) return rc;
   DeviceGuard dg(b->ctx->device);
-  return project_backward_impl(b, d_a, static_cast<float*>(ws), ws, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = project_backward_impl(b, d_a, static_cast<float*>(ws), ws, st);
+  if (rc) return rc;
+  cudaError_t e;
+  {
+    TimedScope ts(b, FMAP_KIND_STATUS, st);
+    e = launch_status_from_control(ws, status, b->plan.sizes.n_pairs, st);
+  }
+  return e == cudaSuccess ? FMAP_OK : cuda_fail(e, "status");
 }
 
 int32_t fmap_loss_orth(fmap_batch* b, const float* c, const float* c_gt, float* loss, float* d_c, void* ws,

@@ -230,7 +230,7 @@ def test_calls_without_batch_are_rejected(lib):
     assert lib.fmap_project(None, None, None, 0, None) == 1
     assert lib.fmap_solve(None, None, None, None, None, None, 0, None) == 1
     assert lib.fmap_adjoint(None, None, None, None, None, None, None, None, None, None, 0, None) == 1
-    assert lib.fmap_project_backward(None, None, None, 0, None) == 1
+    assert lib.fmap_project_backward(None, None, None, None, 0, None) == 1
 
 
 # ------------------------------------------------------------ independence of oracle and CUDA path

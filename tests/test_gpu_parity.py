@@ -532,6 +532,33 @@ def test_adjoint_default_on_a_batch_that_fills_the_sms():
         assert rel_fro(out["dA"][s], ref["dA"][s]) <= 1e-5
 
 
+def test_timeout_after_the_row_solves_reaches_every_pair():
+    """A bounded wait that gave up after the row solves (adjoint GEMMs, backward projection)
+    leaves FMAP_ERR_TIMEOUT in the workspace's control word; the backward entry points turn
+    it into every pair's status. The failure is made on the host: the test writes the code
+    into the control word (no GPU wait runs out), and a clean control word leaves the status
+    at 0."""
+    from paper_2604_10377_gb300 import _lib, api
+    wl = synth.make_small(51, 3, (500, 1500), [20, 40, 70], 64, feat_dtype="bf16")
+    b = api.batch_from_workload(wl, with_grad=True)
+    a = b.project(); c = b.solve(a)
+    dc = torch.randn_like(c) * 1e-3
+    b.adjoint(dc, a, c)
+    b.status.zero_()
+    b.project_backward()
+    torch.cuda.synchronize()
+    assert np.all(b.status[:3].cpu().numpy() == 0)
+    b.ws[:4].view(torch.int32).fill_(_lib.FMAP_ERR_TIMEOUT)
+    b.status.zero_()
+    b.status[1] = _lib.FMAP_ERR_NOT_SPD | (2 << 8)   # an earlier error is kept
+    b.project_backward()
+    torch.cuda.synchronize()
+    st = b.status[:3].cpu().numpy()
+    assert st[0] == _lib.FMAP_ERR_TIMEOUT and st[2] == _lib.FMAP_ERR_TIMEOUT
+    assert st[1] == _lib.FMAP_ERR_NOT_SPD | (2 << 8)
+    b.ws[:256].zero_()
+
+
 def _tuning_cases():
     from paper_2604_10377_gb300.autotune import CANDIDATES
     return [(knob, v) for knob, vals in CANDIDATES.items() for v in vals if v != 0]
