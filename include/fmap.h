@@ -91,7 +91,8 @@ typedef struct fmap_options {
     int32_t solve_no_g_copy;    /* row solves of k <= 128: 0 keeps a copy of G in shared memory for the
                                    refinement residual (default), 1 reads G from L2 instead (less shared
                                    memory per block, more blocks per SM) */
-    int32_t adjoint_kernel;     /* W = Gamma^T C + C^T Gamma, dA_x = Gamma^T A_y - W A_x, dA_y = Gamma A_x:
+    int32_t adjoint_kernel;     /* W = Gamma^T C + C^T Gamma, dA_x = Gamma^T A_y - W A_x, dA_y = Gamma A_x,
+                                   and the training loss's E = C C^T - I, dL/dC = 4 E C + 2 (C - C_gt):
                                    1 tensor cores (three TF32 passes), 2 CUDA cores (FP32 FMA tiles);
                                    0 the built-in choice: tensor cores when dA_x has at least two
                                    128-column tiles per SM, else CUDA cores */

@@ -10,6 +10,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "adjoint_tc.cuh"
 #include "fmap_internal.cuh"
 
 using namespace fmap;
@@ -101,6 +102,7 @@ struct Plan {
   uint32_t bw_b_bytes = 0;
   // tensor-core adjoint GEMMs (built when the batch is created: the SM count sets the tiles)
   AdjTcPlan adj;
+  AdjTcPlan loss_tc;        // the training loss's GEMMs on the same kernel (E, then dL/dC)
   bool row_grads = false;   // some pair has per-row lambda gradients to write
   fmap_sizes sizes{};
 };
@@ -577,6 +579,7 @@ struct fmap_batch {
   const int32_t* d_bw_cta_first = nullptr;
   const TcBwdGroup* d_bw_groups = nullptr;
   const AdjItem* d_adj_items = nullptr;
+  const AdjItem* d_loss_items = nullptr;
   int sm_count = 152;
 };
 
@@ -718,6 +721,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
     P.adj.stages = ctx->opt.adjoint_stages;
     P.adj.features = ctx->opt.adjoint_features;
     adjoint_tc_plan(pk, b->sm_count, P.adj);
+    adjoint_tc_loss_plan(pk, P.loss_tc);
   }
 
   // one allocation for every table
@@ -738,7 +742,8 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   const int64_t o_bo = o_bi + bytes_of(P.bw_items.size(), sizeof(TcBwdItem));
   const int64_t o_bg = o_bo + bytes_of(P.bw_cta_first.size(), sizeof(int32_t));
   const int64_t o_ai = o_bg + bytes_of(P.bw_groups.size(), sizeof(TcBwdGroup));
-  const int64_t total = o_ai + bytes_of(P.adj.items.size(), sizeof(AdjItem)) + 256;
+  const int64_t o_li = o_ai + bytes_of(P.adj.items.size(), sizeof(AdjItem));
+  const int64_t total = o_li + bytes_of(P.loss_tc.items.size(), sizeof(AdjItem)) + 256;
   e = cudaMalloc(&b->dev_mem, (size_t)total);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(batch tables)"); }
   char* base = static_cast<char*>(b->dev_mem);
@@ -749,6 +754,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   put(o_sl, P.slot_list.data(), P.slot_list.size() * sizeof(int64_t));
   put(o_sy, P.systems.data(), P.systems.size() * sizeof(int2));
   put(o_ai, P.adj.items.data(), P.adj.items.size() * sizeof(AdjItem));
+  put(o_li, P.loss_tc.items.data(), P.loss_tc.items.size() * sizeof(AdjItem));
   if (n_shapes > 0) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) { cudaFree(b->dev_mem); delete b; return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled"); }
@@ -868,6 +874,7 @@ int32_t fmap_batch_create(fmap_ctx* ctx, const fmap_shape_desc* shapes, int32_t 
   b->d_bw_cta_first = reinterpret_cast<const int32_t*>(base + o_bo);
   b->d_bw_groups = reinterpret_cast<const TcBwdGroup*>(base + o_bg);
   b->d_adj_items = reinterpret_cast<const AdjItem*>(base + o_ai);
+  b->d_loss_items = reinterpret_cast<const AdjItem*>(base + o_li);
   *out = b;
   return FMAP_OK;
 }
@@ -1173,8 +1180,15 @@ int32_t fmap_loss_orth(fmap_batch* b, const float* c, const float* c_gt, float* 
   cudaError_t e;
   {
     TimedScope ts(b, FMAP_KIND_LOSS, static_cast<cudaStream_t>(stream));
-    e = launch_loss_orth(b->dev, b->plan.max_k, c, c_gt, loss, d_c, static_cast<float*>(ws),
-                         static_cast<float*>(ws) + b->plan.loss_part_off, static_cast<cudaStream_t>(stream));
+    // the GEMMs on the tensor cores when the adjoint's run there (both need dL/dC: its tiles
+    // also carry ||C - C_gt||^2), else the FP32 FMA tiles
+    const int ak = b->plan.opt.adjoint_kernel;
+    const bool tc = d_c && !b->plan.loss_tc.items.empty() && (ak == 1 || (ak == 0 && b->plan.adj.fills_sms));
+    float* w = static_cast<float*>(ws);
+    e = tc ? launch_loss_tc(b->dev, b->d_loss_items, b->plan.loss_tc, c, c_gt, loss, d_c, w, w + b->plan.loss_part_off,
+                            static_cast<cudaStream_t>(stream))
+           : launch_loss_orth(b->dev, b->plan.max_k, c, c_gt, loss, d_c, w, w + b->plan.loss_part_off,
+                              static_cast<cudaStream_t>(stream));
   }
   if (e != cudaSuccess) return cuda_fail(e, "loss");
   return FMAP_OK;

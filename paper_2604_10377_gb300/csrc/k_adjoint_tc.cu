@@ -3,9 +3,14 @@
 //   kind 2: W    = Gamma^T C + C^T Gamma = [Gamma^T | C^T] [C ; Gamma]      (k_X x k_X, w_off)
 //   kind 1: dA_y = Gamma A_x                                                 (k_Y x d, sy_off)
 //   kind 0: dA_x = Gamma^T A_y - W A_x = [Gamma^T | -W] [A_y ; A_x]         (k_X x d, sx_off)
+// and the training loss L = ||C C^T - I||^2 + ||C - C_gt||^2 of the same pairs:
+//   kind 3: E    = C C^T - I                                            (k_Y x k_Y, e_off)
+//   kind 4: dL/dC = 4 E C + 2 (C - C_gt)                                (k_Y x k_X, into d_c)
 // M = the output's rows in tiles of 128, N = its columns in tiles of NT (64, 128 or 256),
-// K = the reduction (2 k_Y, k_X or k_Y + k_X) in blocks of 32. Kinds 2 and 1 share the first
-// launch, kind 0 (which reads W) is the second; each launch walks a host-built list of
+// K = the reduction (2 k_Y, k_X, k_Y + k_X or k_Y) in blocks of 32. Kinds 2 and 1 share the
+// first launch, kind 0 (which reads W) is the second; the loss takes kind 3, then kind 4
+// (which reads E), whose tiles also leave their part of ||E||^2 and ||C - C_gt||^2, summed
+// per pair in a fixed order by a third launch. Each launch walks a host-built list of
 // (pair, kind, row tile, column tile) items, longest reduction first.
 //
 // tcgen05.mma kind::tf32 in three passes on TF32 head / remainder splits (x = h + l with
@@ -16,11 +21,19 @@
 // (16-byte stores, conflict-free under the swizzle); thread 0 issues the MMAs and commits
 // each shared-memory stage to its barrier. All waits are bounded; a wait that gives up sets
 // the workspace's control word to FMAP_ERR_TIMEOUT.
+#include "adjoint_tc.cuh"
 #include "fmap_internal.cuh"
 #include "tc_ptx.cuh"
 
 namespace fmap {
 namespace {
+
+// Operands and outputs of the training-loss kinds (3, 4); unused by the adjoint kinds.
+struct LossArgs {
+  const float* c_gt;   // flat C_gt (c offsets)
+  float* d_c;          // flat dL/dC
+  float* partial;      // per pair kMaxLossTiles partial sums of the loss, one per output tile
+};
 
 constexpr int kAdjThreads = 256;
 constexpr int kAdjRows = 128;                              // MMA M
@@ -59,19 +72,24 @@ __device__ __forceinline__ void put_split4(uint32_t head, uint32_t rem, uint32_t
 // NT output columns per CTA (64, 128 or 256: the MMA's N). STAGES shared-memory stages: with
 // one, a CTA's conversion of block kb + 1 waits for the MMAs of kb and the other CTAs on the
 // SM fill the gap; with two, a CTA converts block kb + 1 while the MMAs of kb run.
-template <int STAGES, int NT>
-__global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, const AdjItem* items,
+// LOSS: the instantiation of the loss kinds (3, 4); the adjoint's (0, 1, 2) leave it false.
+// The launch bound asks for the CTAs per SM that the shared memory allows (one stage:
+// 4 / 3 / 2 at 64 / 128 / 256 columns; two stages: 2 / 1 / 1).
+template <int STAGES, int NT, bool LOSS>
+__global__ void __launch_bounds__(kAdjThreads, STAGES == 1 ? (NT == 256 ? 2 : (NT == 128 ? 3 : 4)) : (NT == 64 ? 2 : 1))
+    adjoint_tc_kernel(BatchDev b, const AdjItem* items,
                                                                  const float* a_flat, const float* c_flat,
-                                                                 float* ws) {
+                                                                 float* ws, LossArgs la) {
   using T = AdjTile<NT>;
   extern __shared__ uint8_t smem_raw[];
   const AdjItem it = items[blockIdx.x];
   const PairDev pd = b.pairs[it.pair];
   const int kind = it.kind;
   const int k = pd.k, ky = b.shapes[pd.y].k, d = pd.d;
-  const int rows = kind == 1 ? ky : k;                         // output rows
-  const int ncols = kind == 2 ? k : d;                         // output columns (and B rows)
-  const int kred = kind == 0 ? ky + k : (kind == 1 ? k : 2 * ky);
+  // output rows, output columns (and B rows), reduction length
+  const int rows = (kind == 0 || kind == 2) ? k : ky;
+  const int ncols = kind == 2 ? k : (kind == 3 ? ky : (kind == 4 ? k : d));
+  const int kred = kind == 0 ? ky + k : (kind == 2 ? 2 * ky : (kind == 4 ? ky : k));
   const int r0 = it.r0, f0 = it.f0;
   const int nn = min(NT, ncols - f0), npad = (nn + 15) & ~15;
   const int nkb = (kred + 31) / 32;
@@ -81,6 +99,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
   uint64_t* acc = empty + STAGES;                                             // every MMA completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 2);                       // [8] loss partials
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) tc::mbar_init(&empty[s], 1);
@@ -104,24 +123,29 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
   const float* __restrict__ sa2 = kind == 0 ? ws + pd.w_off : cm;
   const int a2 = kind == 0 ? k : ky;
   const float sgn2 = kind == 0 ? -1.f : 1.f;
-  // B operand: b1 rows of sb1 then b2 rows of sb2, row stride ldb, columns f < ncols.
+  // A operand, kinds 1, 3, 4, read along rows a < k_Y: Gamma, C or E (row stride lda)
+  const float* __restrict__ sar = kind == 1 ? gam : (kind == 3 ? cm : ws + pd.e_off);
+  const int lda = kind == 4 ? ky : k;
+  // B operand: b1 rows of sb1 then b2 rows of sb2, row stride ldb, columns f < ncols; kind 3
+  // reads it along rows instead (B[j][m] = C[j][m])
   const float* __restrict__ sb1 = kind == 0 ? a_flat + b.shapes[pd.y].a_off : (kind == 1 ? ax : cm);
   const float* __restrict__ sb2 = kind == 0 ? ax : gam;
-  const int b1 = kind == 1 ? k : ky, b2 = kind == 0 ? k : (kind == 1 ? 0 : ky);
+  const int b1 = kind == 1 ? k : ky, b2 = kind == 0 ? k : ((kind == 1 || kind == 4) ? 0 : ky);
   const int ldb = ncols;
   const uint32_t idesc = tc::idesc_tf32(kAdjRows, (uint32_t)npad);
   const uint32_t sbase = tc::smem_u32(smem);
 
   // A operand, kinds 0 and 2: thread tid owns row tid % 128 and the 16 K indices
   // 16 * (tid / 128) + j (a warp's loads of one j are 32 consecutive floats of a column).
-  // Kind 1 (Gamma, read along rows): lane = K index, warp + 8 u = row.
-  // B operand: thread tid owns column tid % NT and kPerB consecutive K indices.
+  // Kinds 1, 3, 4 (read along rows): lane = K index, warp + 8 u = row.
+  // B operand: thread tid owns column tid % NT and kPerB consecutive K indices; kind 3:
+  // lane = K index, warp + 8 u = row, like the A operand of kind 1.
   const int ra = tid & (kAdjRows - 1), kq = 16 * (tid >> 7);
   const int fr = tid % NT, kqb = (tid / NT) * T::kPerB, f = f0 + fr;
   const bool b_row = fr < npad, b_in = f < ncols;
   float xa[16], xb[T::kPerB];
   auto fetch = [&](int kb) {
-    if (kind != 1) {
+    if (!LOSS && (kind == 0 || kind == 2)) {
       const int a = r0 + ra;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -138,8 +162,17 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int a = r0 + warp + 8 * u;
-        xa[u] = (a < ky && m < k) ? gam[(int64_t)a * k + m] : 0.f;
+        xa[u] = (a < ky && m < kred) ? sar[(int64_t)a * lda + m] : 0.f;
       }
+    }
+    if (LOSS && kind == 3) {
+      const int m = 32 * kb + lane;
+#pragma unroll
+      for (int u = 0; u < T::kPerB; ++u) {
+        const int jr = f0 + warp + 8 * u;
+        xb[u] = (jr < ky && m < k) ? cm[(int64_t)jr * k + m] : 0.f;
+      }
+      return;
     }
 #pragma unroll
     for (int j = 0; j < T::kPerB; ++j) {
@@ -160,7 +193,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
                    bl = bh + T::kBTile;
     // the stage's previous MMAs (block kb - STAGES) have read it
     if (kb >= STAGES) tc::mbar_wait(&empty[s], (uint32_t)(((kb - STAGES) / STAGES) & 1), abort_flag);
-    if (kind != 1) {
+    if (!LOSS && (kind == 0 || kind == 2)) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) put_split4(ah, al, swz_chunk(ra, (kq >> 2) + c), xa + 4 * c);
     } else {
@@ -173,7 +206,15 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
         st_shared_f32(al + off, xa[u] - h);
       }
     }
-    if (b_row) {
+    if (LOSS && kind == 3) {
+#pragma unroll
+      for (int u = 0; u < T::kPerB; ++u) {
+        const uint32_t off = swz_chunk(warp + 8 * u, lane >> 2) + (uint32_t)((lane & 3) << 2);
+        const float h = tc::tf32_rna(xb[u]);
+        st_shared_f32(bh + off, h);
+        st_shared_f32(bl + off, xb[u] - h);
+      }
+    } else if (b_row) {
 #pragma unroll
       for (int c = 0; c < T::kPerB / 4; ++c) put_split4(bh, bl, swz_chunk(fr, (kqb >> 2) + c), xb + 4 * c);
     }
@@ -200,27 +241,67 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
   bool ok = !*abort_flag && tc::mbar_wait(acc, 0, abort_flag);
   ok = __all_sync(0xffffffffu, ok);   // the TMEM loads below are warp-collective
   tc::tc_fence_after();
+  float part = 0.f;   // kinds 3, 4: this thread's share of the tile's loss terms
   if (ok) {
     // lanes of quadrant warp % 4 are output rows; warps w and w + 4 take column halves
     const int q = warp & 3, h = warp >> 2;
     const int row = r0 + 32 * q + lane;
-    float* out = ws + (kind == 0 ? pd.sx_off : (kind == 1 ? pd.sy_off : pd.w_off));
-    const bool vec = (ncols & 3) == 0;   // 16-byte aligned rows (every offset is)
+    float* out = LOSS ? (kind == 3 ? ws + pd.e_off : la.d_c + pd.c_off)
+                      : ws + (kind == 0 ? pd.sx_off : (kind == 1 ? pd.sy_off : pd.w_off));
+    const float* gt = LOSS ? la.c_gt + pd.c_off : nullptr;
+    // 16-byte stores where every row starts on a 16-byte boundary (the workspace offsets are
+    // aligned; dL/dC sits at the pair's c offset, which need not be)
+    const bool vec = (ncols & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
     for (int c0 = (NT / 2) * h; c0 < npad && c0 < (NT / 2) * (h + 1); c0 += 16) {
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (row < rows) {
-        float* o = out + (int64_t)row * ncols + f0 + c0;
-        if (vec && f0 + c0 + 16 <= ncols) {
+        const int col0 = f0 + c0;
+        if (LOSS && kind == 3) {
+          // E = C C^T - I, and ||E||^2
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            v[j] -= (col0 + j == row) ? 1.f : 0.f;
+            if (col0 + j < ncols) part = fmaf(v[j], v[j], part);
+          }
+        } else if (LOSS) {
+          // dL/dC = 4 E C + 2 (C - C_gt), and ||C - C_gt||^2
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (col0 + j < ncols) {
+              const float r = cm[(int64_t)row * k + col0 + j] - gt[(int64_t)row * k + col0 + j];
+              part = fmaf(r, r, part);
+              v[j] = fmaf(4.f, v[j], 2.f * r);
+            }
+          }
+        }
+        float* o = out + (int64_t)row * ncols + col0;
+        if (vec && col0 + 16 <= ncols) {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             reinterpret_cast<float4*>(o)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (f0 + c0 + j < ncols) o[j] = v[j];
+            if (col0 + j < ncols) o[j] = v[j];
         }
       }
+    }
+  }
+  if (LOSS) {
+    // the tile's loss partial: warp sums, then the eight warps in order (reproducible)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < kAdjThreads / 32; ++w) t += red[w];
+      const int nrt = (ky + kAdjRows - 1) / kAdjRows;
+      const int ne = nrt * ((ky + NT - 1) / NT);                 // E tiles of the pair
+      const int slot = kind == 3 ? (r0 / kAdjRows) * ((ky + NT - 1) / NT) + f0 / NT
+                                 : ne + (r0 / kAdjRows) * ((k + NT - 1) / NT) + f0 / NT;
+      la.partial[(int64_t)it.pair * kMaxLossTiles + slot] = t;
     }
   }
   tc::tc_fence_before();
@@ -241,18 +322,33 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_tc_kernel(BatchDev b, con
 }
 
 template <int STAGES, int NT>
-constexpr size_t adj_smem() { return 1024 + (size_t)STAGES * AdjTile<NT>::kStage + 64; }
+constexpr size_t adj_smem() { return 1024 + (size_t)STAGES * AdjTile<NT>::kStage + 128; }
 
-template <int STAGES, int NT>
+template <int STAGES, int NT, bool LOSS = false>
 cudaError_t set_smem_one() {
-  return cudaFuncSetAttribute(adjoint_tc_kernel<STAGES, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(adjoint_tc_kernel<STAGES, NT, LOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)adj_smem<STAGES, NT>());
 }
 
-template <int STAGES, int NT>
+template <int STAGES, int NT, bool LOSS = false>
 void launch_one(const BatchDev& b, const AdjItem* items, int n, const float* a, const float* c, float* ws,
-                cudaStream_t st) {
-  if (n > 0) adjoint_tc_kernel<STAGES, NT><<<n, kAdjThreads, adj_smem<STAGES, NT>(), st>>>(b, items, a, c, ws);
+                cudaStream_t st, LossArgs la = LossArgs{}) {
+  if (n > 0)
+    adjoint_tc_kernel<STAGES, NT, LOSS><<<n, kAdjThreads, adj_smem<STAGES, NT>(), st>>>(b, items, a, c, ws, la);
+}
+
+// loss[p] = the pair's tile partials of ||E||^2 (kind 3 tiles), then of ||C - C_gt||^2
+// (kind 4 tiles), added in slot order
+__global__ void loss_tc_sum_kernel(BatchDev b, const float* partial, float* loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= b.n_pairs) return;
+  const PairDev pd = b.pairs[p];
+  const int k = pd.k, ky = b.shapes[pd.y].k;
+  const int nrt = (ky + kAdjRows - 1) / kAdjRows;
+  const int n = nrt * ((ky + kLossNt - 1) / kLossNt) + nrt * ((k + kLossNt - 1) / kLossNt);
+  float t = 0.f;
+  for (int s = 0; s < n; ++s) t += partial[(int64_t)p * kMaxLossTiles + s];
+  loss[p] = t;
 }
 
 template <int STAGES>
@@ -272,7 +368,8 @@ cudaError_t adjoint_tc_set_smem() {
   if ((e = set_smem_one<1, 256>()) != cudaSuccess) return e;
   if ((e = set_smem_one<2, 64>()) != cudaSuccess) return e;
   if ((e = set_smem_one<2, 128>()) != cudaSuccess) return e;
-  return set_smem_one<2, 256>();
+  if ((e = set_smem_one<2, 256>()) != cudaSuccess) return e;
+  return set_smem_one<1, kLossNt, true>();
 }
 
 void adjoint_tc_plan(const std::vector<int3>& shapes, int sms, AdjTcPlan& P) {
@@ -321,6 +418,47 @@ cudaError_t launch_adjoint_tc(const BatchDev& b, const AdjItem* items, const Adj
   if (P.stages == 1) launch_nt<1>(P.features, b, items + P.n_first, n2, a, c, ws, st);
   else launch_nt<2>(P.features, b, items + P.n_first, n2, a, c, ws, st);
   return cudaGetLastError();
+}
+
+void adjoint_tc_loss_plan(const std::vector<int3>& shapes, AdjTcPlan& P) {
+  // kind 3 tiles, then kind 4 tiles, each longest reduction first; 128 columns per CTA
+  std::vector<std::pair<int, AdjItem>> e_items, g_items;
+  for (int p = 0; p < (int)shapes.size(); ++p) {
+    const int k = shapes[p].x, ky = shapes[p].y;
+    for (int r0 = 0; r0 < ky; r0 += kAdjRows) {
+      for (int f0 = 0; f0 < ky; f0 += kLossNt) e_items.push_back({(k + 31) / 32, AdjItem{p, 3, r0, f0}});
+      for (int f0 = 0; f0 < k; f0 += kLossNt) g_items.push_back({(ky + 31) / 32, AdjItem{p, 4, r0, f0}});
+    }
+  }
+  auto longest_first = [](const std::pair<int, AdjItem>& u, const std::pair<int, AdjItem>& v) {
+    return u.first > v.first;
+  };
+  std::stable_sort(e_items.begin(), e_items.end(), longest_first);
+  std::stable_sort(g_items.begin(), g_items.end(), longest_first);
+  P.items.clear();
+  for (const auto& x : e_items) P.items.push_back(x.second);
+  for (const auto& x : g_items) P.items.push_back(x.second);
+  P.n_first = (int)e_items.size();
+  P.features = kLossNt;
+  P.stages = 1;
+}
+
+cudaError_t launch_loss_tc(const BatchDev& b, const AdjItem* items, const AdjTcPlan& P, const float* c,
+                           const float* c_gt, float* loss, float* d_c, float* ws, float* partial, cudaStream_t st) {
+  if (P.items.empty()) return cudaSuccess;
+  const LossArgs la{c_gt, d_c, partial};
+  const int n2 = (int)P.items.size() - P.n_first;
+  // E, then dL/dC (which reads E), then the loss sums
+  launch_one<1, kLossNt, true>(b, items, P.n_first, nullptr, c, ws, st, la);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  launch_one<1, kLossNt, true>(b, items + P.n_first, n2, nullptr, c, ws, st, la);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (loss) {
+    loss_tc_sum_kernel<<<(b.n_pairs + 127) / 128, 128, 0, st>>>(b, partial, loss);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace fmap

@@ -505,6 +505,11 @@ def test_adjoint_gemm_kernels(tuning, d):
     out = _gpu_backward(wl, tuning=tuning)
     shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
     assert np.all(out["status"] == 0)
+    # the training loss and dL/dC run on the same kernel (E = C C^T - I, then 4 E C + 2 (C - C_gt));
+    # odd k put the pairs' dL/dC at offsets that are not 16-byte aligned
+    for p in range(len(wl.pairs)):
+        assert abs(out["loss"][p] - losses[p]) <= TOL["fp32"] * max(1.0, abs(losses[p]))
+        assert rel_fro(out["dC"][p], dcs[p]) <= 10 * TOL["fp32"]
     for s in range(len(wl.shapes)):
         assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["fp32"]
         assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
@@ -518,12 +523,15 @@ def test_adjoint_gemm_kernels(tuning, d):
 
 def test_adjoint_default_on_a_batch_that_fills_the_sms():
     """160 pairs (k = 30, d = 256: 320 dA_x tiles of 128 columns, two per SM on 152 SMs):
-    the built-in choice runs the adjoint GEMMs on the tensor cores; dA and dF of every shape
-    against the oracle, and dA against the FP32 FMA tiles."""
+    the built-in choice runs the adjoint GEMMs and the training loss's GEMMs on the tensor
+    cores; the loss, dC, dA and dF against the oracle, and dA against the FP32 FMA tiles."""
     wl = synth.make_small(43, 160, (300, 600), [30], 256)
     out = _gpu_backward(wl)
     shapes_o, pairs_o, fwd, losses, dcs, g = _oracle_backward(wl)
     assert np.all(out["status"] == 0)
+    for p in range(len(wl.pairs)):
+        assert abs(out["loss"][p] - losses[p]) <= TOL["fp32"] * max(1.0, abs(losses[p]))
+        assert rel_fro(out["dC"][p], dcs[p]) <= 10 * TOL["fp32"]
     for s in range(len(wl.shapes)):
         assert rel_fro(out["dA"][s], g["dA"][s]) <= GTOL["fp32"]
         assert rel_fro(out["dF"][s], g["dF"][s]) <= GTOL["fp32"]
